@@ -1,0 +1,138 @@
+"""CPU oracle for rooted spanning trees (TEST INFRASTRUCTURE ONLY).
+
+Thin ctypes wrapper over ``rst_oracle.c``.  Only the test suite,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
+package; the library itself never does.
+
+Parity status per function (what pins each one, see tests/test_oracle_pins.py):
+
+* ``cc_kruskal``   pinned: brute-force minimum spanning forest on <= 8
+                   vertices, closed forms (grid comb), invariants.
+* ``root_forest``  pinned: closed forms (path, star), invariants, verifier.
+* ``euler_tour``   pinned: closed forms (path, star rooted at centre and at a
+                   leaf, hand-derived golden tours), rotation-rule DFS,
+                   agreement of its parent with ``root_forest``.
+* ``bfs``          pinned: Manhattan levels on grids, brute-force parent rule.
+* ``verify``       pinned: Kirchhoff spanning-tree counts (n <= 6), mutations.
+* ``prrst``        parity unpinned for its edge set (the paper fixes no unique
+                   tree); its output is pinned only through ``verify``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+VALID, BAD_ROOT, PARENT_RANGE, NON_EDGE, CYCLE, NOT_SPANNING, COMPONENT_ROOT = range(7)
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            raise RuntimeError(f"{_SO} missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(_SO)
+        P, I64, I32, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        lib.or_cc_kruskal.argtypes = [I64, P, P, P, P, P, P]
+        lib.or_root_forest.argtypes = [I64, I64, P, P, I32, P]
+        lib.or_euler_tour.argtypes = [I64, I64, P, P, I32, P, P, P, P]
+        lib.or_bfs.argtypes = [I64, P, P, I32, P, P]
+        lib.or_verify.argtypes = [I64, P, P, I32, P, I]
+        if hasattr(lib, "or_prrst"):
+            lib.or_prrst.argtypes = [I64, P, P, I32, P, P]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data
+
+
+def _csr(offsets, cols):
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    col = np.ascontiguousarray(np.asarray(cols, dtype=np.int32))
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    return off, col
+
+
+def cc_kruskal(n, offsets, cols):
+    """Return (labels[n], tree_u[T], tree_v[T]) with tree edges u < v in ascending key order."""
+    off, col = _csr(offsets, cols)
+    lab = np.empty(max(n, 1), dtype=np.int32)
+    tu = np.empty(max(n, 1), dtype=np.int32)
+    tv = np.empty(max(n, 1), dtype=np.int32)
+    t = ctypes.c_int64(0)
+    rc = _L().or_cc_kruskal(n, _p(off), _p(col), _p(lab), _p(tu), _p(tv), ctypes.byref(t))
+    if rc != 0:
+        raise ValueError(f"or_cc_kruskal failed: {rc}")
+    T = t.value
+    return lab[:n].copy(), tu[:T].copy(), tv[:T].copy()
+
+
+def root_forest(n, tree_u, tree_v, root):
+    tu = np.ascontiguousarray(np.asarray(tree_u, dtype=np.int32))
+    tv = np.ascontiguousarray(np.asarray(tree_v, dtype=np.int32))
+    T = int(tu.size)
+    if T == 0:
+        tu = np.zeros(1, np.int32); tv = np.zeros(1, np.int32)
+    par = np.empty(max(n, 1), dtype=np.int32)
+    rc = _L().or_root_forest(n, T, _p(tu), _p(tv), int(root), _p(par))
+    if rc != 0:
+        raise ValueError(f"or_root_forest failed: {rc}")
+    return par[:n].copy()
+
+
+def euler_tour(n, tree_u, tree_v, root):
+    """Return (src[2T], dst[2T], rank[2T], parent[n]); arcs in sorted (src, dst) order."""
+    tu = np.ascontiguousarray(np.asarray(tree_u, dtype=np.int32))
+    tv = np.ascontiguousarray(np.asarray(tree_v, dtype=np.int32))
+    T = int(tu.size)
+    E = 2 * T
+    src = np.empty(max(E, 1), np.int32); dst = np.empty(max(E, 1), np.int32)
+    rank = np.empty(max(E, 1), np.int32); par = np.empty(max(n, 1), np.int32)
+    if T == 0:
+        tu = np.zeros(1, np.int32); tv = np.zeros(1, np.int32)
+    rc = _L().or_euler_tour(n, T, _p(tu), _p(tv), int(root), _p(src), _p(dst), _p(rank), _p(par))
+    if rc != 0:
+        raise ValueError(f"or_euler_tour failed: {rc}")
+    return src[:E].copy(), dst[:E].copy(), rank[:E].copy(), par[:n].copy()
+
+
+def bfs(n, offsets, cols, root):
+    """Return (level[n], parent[n])."""
+    off, col = _csr(offsets, cols)
+    lev = np.empty(max(n, 1), np.int32); par = np.empty(max(n, 1), np.int32)
+    rc = _L().or_bfs(n, _p(off), _p(col), int(root), _p(lev), _p(par))
+    if rc != 0:
+        raise ValueError(f"or_bfs failed: {rc}")
+    return lev[:n].copy(), par[:n].copy()
+
+
+def verify(n, offsets, cols, root, parent, strict_roots=True):
+    off, col = _csr(offsets, cols)
+    par = np.ascontiguousarray(np.asarray(parent, dtype=np.int32))
+    if par.size == 0:
+        par = np.zeros(1, np.int32)
+    return int(_L().or_verify(n, _p(off), _p(col), int(root), _p(par), 1 if strict_roots else 0))
+
+
+def rst(n, offsets, cols, root):
+    """The reference RST of the CC + Euler pipeline: Kruskal forest rooted at root."""
+    lab, tu, tv = cc_kruskal(n, offsets, cols)
+    return root_forest(n, tu, tv, root)
+
+
+def prrst(n, offsets, cols, root):
+    off, col = _csr(offsets, cols)
+    par = np.empty(max(n, 1), np.int32)
+    rounds = ctypes.c_int64(0)
+    rc = _L().or_prrst(n, _p(off), _p(col), int(root), _p(par), ctypes.byref(rounds))
+    if rc != 0:
+        raise ValueError(f"or_prrst failed: {rc}")
+    return par[:n].copy(), rounds.value
