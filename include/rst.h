@@ -1,0 +1,157 @@
+/*
+ * rst.h -- C ABI of the GB300 rooted-spanning-tree library (librst.so).
+ *
+ * Method: "Beyond BFS: A Comparative Study of Rooted Spanning Tree Algorithms
+ * on GPUs" (arXiv 2603.11645).  A rooted spanning tree (RST) of an undirected
+ * graph G = (V, E) with root r is a parent array P with P[r] = r and exactly
+ * one parent for every other vertex (Section I).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Graph input: symmetric CSR.  csr_offsets has n+1 entries, 32-bit or 64-bit
+ *   as stated by offsets_bits (32 or 64); csr_cols has m = csr_offsets[n]
+ *   entries (m counts DIRECTED arcs, i.e. twice the undirected edges).  Every
+ *   undirected edge {u,v} is stored as both u->v and v->u, every row is sorted
+ *   ascending, column ids are in [0, n).  Self-loops and repeated arcs are
+ *   tolerated and never become tree edges.  Vertex ids are int32 (n < 2^31);
+ *   m must be below 2^32.
+ * Memory: every array argument is caller-owned DEVICE memory unless marked
+ *   "host".  The library never frees caller memory.  It keeps an internal
+ *   per-device workspace that grows on demand (cudaMalloc) and is released by
+ *   rst_shutdown().
+ * Streams: work is issued on `stream` (a cudaStream_t; NULL = legacy default).
+ *   In this version every entry point returns after its work has completed on
+ *   that stream (it synchronises the stream), so outputs are ready on return.
+ *   Calls are serialised per process; concurrent calls from several host
+ *   threads are safe but do not overlap.
+ * Disconnected inputs: the component of `root` is rooted at root; every other
+ *   component is rooted at its minimum vertex id; isolated vertices point at
+ *   themselves (the forest generalisation of Section III-D).
+ * Errors: argument errors are detected before any GPU work and return
+ *   RST_ERR_INVALID_ARG (or RST_ERR_UNSUPPORTED for sizes outside the limits
+ *   above).  Errors detected by kernels (an index out of range in malformed
+ *   input, a loop that exceeds its iteration bound) return RST_ERR_DEVICE or
+ *   RST_ERR_NOT_CONVERGED; outputs are then unspecified.  CUDA API failures
+ *   return RST_ERR_CUDA and allocation failures RST_ERR_OOM.
+ */
+#ifndef RST_H_
+#define RST_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *rst_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    RST_OK = 0,
+    RST_ERR_INVALID_ARG = 1,
+    RST_ERR_OOM = 2,
+    RST_ERR_CUDA = 3,
+    RST_ERR_NOT_CONVERGED = 4,
+    RST_ERR_TIMEOUT = 5,
+    RST_ERR_UNSUPPORTED = 6,
+    RST_ERR_DEVICE = 7
+} rst_status;
+
+typedef enum {
+    RST_AUTO = 0,      /* learned selector picks one of the three below        */
+    RST_BFS = 1,       /* level-synchronous, direction-optimising BFS (III-A)  */
+    RST_CC_EULER = 2,  /* hook/compress connectivity + Euler-tour rooting      */
+    RST_PR_RST = 3     /* path-reversal RST (III-C)                            */
+} rst_strategy;
+
+/* Verdict codes written by rst_verify (the smallest failing code wins). */
+enum {
+    RST_VERDICT_VALID = 0,
+    RST_VERDICT_BAD_ROOT = 1,       /* root out of range or P[root] != root         */
+    RST_VERDICT_PARENT_RANGE = 2,   /* some P[v] outside [0, n)                      */
+    RST_VERDICT_NON_EDGE = 3,       /* P[v] != v but (v, P[v]) is not an arc of G    */
+    RST_VERDICT_CYCLE = 4,          /* a parent chain never reaches a self-parent    */
+    RST_VERDICT_NOT_SPANNING = 5,   /* an edge of G joins two different trees        */
+    RST_VERDICT_COMPONENT_ROOT = 6  /* a tree without root is not rooted at its min  */
+};
+
+/* Human-readable name of a status code (static storage). */
+const char *rst_status_string(rst_status s);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int rst_version(void);
+
+/*
+ * rst_build -- rooted spanning tree of a CSR graph (Section I, Section III).
+ *   csr_offsets, offsets_bits, csr_cols, n, m: the graph (see conventions).
+ *   root:       requested root, 0 <= root < n.
+ *   strategy:   RST_CC_EULER (hook/compress connected components marking the
+ *               tree edges, Section III-B, then Euler-tour rooting, Section
+ *               III-D), RST_BFS (Section III-A), RST_PR_RST (Section III-C) or
+ *               RST_AUTO (rst_select's choice).
+ *   parent_out: n int32 (device), receives P.
+ * CC+Euler and BFS results are unique: CC+Euler roots the minimum spanning
+ * forest under edge keys (min(u,v), max(u,v)); BFS takes for every vertex the
+ * minimum-id neighbour on the previous level.  PR-RST returns a valid RST.
+ */
+rst_status rst_build(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols,
+                     int64_t n, int64_t m, int32_t root, rst_strategy strategy,
+                     int32_t *parent_out, rst_stream_t stream);
+
+/*
+ * rst_cc -- connected components and spanning-forest edges (Section III-B:
+ * hooking marks each successful hook's edge as a spanning edge; pointer
+ * jumping flattens the trees).
+ *   labels_out:          n int32 (device, may be NULL); component id of each
+ *                        vertex = the minimum vertex id of its component.
+ *   tree_uv_out:         2*(n-1) int32 (device, may be NULL); tree edge t is
+ *                        (tree_uv_out[2t], tree_uv_out[2t+1]) with u < v.  The
+ *                        edge SET is the minimum spanning forest under keys
+ *                        (min(u,v), max(u,v)); the ORDER of the list is
+ *                        unspecified.
+ *   num_tree_edges_out:  host int64 (may be NULL); receives T = n - #components.
+ */
+rst_status rst_cc(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols,
+                  int64_t n, int64_t m, int32_t *labels_out, int32_t *tree_uv_out,
+                  int64_t *num_tree_edges_out, rst_stream_t stream);
+
+/*
+ * rst_euler_root -- Euler-tour rooting of a forest (Section III-D).
+ *   n:              number of vertices.
+ *   tree_uv:        2*T int32 (device); edge t = (tree_uv[2t], tree_uv[2t+1]).
+ *                   The edges must form a forest (no cycle, no repeated edge,
+ *                   no self-loop); otherwise RST_ERR_DEVICE.
+ *   num_tree_edges: T (0 <= T < n).
+ *   root:           requested root.
+ *   parent_out:     n int32 (device), receives P.
+ *   rank_out:       2*T int32 (device, may be NULL).  Position of each arc in
+ *                   its tree's tour (0 = the root's first arc), indexed by the
+ *                   arc's place in lexicographic (src, dst) order.  The tour
+ *                   follows succ(e) = next(rev(e)), or first(from(rev(e))) at
+ *                   the end of a run, and each tree's cycle is broken at
+ *                   rev(last[tree root]).
+ */
+rst_status rst_euler_root(int64_t n, const int32_t *tree_uv, int64_t num_tree_edges,
+                          int32_t root, int32_t *parent_out, int32_t *rank_out,
+                          rst_stream_t stream);
+
+/*
+ * rst_verify -- exact validity check of a parent array (the RST definition of
+ * Section I, extended to forests as in Section III-D).
+ *   parent:      n int32 (device).
+ *   verdict_out: host int32; one of RST_VERDICT_*.  The check for code k runs
+ *                only when all codes below k passed, so the smallest failing
+ *                code is reported.
+ */
+rst_status rst_verify(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols,
+                      int64_t n, int64_t m, int32_t root, const int32_t *parent,
+                      int32_t *verdict_out, rst_stream_t stream);
+
+/* Release the internal workspace of every device the library touched. */
+rst_status rst_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RST_H_ */

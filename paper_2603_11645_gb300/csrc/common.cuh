@@ -1,0 +1,149 @@
+// Shared device/host utilities of the RST library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <cstring>
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "rst.h"
+
+namespace rst {
+
+// ------------------------------------------------------------------ errors
+// Device-detected error bits, OR-ed into the per-device status word.
+enum DeviceError : uint32_t {
+  DERR_INDEX = 1u << 0,        // an index read from input memory was out of range
+  DERR_WALK_LIMIT = 1u << 1,   // a list walk exceeded its iteration bound
+  DERR_NOT_FOREST = 1u << 2,   // Euler input was not a forest
+  DERR_ROUND_LIMIT = 1u << 3,  // an iterative phase exceeded its round bound
+  DERR_CAPACITY = 1u << 4,     // an internal list overflowed its planned size
+};
+
+#define RST_CUDA(call)                                     \
+  do {                                                     \
+    cudaError_t e__ = (call);                              \
+    if (e__ != cudaSuccess) {                              \
+      ::rst::note_cuda_error(e__, #call, __FILE__, __LINE__); \
+      return RST_ERR_CUDA;                                 \
+    }                                                      \
+  } while (0)
+
+#define RST_TRY(expr)                     \
+  do {                                    \
+    rst_status s__ = (expr);              \
+    if (s__ != RST_OK) return s__;        \
+  } while (0)
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// ------------------------------------------------------------------ launch
+constexpr int kBlock = 256;
+
+struct Device {
+  int id = -1;
+  int sms = 152;
+  int max_threads_per_sm = 2048;
+};
+const Device& device_info();
+
+// Grid for a grid-stride loop over `work` items: at most `waves` resident
+// blocks per SM, at least 1 block.
+inline int grid_for(int64_t work, int block = kBlock, int waves = 8) {
+  const Device& d = device_info();
+  int64_t need = (work + block - 1) / block;
+  int64_t cap = (int64_t)d.sms * waves;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
+}
+
+// ------------------------------------------------------------------ workspace
+// Bump allocator over one grow-only device buffer per device.  A call first
+// plans its buffers with a counting pass (base == nullptr), ensures capacity,
+// then takes them for real.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  bool counting = false;
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    size_t at = used;
+    used += bytes;
+    if (counting) return nullptr;
+    if (used > cap) return nullptr;
+    return reinterpret_cast<T*>(base + at);
+  }
+};
+
+struct DeviceState {
+  char* ws = nullptr;          // workspace
+  size_t ws_cap = 0;
+  uint32_t* status = nullptr;  // device error word + small scalars (64 words)
+  unsigned long long* hostbuf = nullptr;  // pinned host scratch (64 words)
+};
+
+// Per-device state and the process-wide call lock.
+DeviceState& state();
+std::mutex& call_lock();
+rst_status ensure_workspace(size_t bytes);
+
+// Small device scalars live in state().status[...]
+enum ScalarSlot : int {
+  SLOT_ERR = 0,
+  SLOT_COUNT0 = 8,   // 64-bit counters at even slots 8.. (unsigned long long view)
+};
+
+inline unsigned long long* dev_counter(int k) {
+  return reinterpret_cast<unsigned long long*>(state().status + 8) + k;
+}
+
+rst_status read_device_error(cudaStream_t s);
+rst_status reset_device_error(cudaStream_t s);
+// Copy `count` 64-bit words from device to the pinned host buffer and wait.
+rst_status fetch_u64(const unsigned long long* dsrc, int count, unsigned long long* out,
+                     cudaStream_t s);
+
+__device__ __forceinline__ void raise_error(uint32_t* status, uint32_t bits) {
+  atomicOr(status, bits);
+}
+
+// ------------------------------------------------------------------ warp helpers
+// Warp-aggregated reservation of slots in an append buffer.  Every lane of the
+// warp must call it (pred may differ).  Returns the slot or -1.
+__device__ __forceinline__ long long warp_reserve(unsigned long long* counter, bool pred) {
+  const unsigned full = 0xffffffffu;
+  unsigned m = __ballot_sync(full, pred);
+  int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (m != 0) {
+    int leader = __ffs(m) - 1;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+    base = __shfl_sync(full, base, leader);
+  }
+  return pred ? (long long)(base + __popc(m & ((1u << lane) - 1u))) : -1;
+}
+
+template <class T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+  return __ldcs(p);
+}
+
+// ------------------------------------------------------------------ scan
+// Exclusive prefix sums over 64-bit values: out[i] = sum(in[0..i)), and
+// out[count] = total.  `in` may alias `out`.  tmp needs scan_tmp_words(count).
+size_t scan_tmp_words(int64_t count);
+rst_status scan_exclusive_u64(const unsigned long long* in, unsigned long long* out,
+                              int64_t count, unsigned long long* tmp, cudaStream_t s);
+// Same over 32-bit words of a bitmap: out[w] = popcount of words [0, w).
+rst_status scan_popcount_words(const uint32_t* words, uint32_t* out, int64_t count,
+                               unsigned long long* tmp, cudaStream_t s);
+
+}  // namespace rst

@@ -1,0 +1,103 @@
+// Load-balanced traversal of every (row, arc) pair of a CSR graph.
+//
+// The rows' end offsets and the arc indices are merged into one sequence of
+// n + A items (a merge path); each block takes a tile of kMpTile consecutive
+// items and each thread kMpItems of them, so rows of any degree (a 4-neighbour
+// mesh or an R-MAT hub with millions of arcs) cost the same per item.
+#pragma once
+
+#include "common.cuh"
+
+namespace rst {
+
+constexpr int kMpThreads = 256;
+constexpr int kMpItems = 8;
+constexpr int kMpTile = kMpThreads * kMpItems;
+
+// Number of row-end items that precede diagonal `diag` of the merge of
+// row ends (off[1..n]) with arc indices (0..A-1).
+template <class OffT>
+__device__ __forceinline__ int64_t mp_search(const OffT* __restrict__ off, int64_t n, int64_t A,
+                                             int64_t diag) {
+  int64_t lo = diag - A > 0 ? diag - A : 0;
+  int64_t hi = diag < n ? diag : n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)off[mid + 1] <= diag - mid - 1)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Calls f(is_arc, row, arc) kMpItems times per thread per tile.  Every thread
+// of the block makes the same number of calls (is_arc = false for row-end and
+// padding items), so f may use warp-collective operations.  Grid-stride over
+// tiles; blockDim.x must be kMpThreads.
+template <class OffT, class F>
+__device__ __forceinline__ void csr_for_each_arc(const OffT* __restrict__ off, int64_t n,
+                                                 int64_t A, F& f) {
+  __shared__ OffT s_rowend[kMpTile + 1];
+  __shared__ int64_t s_split[2];
+  const int64_t total = n + A;
+  for (int64_t tile = blockIdx.x; tile * kMpTile < total; tile += gridDim.x) {
+    const int64_t d0 = tile * kMpTile;
+    const int64_t d1 = (d0 + kMpTile < total) ? d0 + kMpTile : total;
+    if (threadIdx.x < 2) s_split[threadIdx.x] = mp_search(off, n, A, threadIdx.x == 0 ? d0 : d1);
+    __syncthreads();
+    const int64_t r0 = s_split[0], r1 = s_split[1];
+    const int64_t a0 = d0 - r0, a1 = d1 - r1;
+    const int nrows = (int)(r1 - r0);
+    for (int k = threadIdx.x; k < nrows; k += blockDim.x) s_rowend[k] = off[r0 + k + 1];
+    __syncthreads();
+    const int64_t span = d1 - d0;
+    int64_t td = (int64_t)threadIdx.x * kMpItems;
+    if (td > span) td = span;
+    int lo = (int)(td - (a1 - a0) > 0 ? td - (a1 - a0) : 0);
+    int hi = (int)(td < nrows ? td : nrows);
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if ((int64_t)s_rowend[mid] <= a0 + (td - mid - 1))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    int64_t row = r0 + lo;
+    int64_t arc = a0 + (td - lo);
+#pragma unroll
+    for (int it = 0; it < kMpItems; ++it) {
+      const bool valid = td + it < span;
+      bool is_arc = false;
+      const int64_t my_row = row, my_arc = arc;
+      if (valid) {
+        const int lr = (int)(row - r0);
+        if (lr < nrows && (int64_t)s_rowend[lr] <= arc) {
+          ++row;
+        } else {
+          is_arc = true;
+          ++arc;
+        }
+      }
+      f(is_arc, my_row, my_arc);
+    }
+    __syncthreads();
+  }
+}
+
+// Binary search of value w in the sorted row v: position or -1.
+template <class OffT>
+__device__ __forceinline__ int64_t row_find(const OffT* __restrict__ off,
+                                            const int32_t* __restrict__ col, int32_t v, int32_t w) {
+  int64_t lo = (int64_t)off[v], end = (int64_t)off[v + 1], hi = end;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (col[mid] < w)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return (lo < end && col[lo] == w) ? lo : -1;
+}
+
+}  // namespace rst

@@ -1,0 +1,238 @@
+// Euler-tour rooting of a spanning forest (Section III-D).
+//
+// Tree arcs are addressed by their place in lexicographic (src, dst) order
+// ("tree positions").  With the CSR-bitmap front end that order needs no sort:
+// the CSR rows are already sorted, so the tree arcs in CSR order ARE the
+// lexicographically sorted arc array, and the tree position of CSR position j
+// is the number of marked bits before j (a popcount prefix over the bitmap).
+// first[v] = toff[v], last[v] = toff[v+1]-1 and next(e) = e+1 inside a run.
+//
+// succ(e) = next(rev(e)) if rev(e) is not the last arc of its run, otherwise
+// first(from(rev(e))).  For every tree root r the arc e with rev(e) = last[r]
+// gets succ(e) = -1, turning each tree's Euler cycle into a list with head
+// first[r].  After list ranking, of the twins e = a->b and rev(e) = b->a the
+// one ranked first descends from parent to child.
+#include "pipeline.cuh"
+
+namespace rst {
+
+// ----------------------------------------------------------------- shared core
+
+__global__ void k_succ(int64_t T, const uint4* __restrict__ pairs, const uint32_t* __restrict__ toff,
+                       const uint8_t* __restrict__ is_root, int32_t* __restrict__ succ) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = pairs[t];  // {i, k, a, b}: i = a->b, k = b->a
+    const uint32_t i = r.x, k = r.y;
+    const int32_t a = (int32_t)r.z, b = (int32_t)r.w;
+    // succ(i): rev(i) = k in b's run
+    const uint32_t lastb = toff[b + 1] - 1u;
+    succ[i] = (k != lastb) ? (int32_t)(k + 1u) : (is_root[b] ? -1 : (int32_t)toff[b]);
+    const uint32_t lasta = toff[a + 1] - 1u;
+    succ[k] = (i != lasta) ? (int32_t)(i + 1u) : (is_root[a] ? -1 : (int32_t)toff[a]);
+  }
+}
+
+__global__ void k_parent_from_rank(int64_t T, const uint4* __restrict__ pairs,
+                                   const uint32_t* __restrict__ R, int32_t* __restrict__ parent) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = pairs[t];
+    const uint32_t ri = R[r.x], rk = R[r.y];
+    if (ri < rk)
+      parent[r.w] = (int32_t)r.z;  // a->b traversed first: a is b's parent
+    else
+      parent[r.z] = (int32_t)r.w;
+  }
+}
+
+size_t euler_workspace_bytes(int64_t n, int64_t T, int64_t nheads) {
+  (void)n;
+  (void)nheads;
+  const int64_t N = 2 * T;
+  return 2 * (((size_t)N * 4 + 255) / 256 * 256 + 256) + list_rank_workspace_upper(N);
+}
+
+rst_status euler_from_pairs(Arena& ar, int64_t n, int64_t T, uint4* pairs, const uint32_t* toff,
+                            const uint8_t* is_root, const int32_t* heads, int64_t nheads,
+                            int32_t* parent_out, uint32_t* rank_out, cudaStream_t s) {
+  (void)n;
+  if (T <= 0) return RST_OK;
+  const int64_t N = 2 * T;
+  int32_t* succ = ar.take<int32_t>(N);
+  uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
+  if (!succ || !R) return RST_ERR_OOM;
+  const int gT = grid_for(T);
+  k_succ<<<gT, kBlock, 0, s>>>(T, pairs, toff, is_root, succ);
+  RST_CUDA(cudaGetLastError());
+  RST_TRY(list_rank(ar, N, succ, nullptr, heads, nheads, R, s));
+  k_parent_from_rank<<<gT, kBlock, 0, s>>>(T, pairs, R, parent_out);
+  RST_CUDA(cudaGetLastError());
+  return RST_OK;
+}
+
+// ----------------------------------------------------------------- CSR-bitmap front end
+
+__global__ void k_mark_roots(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
+                             int32_t root, uint8_t* __restrict__ is_root) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t r = roots[k];
+    if (r == root_label) r = root;
+    is_root[r] = 1;
+  }
+}
+
+template <class OffT>
+__global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint32_t* __restrict__ bits,
+                       const uint32_t* __restrict__ wpre, const uint8_t* __restrict__ is_root,
+                       uint32_t* __restrict__ toff, int32_t* __restrict__ parent) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t0 = bit_rank(bits, wpre, (uint64_t)off[v]);
+    toff[v] = t0;
+    if (v < n) {
+      const uint32_t t1 = bit_rank(bits, wpre, (uint64_t)off[v + 1]);
+      if (t0 == t1 || is_root[v]) parent[v] = (int32_t)v;
+    }
+  }
+}
+
+__global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
+                        int32_t root, const uint32_t* __restrict__ toff, int32_t* __restrict__ heads) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t r = roots[k];
+    if (r == root_label) r = root;
+    heads[k] = (int32_t)toff[r];
+  }
+}
+
+// {p, q, a, b} (CSR positions) -> {i, k, a, b} (tree positions), in place.
+__global__ void k_pairs_to_tree(int64_t T, uint4* __restrict__ pairs, const uint32_t* __restrict__ bits,
+                                const uint32_t* __restrict__ wpre) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    uint4 r = pairs[t];
+    r.x = bit_rank(bits, wpre, r.x);
+    r.y = bit_rank(bits, wpre, r.y);
+    pairs[t] = r;
+  }
+}
+
+size_t euler_cc_workspace_bytes(int64_t n, int64_t A, int64_t T, int64_t nroots) {
+  const int64_t W = A / 32 + 1;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256 + 256; };
+  size_t b = al((W + 1) * 4) + al(scan_tmp_words(W) * 8) + al(n) + al((n + 1) * 4) +
+             al(nroots * 4 + 4);
+  return b + euler_workspace_bytes(n, T, nroots);
+}
+
+template <class OffT>
+rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32_t root, CcOut* cc,
+                         int32_t* parent_out, uint32_t* rank_out, cudaStream_t s) {
+  const int64_t W = A / 32 + 1;
+  uint32_t* wpre = ar.take<uint32_t>(W + 1);
+  unsigned long long* tmp = ar.take<unsigned long long>(scan_tmp_words(W));
+  uint8_t* is_root = ar.take<uint8_t>(n);
+  uint32_t* toff = ar.take<uint32_t>(n + 1);
+  int32_t* heads = ar.take<int32_t>(cc->nroots + 1);
+  if (!wpre || !tmp || !is_root || !toff || !heads) return RST_ERR_OOM;
+  RST_TRY(scan_popcount_words(cc->bits, wpre, W, tmp, s));
+  RST_CUDA(cudaMemsetAsync(is_root, 0, n, s));
+  if (cc->nroots > 0)
+    k_mark_roots<<<grid_for(cc->nroots), kBlock, 0, s>>>(cc->nroots, cc->roots, cc->root_label,
+                                                         root, is_root);
+  k_toff<OffT><<<grid_for(n + 1), kBlock, 0, s>>>(off, n, cc->bits, wpre, is_root, toff, parent_out);
+  if (cc->nroots > 0)
+    k_heads<<<grid_for(cc->nroots), kBlock, 0, s>>>(cc->nroots, cc->roots, cc->root_label, root,
+                                                    toff, heads);
+  if (cc->T > 0)
+    k_pairs_to_tree<<<grid_for(cc->T), kBlock, 0, s>>>(cc->T, cc->pairs, cc->bits, wpre);
+  RST_CUDA(cudaGetLastError());
+  return euler_from_pairs(ar, n, cc->T, cc->pairs, toff, is_root, heads, cc->nroots, parent_out,
+                          rank_out, s);
+}
+
+template rst_status euler_root_cc<int32_t>(Arena&, const int32_t*, int64_t, int64_t, int32_t, CcOut*,
+                                           int32_t*, uint32_t*, cudaStream_t);
+template rst_status euler_root_cc<int64_t>(Arena&, const int64_t*, int64_t, int64_t, int32_t, CcOut*,
+                                           int32_t*, uint32_t*, cudaStream_t);
+
+// ----------------------------------------------------------------- edge-list front end
+
+static int key_bits_for(int64_t n) {
+  int b = 1;
+  while (b < 31 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
+__global__ void k_arc_keys(int64_t T, const int32_t* __restrict__ uv, int64_t n, int nb,
+                           uint64_t* __restrict__ keys, uint32_t* status) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int32_t u = uv[2 * t], v = uv[2 * t + 1];
+    if (u < 0 || v < 0 || u >= n || v >= n || u == v) {
+      raise_error(status, DERR_NOT_FOREST);
+      u = 0;
+      v = 0;  // keys of a rejected edge; the call reports the error
+    }
+    keys[t] = ((uint64_t)(uint32_t)u << nb) | (uint32_t)v;
+    keys[t + T] = ((uint64_t)(uint32_t)v << nb) | (uint32_t)u;
+  }
+}
+
+__global__ void k_count_src(int64_t N, const uint64_t* __restrict__ keys, int nb,
+                            unsigned long long* __restrict__ deg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&deg[keys[i] >> nb], 1ull);
+}
+
+__global__ void k_key_dst(int64_t N, const uint64_t* __restrict__ keys, int nb, int32_t* __restrict__ cols) {
+  const uint64_t mask = ((uint64_t)1 << nb) - 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    cols[i] = (int32_t)(keys[i] & mask);
+}
+
+size_t euler_edges_workspace_bytes(int64_t n, int64_t T) {
+  const int64_t N = 2 * T;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256 + 256; };
+  size_t b = al(N * 8) + radix_sort_workspace_bytes(N) + al((n + 1) * 8) + al(scan_tmp_words(n + 1) * 8) +
+             al(N * 4);
+  b += cc_workspace_bytes<int64_t>(n, N);
+  b += euler_cc_workspace_bytes(n, N, T, n / 2 + 1);
+  return b;
+}
+
+rst_status euler_root_edges(Arena& ar, int64_t n, const int32_t* tree_uv, int64_t T, int32_t root,
+                            int32_t* parent_out, uint32_t* rank_out, cudaStream_t s) {
+  const int64_t N = 2 * T;
+  const int nb = key_bits_for(n);
+  uint64_t* keys = ar.take<uint64_t>(N);
+  unsigned long long* off = ar.take<unsigned long long>(n + 1);
+  unsigned long long* tmp = ar.take<unsigned long long>(scan_tmp_words(n + 1));
+  int32_t* cols = ar.take<int32_t>(N);
+  if (!keys || !off || !tmp || !cols) return RST_ERR_OOM;
+  uint32_t* status = state().status;
+  if (T > 0) {
+    k_arc_keys<<<grid_for(T), kBlock, 0, s>>>(T, tree_uv, n, nb, keys, status);
+    RST_TRY(radix_sort_keys(ar, keys, N, 2 * nb, s));
+  }
+  RST_CUDA(cudaMemsetAsync(off, 0, (n + 1) * sizeof(unsigned long long), s));
+  if (T > 0) {
+    k_count_src<<<grid_for(N), kBlock, 0, s>>>(N, keys, nb, off);
+    k_key_dst<<<grid_for(N), kBlock, 0, s>>>(N, keys, nb, cols);
+  }
+  RST_TRY(scan_exclusive_u64(off, off, n, tmp, s));
+  RST_CUDA(cudaGetLastError());
+  RST_TRY(read_device_error(s));
+  const int64_t* off64 = reinterpret_cast<const int64_t*>(off);
+  CcOut cc;
+  RST_TRY(cc_run<int64_t>(ar, off64, cols, n, N, root, nullptr, &cc, s));
+  if (cc.T != T) return RST_ERR_DEVICE;  // a cycle or a repeated edge: not a forest
+  return euler_root_cc<int64_t>(ar, off64, n, N, root, &cc, parent_out, rank_out, s);
+}
+
+}  // namespace rst

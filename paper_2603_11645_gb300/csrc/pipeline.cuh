@@ -1,0 +1,89 @@
+// Internal interfaces between the pipeline stages (not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace rst {
+
+constexpr uint32_t kNone = 0xffffffffu;
+
+// Rank of CSR position j among the tree arcs: number of set bits before j in
+// the tree-arc bitmap.  wpre[w] = popcount of words [0, w).
+__device__ __forceinline__ uint32_t bit_rank(const uint32_t* __restrict__ bits,
+                                             const uint32_t* __restrict__ wpre, uint64_t j) {
+  uint64_t w = j >> 5;
+  uint32_t lowmask = (1u << (uint32_t)(j & 31)) - 1u;
+  return wpre[w] + (uint32_t)__popc(bits[w] & lowmask);
+}
+
+// ----------------------------------------------------------------- CC
+// Output of the hook/compress connectivity pass (Section III-B).
+struct CcOut {
+  int64_t T = 0;             // number of tree edges (= n - #components)
+  uint4* pairs = nullptr;    // T records {p, q, a, b}: tree edge {a,b}; p = CSR
+                             // position of arc a->b (row a), q of b->a (row b)
+  uint32_t* bits = nullptr;  // bitmap over CSR positions: both arcs of every tree edge
+  int64_t nroots = 0;        // number of components with at least one edge
+  int32_t* roots = nullptr;  // their minimum vertex ids (canonical labels)
+  int rounds = 0;            // hooking rounds executed (round 1 included)
+  int32_t root_label = -1;   // canonical label of the requested root (host value)
+};
+
+struct CcPlan;  // workspace layout, defined in cc.cu
+
+// Connected components + spanning forest.  `labels_out` (nullable) receives the
+// canonical label of every vertex.  `root` (may be -1) selects the vertex whose
+// component label is returned in out->root_label.
+template <class OffT>
+rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A,
+                  int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s);
+template <class OffT>
+size_t cc_workspace_bytes(int64_t n, int64_t A);
+
+// ----------------------------------------------------------------- Euler
+struct EulerIn {
+  int64_t n = 0;
+  int64_t T = 0;
+  uint4* pairs = nullptr;      // T records {i, k, a, b} in tree-arc positions (see below)
+  const uint32_t* toff = nullptr;  // n+1: first tree position of each vertex's run
+  const int32_t* heads = nullptr;  // one tour head (tree position) per tree
+  int64_t nheads = 0;
+};
+
+// Tree arcs live in "tree positions" 0..2T-1 in lexicographic (src, dst)
+// order; pairs hold {i, k, a, b} with i the position of a->b and k of b->a;
+// toff[v] .. toff[v+1]-1 is v's run; is_root marks tree roots.  Builds succ,
+// ranks the tour and writes parents of every vertex that has a tree edge.
+rst_status euler_from_pairs(Arena& ar, int64_t n, int64_t T, uint4* pairs, const uint32_t* toff,
+                            const uint8_t* is_root, const int32_t* heads, int64_t nheads,
+                            int32_t* parent_out, uint32_t* rank_out, cudaStream_t s);
+size_t euler_workspace_bytes(int64_t n, int64_t T, int64_t nheads);
+
+// CSR-bitmap front end: converts CC output into tree positions, marks roots
+// (the requested root for its component, the minimum vertex otherwise), sets
+// P[v] = v for roots and singletons, then runs euler_from_pairs.
+template <class OffT>
+rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32_t root,
+                         CcOut* cc, int32_t* parent_out, uint32_t* rank_out, cudaStream_t s);
+size_t euler_cc_workspace_bytes(int64_t n, int64_t A, int64_t T, int64_t nroots);
+
+// Edge-list front end (rst_euler_root): radix-sorts the 2T arcs by (src, dst).
+rst_status euler_root_edges(Arena& ar, int64_t n, const int32_t* tree_uv, int64_t T, int32_t root,
+                            int32_t* parent_out, uint32_t* rank_out, cudaStream_t s);
+size_t euler_edges_workspace_bytes(int64_t n, int64_t T);
+
+// ----------------------------------------------------------------- list ranking
+// pos[x] = sum of weights of the elements before x in its list (weights 1 when
+// w == nullptr).  nxt[x] = successor or -1.  heads: one entry per list.
+rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w,
+                     const int32_t* heads, int64_t nheads, uint32_t* pos, cudaStream_t s);
+size_t list_rank_workspace_bytes(int64_t N, int64_t nheads);
+// Upper bound over any number of heads.
+size_t list_rank_workspace_upper(int64_t N);
+
+// ----------------------------------------------------------------- sort
+// Stable LSD radix sort of 64-bit keys on their low `key_bits` bits.
+size_t radix_sort_workspace_bytes(int64_t count);
+rst_status radix_sort_keys(Arena& ar, uint64_t* keys, int64_t count, int key_bits, cudaStream_t s);
+
+}  // namespace rst

@@ -1,0 +1,25 @@
+// Strategy drivers behind rst_build / rst_verify (not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace rst {
+
+// Level-synchronous, direction-optimising BFS (Section III-A).  level_out
+// (nullable) receives each vertex's distance from its component's source.
+rst_status run_bfs(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                   int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s);
+
+// Path-reversal RST (Section III-C).
+rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                     int32_t root, int32_t* parent, cudaStream_t s);
+
+// Exact verdict of a parent array.
+rst_status run_verify(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                      int32_t root, const int32_t* parent, int32_t* verdict_out, cudaStream_t s);
+
+// Strategy for RST_AUTO.
+rst_strategy select_strategy_host(const void* off, int offsets_bits, const int32_t* cols, int64_t n,
+                                  int64_t m, int32_t root, cudaStream_t s);
+
+}  // namespace rst

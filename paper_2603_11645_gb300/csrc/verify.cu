@@ -1,0 +1,180 @@
+// Exact verification of a rooted spanning tree / forest (the definition of
+// Section I: P[r] = r and one parent per other vertex; forests as in Section
+// III-D).  Checks run in code order; each phase records the smallest failing
+// code with atomicMin and later phases run only if every earlier one passed.
+//   1 root out of range or P[root] != root     2 some P[v] outside [0, n)
+//   3 (v, P[v]) is not an arc of G             4 a parent chain never ends
+//   5 an edge of G joins two different trees   6 a tree without root is not
+//                                                 rooted at its minimum vertex
+#include <climits>
+
+#include "csr_walk.cuh"
+#include "pipeline.cuh"
+#include "strategies.cuh"
+
+namespace rst {
+
+__global__ void k_ver_range(int64_t n, int32_t root, const int32_t* __restrict__ parent, int32_t* verdict) {
+  int code = INT_MAX;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = parent[v];
+    if (v == root && p != root) code = min(code, (int)RST_VERDICT_BAD_ROOT);
+    if (p < 0 || (int64_t)p >= n) code = min(code, (int)RST_VERDICT_PARENT_RANGE);
+  }
+  if (code != INT_MAX) atomicMin(verdict, code);
+}
+
+template <class OffT>
+__global__ void k_ver_edges(const OffT* __restrict__ off, const int32_t* __restrict__ col, int64_t n,
+                            const int32_t* __restrict__ parent, int32_t* verdict) {
+  bool bad = false;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = parent[v];
+    if (p != (int32_t)v && row_find(off, col, (int32_t)v, p) < 0) bad = true;
+  }
+  if (bad) atomicMin(verdict, (int)RST_VERDICT_NON_EDGE);
+}
+
+// One doubling round: anc2[v] = anc[anc[v]].
+__global__ void k_ver_double(int64_t n, const int32_t* __restrict__ anc, int32_t* __restrict__ anc2) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    anc2[v] = anc[anc[v]];
+}
+
+// After >= log2(n)+1 doublings anc[v] lies >= n steps up: it must be a self-parent.
+__global__ void k_ver_cycle(int64_t n, const int32_t* __restrict__ parent, const int32_t* __restrict__ tr,
+                            int32_t* verdict) {
+  bool bad = false;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = tr[v];
+    if (parent[r] != r) bad = true;
+  }
+  if (bad) atomicMin(verdict, (int)RST_VERDICT_CYCLE);
+}
+
+template <class OffT>
+struct SpanFn {
+  const int32_t* __restrict__ col;
+  const int32_t* __restrict__ tr;
+  bool bad;
+  __device__ __forceinline__ void operator()(bool is_arc, int64_t row, int64_t arc) {
+    if (is_arc && tr[row] != tr[col[arc]]) bad = true;
+  }
+};
+
+template <class OffT>
+__global__ void __launch_bounds__(kMpThreads) k_ver_span(const OffT* __restrict__ off, int64_t n, int64_t A,
+                                                         const int32_t* __restrict__ col,
+                                                         const int32_t* __restrict__ tr, int32_t* verdict) {
+  SpanFn<OffT> f{col, tr, false};
+  csr_for_each_arc(off, n, A, f);
+  if (f.bad) atomicMin(verdict, (int)RST_VERDICT_NOT_SPANNING);
+}
+
+// Minimum vertex of each tree that does not contain root.
+__global__ void k_ver_minv(int64_t n, const int32_t* __restrict__ tr, int32_t root_tree,
+                           int32_t* __restrict__ mn) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = tr[v];
+    if (r != root_tree) atomicMin(&mn[r], (int32_t)v);
+  }
+}
+
+__global__ void k_ver_roots(int64_t n, const int32_t* __restrict__ parent, const int32_t* __restrict__ tr,
+                            int32_t root_tree, const int32_t* __restrict__ mn, int32_t* verdict) {
+  bool bad = false;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (parent[v] == (int32_t)v && tr[v] != root_tree && mn[v] != (int32_t)v) bad = true;
+  }
+  if (bad) atomicMin(verdict, (int)RST_VERDICT_COMPONENT_ROOT);
+}
+
+__global__ void k_fill_i32_v(int32_t* p, int64_t count, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+template <class OffT>
+static rst_status verify_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
+                              const int32_t* parent, int32_t* verdict_out, cudaStream_t s) {
+  if (root < 0 || root >= n) {
+    *verdict_out = RST_VERDICT_BAD_ROOT;
+    return RST_OK;
+  }
+  const size_t ws = 3 * (((size_t)n * 4 + 255) / 256 * 256 + 256);
+  RST_TRY(ensure_workspace(ws));
+  RST_TRY(reset_device_error(s));
+  DeviceState& st = state();
+  Arena ar{st.ws, st.ws_cap, 0, false};
+  int32_t* a0 = ar.take<int32_t>(n);
+  int32_t* a1 = ar.take<int32_t>(n);
+  int32_t* mn = ar.take<int32_t>(n);
+  int32_t* verdict = reinterpret_cast<int32_t*>(st.status + 4);
+  if (!a0 || !a1 || !mn) return RST_ERR_OOM;
+  const int g = grid_for(n);
+  auto fetch = [&](int32_t* out) -> rst_status {
+    RST_CUDA(cudaMemcpyAsync(st.hostbuf, verdict, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RST_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(out, st.hostbuf, sizeof(int32_t));
+    return RST_OK;
+  };
+  k_fill_i32_v<<<1, 32, 0, s>>>(verdict, 1, INT_MAX);
+  int32_t v = INT_MAX;
+  // phase 1-2
+  k_ver_range<<<g, kBlock, 0, s>>>(n, root, parent, verdict);
+  RST_CUDA(cudaGetLastError());
+  RST_TRY(fetch(&v));
+  if (v == INT_MAX) {
+    k_ver_edges<OffT><<<g, kBlock, 0, s>>>(off, col, n, parent, verdict);
+    RST_TRY(fetch(&v));
+  }
+  if (v == INT_MAX) {
+    RST_CUDA(cudaMemcpyAsync(a0, parent, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    int rounds = 1;
+    while (((int64_t)1 << rounds) <= n) ++rounds;
+    for (int r = 0; r <= rounds; ++r) {
+      k_ver_double<<<g, kBlock, 0, s>>>(n, a0, a1);
+      std::swap(a0, a1);
+    }
+    k_ver_cycle<<<g, kBlock, 0, s>>>(n, parent, a0, verdict);
+    RST_CUDA(cudaGetLastError());
+    RST_TRY(fetch(&v));
+  }
+  if (v == INT_MAX) {
+    const int64_t tiles = (n + A + kMpTile - 1) / kMpTile;
+    const int gt = (int)(tiles < (int64_t)device_info().sms * 8 ? (tiles > 0 ? tiles : 1)
+                                                                 : (int64_t)device_info().sms * 8);
+    k_ver_span<OffT><<<gt, kMpThreads, 0, s>>>(off, n, A, col, a0, verdict);
+    RST_CUDA(cudaGetLastError());
+    RST_TRY(fetch(&v));
+  }
+  if (v == INT_MAX) {
+    int32_t root_tree = 0;
+    RST_CUDA(cudaMemcpyAsync(st.hostbuf, a0 + root, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RST_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(&root_tree, st.hostbuf, sizeof(int32_t));
+    k_fill_i32_v<<<g, kBlock, 0, s>>>(mn, n, INT_MAX);
+    k_ver_minv<<<g, kBlock, 0, s>>>(n, a0, root_tree, mn);
+    k_ver_roots<<<g, kBlock, 0, s>>>(n, parent, a0, root_tree, mn, verdict);
+    RST_CUDA(cudaGetLastError());
+    RST_TRY(fetch(&v));
+  }
+  *verdict_out = v == INT_MAX ? RST_VERDICT_VALID : v;
+  return read_device_error(s);
+}
+
+rst_status run_verify(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                      int32_t root, const int32_t* parent, int32_t* verdict_out, cudaStream_t s) {
+  if (offsets_bits == 32)
+    return verify_impl<int32_t>((const int32_t*)off, cols, n, m, root, parent, verdict_out, s);
+  return verify_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, verdict_out, s);
+}
+
+}  // namespace rst

@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact comparisons (integer work): parent arrays of CC+Euler and BFS,
+component labels, the tree edge SET (the list order is unspecified), Euler
+ranks indexed by lexicographic arc order, and verifier verdict codes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_11645_gb300 import graphs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(g):
+    d = torch.device("cuda:0")
+    return torch.from_numpy(g.offsets).to(d), torch.from_numpy(g.cols).to(d)
+
+
+def small_graphs():
+    out = []
+    for (W, H, seed) in [(16, 16, 1), (33, 7, 2), (1, 50, 3), (50, 1, 4), (129, 65, 5)]:
+        out.append(graphs.grid(W, H, seed=seed, permute=True, root="random"))
+    out.append(graphs.grid(40, 30, permute=False, root=0))
+    for n, d, s in [(2000, 0.0, 1), (5000, 0.001, 2), (3000, 0.05, 3), (777, 0.5, 4)]:
+        out.append(graphs.chain_chords(n, d, seed=s))
+    out.append(graphs.erdos_renyi(3000, 2000, seed=7))
+    out.append(graphs.erdos_renyi(5000, 12000, seed=8))
+    out.append(graphs.rmat(12, 8, seed=9, connect=False, offsets_bits=64))
+    out.append(graphs.rmat(14, 16, seed=10, connect=True, offsets_bits=64))
+    out.append(graphs.rmat(11, 16, seed=11, connect=True, offsets_bits=32))
+    out.append(graphs.random_4regular(4001, seed=12))
+    return out
+
+
+SMALL = None
+N_SMALL = 16
+
+
+def _small():
+    global SMALL
+    if SMALL is None:
+        SMALL = small_graphs()
+    return SMALL
+
+
+def edge_cases():
+    cases = []
+    cases.append(graphs.from_edges(1, [], [], name="single", root=0))
+    cases.append(graphs.from_edges(2, [0], [1], name="one-edge", root=1))
+    cases.append(graphs.from_edges(5, [], [], name="no-edges", root=3))
+    cases.append(graphs.from_edges(6, [0, 1, 3], [1, 2, 4], name="root-isolated", root=5))
+    cases.append(graphs.from_edges(7, [0, 2, 4, 5], [1, 3, 5, 6], name="root-small-comp", root=3))
+    cases.append(graphs.from_edges(6, [0, 1, 2, 3, 4], [1, 2, 3, 4, 5], name="path-root-mid", root=2))
+    g = graphs.from_edges(5, [0, 0, 0, 0], [1, 2, 3, 4], name="star64", root=4, offsets_bits=64)
+    cases.append(g)
+    return cases
+
+
+def _ids(gs):
+    return [g.name for g in gs]
+
+
+@pytest.mark.parametrize("gi", range(N_SMALL))
+def test_cc_euler_parent_small(gi):
+    g = _small()[gi]
+    off, col = dev(g)
+    import paper_2603_11645_gb300 as rst
+    par = rst.build(off, col, g.root, "cc_euler").cpu().numpy()
+    want = oracle.rst(g.n, g.offsets, g.cols, g.root)
+    assert np.array_equal(par, want), g.name
+
+
+@pytest.mark.parametrize("g", edge_cases(), ids=_ids(edge_cases()))
+def test_cc_euler_edge_cases(g):
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    par = rst.build(off, col, g.root, "cc_euler").cpu().numpy()
+    assert np.array_equal(par, oracle.rst(g.n, g.offsets, g.cols, g.root))
+    labels, uv, T = rst.cc(off, col)
+    lab, tu, tv = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+    assert np.array_equal(labels.cpu().numpy(), lab)
+    assert T == len(tu)
+
+
+@pytest.mark.parametrize("gi", range(N_SMALL))
+def test_cc_labels_and_tree_set(gi):
+    g = _small()[gi]
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    labels, uv, T = rst.cc(off, col)
+    lab, tu, tv = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+    assert np.array_equal(labels.cpu().numpy(), lab)
+    assert T == len(tu)
+    got = uv.cpu().numpy()
+    got = got[np.lexsort((got[:, 1], got[:, 0]))]
+    assert np.array_equal(got[:, 0], tu) and np.array_equal(got[:, 1], tv)
+
+
+@pytest.mark.parametrize("gi", range(N_SMALL))
+def test_euler_root_ranks(gi):
+    g = _small()[gi]
+    import paper_2603_11645_gb300 as rst
+    lab, tu, tv = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+    # feed the tree edges in a scrambled order and orientation
+    rng = np.random.default_rng(gi)
+    perm = rng.permutation(len(tu))
+    flip = rng.random(len(tu)) < 0.5
+    a = np.where(flip, tv, tu)[perm]
+    b = np.where(flip, tu, tv)[perm]
+    uv = torch.from_numpy(np.stack([a, b], 1).astype(np.int32)).cuda()
+    par, rank = rst.euler_root(g.n, uv, g.root)
+    s, d, r, p = oracle.euler_tour(g.n, tu, tv, g.root)
+    assert np.array_equal(par.cpu().numpy(), p)
+    assert np.array_equal(rank.cpu().numpy(), r)
+
+
+@pytest.mark.parametrize("gi", range(N_SMALL))
+def test_bfs_parent_small(gi):
+    g = _small()[gi]
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    par = rst.build(off, col, g.root, "bfs").cpu().numpy()
+    lev, want = oracle.bfs(g.n, g.offsets, g.cols, g.root)
+    assert np.array_equal(par, want), g.name
+
+
+@pytest.mark.parametrize("g", edge_cases(), ids=_ids(edge_cases()))
+def test_bfs_edge_cases(g):
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    par = rst.build(off, col, g.root, "bfs").cpu().numpy()
+    assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+
+
+@pytest.mark.parametrize("gi", [0, 3, 6, 8, 10, 12, 15])
+def test_verify_matches_oracle(gi):
+    g = _small()[gi]
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    par = oracle.rst(g.n, g.offsets, g.cols, g.root)
+    rng = np.random.default_rng(gi)
+    variants = [par.copy()]
+    nonroot = np.flatnonzero(par != np.arange(g.n))
+    for k in range(12):
+        p = par.copy()
+        v = int(rng.choice(nonroot)) if len(nonroot) else 0
+        kind = k % 6
+        if kind == 0:
+            p[g.root] = (g.root + 1) % g.n
+        elif kind == 1:
+            p[v] = g.n + 5
+        elif kind == 2:
+            p[v] = int(rng.integers(0, g.n))
+        elif kind == 3 and p[v] != g.root:
+            p[p[v]] = v
+        elif kind == 4:
+            p[v] = v
+        elif kind == 5:
+            p = rng.integers(0, g.n, g.n).astype(np.int32)
+        variants.append(p)
+    for p in variants:
+        want = oracle.verify(g.n, g.offsets, g.cols, g.root, p)
+        got = rst.verify(off, col, g.root, torch.from_numpy(p.astype(np.int32)).cuda())
+        assert got == want
+
+
+# ------------------------------------------------------------------ named workloads
+
+@pytest.fixture(scope="module")
+def grid256():
+    return graphs.workload_grid256()
+
+
+def test_grid256_all_outputs(grid256):
+    g = grid256
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    want = oracle.rst(g.n, g.offsets, g.cols, g.root)
+    assert np.array_equal(rst.build(off, col, g.root, "cc_euler").cpu().numpy(), want)
+    lab, tu, tv = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+    uv = torch.from_numpy(np.stack([tu, tv], 1).astype(np.int32)).cuda()
+    par, rank = rst.euler_root(g.n, uv, g.root)
+    s, d, r, p = oracle.euler_tour(g.n, tu, tv, g.root)
+    assert np.array_equal(rank.cpu().numpy(), r)
+    assert np.array_equal(rst.build(off, col, g.root, "bfs").cpu().numpy(),
+                          oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+    assert rst.verify(off, col, g.root, torch.from_numpy(want).cuda()) == 0
+
+
+@pytest.fixture(scope="module")
+def grid4096():
+    return graphs.workload_grid4096()
+
+
+def test_grid4096_cc_euler_and_bfs(grid4096):
+    """Full-size high-diameter workload in the configuration the benchmark times."""
+    g = grid4096
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    want = oracle.rst(g.n, g.offsets, g.cols, g.root)
+    got = rst.build(off, col, g.root, "cc_euler")
+    assert np.array_equal(got.cpu().numpy(), want)
+    assert rst.verify(off, col, g.root, got) == 0
+    bpar = rst.build(off, col, g.root, "bfs").cpu().numpy()
+    assert np.array_equal(bpar, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+
+
+@pytest.fixture(scope="module")
+def rmat24():
+    return graphs.workload_rmat24()
+
+
+@pytest.mark.slow
+def test_rmat24_cc_euler(rmat24):
+    g = rmat24
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    want = oracle.rst(g.n, g.offsets, g.cols, g.root)
+    got = rst.build(off, col, g.root, "cc_euler")
+    assert np.array_equal(got.cpu().numpy(), want)
+    bpar = rst.build(off, col, g.root, "bfs").cpu().numpy()
+    assert np.array_equal(bpar, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
