@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: rooted-spanning-tree build throughput on one GB300 (edges/s = m/time).
+
+Headline: CC+Euler (hook/compress connectivity + Euler-tour rooting) on the
+high-diameter workload, a 4096 x 4096 4-neighbour grid with seed-permuted ids
+and a seeded random root (16,777,216 vertices, 33,546,240 undirected edges,
+int32 CSR).  One step = one rst_build(RST_CC_EULER) over the resident graph.
+Beside it: the library's own level-synchronous GPU BFS on the same graph, the
+per-kernel roofline of the dominant kernel, the end-to-end number through the
+C ABI with host buffers, and the CPU oracle timed on the host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank builds the same graph on its own GPU: the
+single-graph path does not shard, so ranks are replicas ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RST build edges/s (m/time) per graph family vs own GPU BFS; selector regret %"
+WORKLOAD = ("grid 4096x4096 4-neighbour, ids permuted by seed 2, seeded random root, "
+            "int32 CSR (16,777,216 vertices, 33,546,240 undirected edges)")
+L2_BYTES = 129 * 1024 * 1024
+
+
+# ----------------------------------------------------------------- helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_bytes(name, n, A, st, o):
+    """Algorithmic bytes per launch: every element a kernel must read or write,
+    counted once (random accesses are not charged their sector size)."""
+    T = st["T"]
+    N = 2 * T
+    c1, E2 = st["c1"], st["E2"]
+    models = {
+        "k_r1_choose": (n + 1) * o + 4 * n + 8 * n,
+        "k_r1_resolve": 16 * n + (n - c1) * (2 * o + 4 + 16) + 4 * n,
+        "k_r1_number": 8 * n + 8 * c1,
+        "k_r1_label": 16 * n,
+        "k_build_list": (n + 1) * o + 4 * A + 4 * n + 2 * A + 12 * E2,
+        "k_toff": (n + 1) * (o + 8 + 4) + n,
+        "k_pairs_succ": T * (16 + 16 + 16 + 16 + 8),
+        "k_lr_walk1": 16 * N + 12 * ((N + 15) // 16),
+        "k_lr_final1": 8 * N + 4 * N + 4 * ((N + 15) // 16),
+        "k_parent_from_rank": 16 * T + 8 * T + 4 * T,
+    }
+    return models.get(name)
+
+
+def traffic_for(kernel):
+    """Per-launch DRAM bytes from the committed ncu capture, or None when the
+    kernel's source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e:
+        return None
+    h = hashlib.sha256()
+    for rel in e["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != e["sha256"]:
+        return None
+    return e["bytes_per_launch"]
+
+
+# ----------------------------------------------------------------- oracle (CPU baseline)
+
+def oracle_edges_per_s(g, reps=1):
+    import oracle
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        lab, tu, tv = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+        oracle.euler_tour(g.n, tu, tv, g.root)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return g.m / t, t
+
+
+# ----------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2603_11645_gb300 as rst
+    from paper_2603_11645_gb300 import graphs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    L = rst.lib()
+    L.rst_launch_count.restype = ctypes.c_longlong
+    L.rst_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.rst_last_stats.argtypes = [ctypes.c_void_p, ctypes.c_int]
+
+    g = graphs.workload_grid4096()
+    off = torch.from_numpy(g.offsets).to(dev)
+    col = torch.from_numpy(g.cols).to(dev)
+    par = torch.empty(g.n, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(strategy="cc_euler"):
+        rst.build(off, col, g.root, strategy, out=par)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    L.rst_profile_enable(1)
+    launches0 = L.rst_launch_count()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)                       # L2 flush outside the timed window
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    launches = L.rst_launch_count() - launches0
+    ms = (ctypes.c_float * 4096)()
+    names = (ctypes.c_char_p * 4096)()
+    k = L.rst_profile_read(ms, names, 4096)
+    L.rst_profile_enable(0)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * g.m * args.steps / (total_ms / 1e3)
+
+    # stage times: the dominant kernel of the timed region
+    stages = {}
+    for i in range(k):
+        nm = names[i].decode()
+        stages.setdefault(nm, []).append(ms[i])
+    kern = {nm: v for nm, v in stages.items() if nm.startswith("k_")}
+    dom = max(kern, key=lambda nm: sum(kern[nm])) if kern else None
+    stats = (ctypes.c_longlong * 8)()
+    L.rst_last_stats(stats, 8)
+    st = {"rounds": stats[0], "c1": stats[1], "E2": stats[2], "T": stats[3], "nroots": stats[4],
+          "lr_levels": stats[5]}
+    peak, peak_src = measured_peaks()
+    roofline = None
+    if dom:
+        per_launch_ms = sum(kern[dom]) / len(kern[dom])
+        byts = kernel_bytes(dom, g.n, g.A, st, 4)
+        if byts:
+            achieved = byts / (per_launch_ms / 1e3) / 1e9
+            roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "traffic": traffic_for(dom),
+                        "kernel": dom, "algorithmic_bytes": int(byts),
+                        "launch_ms": round(per_launch_ms, 4), "peak_source": peak_src,
+                        "share_of_step": round(sum(kern[dom]) / total_ms, 3) if world == 1 else None}
+    stage_summary = {nm: round(sum(v) / args.steps, 4) for nm, v in
+                     sorted(stages.items(), key=lambda kv: -sum(kv[1]))}
+
+    # end to end through the C ABI from pinned host buffers
+    off_h = torch.from_numpy(g.offsets).pin_memory()
+    col_h = torch.from_numpy(g.cols).pin_memory()
+    par_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    off_d = torch.empty_like(off)
+    col_d = torch.empty_like(col)
+    e2e_steps = max(1, min(args.steps, 5))
+    e2e_ms = []
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        off_d.copy_(off_h, non_blocking=True)
+        col_d.copy_(col_h, non_blocking=True)
+        rst.build(off_d, col_d, g.root, "cc_euler", out=par)
+        par_h.copy_(par, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * g.m * e2e_steps / (e2e_total / 1e3)
+
+    # the library's own GPU BFS on the same graph (the step-bound baseline)
+    bfs_ms = []
+    step("bfs")
+    for _ in range(args.bfs_steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step("bfs")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        bfs_ms.append(e0.elapsed_time(e1))
+    L.rst_last_stats(stats, 8)
+    bfs_levels = stats[5]
+    bfs_med = statistics.median(bfs_ms)
+    ms_step = total_ms / args.steps
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            v, t = oracle_edges_per_s(g, 1)
+            cpu = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one run of the sequential oracle (Kruskal over (min,max) keys + "
+                             f"sequential Euler tour) on the full 4096x4096 workload, {t:.1f} s"}
+        out = {
+            "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "strategy": "cc_euler",
+                       "l2": "L2 flushed (258 MB write) before every timed step; inputs also exceed L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": "edges/s",
+                    "h2d_bytes_per_step": int(g.offsets.nbytes + g.cols.nbytes),
+                    "d2h_bytes_per_step": int(4 * g.n)},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "bfs": {"value": g.m / (bfs_med / 1e3), "unit": "edges/s", "ms_per_step": bfs_med,
+                    "levels": int(bfs_levels),
+                    "cc_euler_speedup": bfs_med / ms_step},
+            "stats": st,
+            "stage_ms": stage_summary,
+        }
+    return out
+
+
+# ----------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2603_11645_gb300 import graphs
+    import oracle
+    # bounded sample of the workload: the same family at 2048 x 2048 (seed 2)
+    g = graphs.grid(2048, 2048, seed=2, permute=True, root="random")
+    for _ in range(args.warmup):
+        oracle_edges_per_s(g, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        lab, tu, tv = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+        oracle.euler_tour(g.n, tu, tv, g.root)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = g.m * args.steps / total
+    sample = ("sequential CPU oracle (Kruskal + Euler tour) per step on a 2048x2048 grid of the "
+              "same family (4,194,304 vertices, 8,384,512 edges)")
+    return {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "strategy": "cc_euler (oracle)"},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--bfs-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -147,6 +147,22 @@ rst_status rst_verify(const void *csr_offsets, int offsets_bits, const int32_t *
                       int64_t n, int64_t m, int32_t root, const int32_t *parent,
                       int32_t *verdict_out, rst_stream_t stream);
 
+/* ---- diagnostics (no counterpart in the paper) ----------------------------
+ * rst_launch_count: number of kernels this library has launched since load.
+ * rst_profile_enable(1) starts recording a CUDA event at each stage boundary
+ * of subsequent calls (on the call's stream); rst_profile_read writes up to
+ * max_stages stage durations in milliseconds and their static names (host
+ * arrays, may be NULL), returns the count and clears the record.
+ * rst_profile_enable(0) stops recording. */
+long long rst_launch_count(void);
+/* Sizes seen by the last call (host array): hooking rounds, components with
+ * edges after round 1, inter-component edges after round 1, tree edges,
+ * components with edges, BFS levels or list-ranking levels.  Returns the
+ * number of values written (at most max). */
+int rst_last_stats(long long *out, int max);
+void rst_profile_enable(int on);
+int rst_profile_read(float *ms_out, const char **names_out, int max_stages);
+
 /* Release the internal workspace of every device the library touched. */
 rst_status rst_shutdown(void);
 

@@ -39,11 +39,14 @@ rst_status build_cc_euler(const OffT* off, const int32_t* cols, int64_t n, int64
                           int32_t* parent, uint32_t* rank_out, cudaStream_t s) {
   const size_t ws = cc_workspace_bytes<OffT>(n, m) + euler_cc_workspace_bytes(n, m, n, n / 2 + 1);
   Arena ar;
+  prof_mark(s, "start");
   RST_TRY(begin(ws, s, &ar));
   CcOut cc;
   RST_TRY(cc_run<OffT>(ar, off, cols, n, m, root, nullptr, &cc, s));
   RST_TRY(euler_root_cc<OffT>(ar, off, n, m, root, &cc, parent, rank_out, s));
-  return read_device_error(s);
+  rst_status st = read_device_error(s);
+  prof_mark(s, "end");
+  return st;
 }
 
 __global__ void k_pairs_to_uv(int64_t T, const uint4* __restrict__ pairs, int32_t* __restrict__ uv) {
@@ -65,7 +68,7 @@ rst_status cc_only(const OffT* off, const int32_t* cols, int64_t n, int64_t m, i
   CcOut cc;
   RST_TRY(cc_run<OffT>(ar, off, cols, n, m, -1, labels, &cc, s));
   if (tree_uv && cc.T > 0) {
-    k_pairs_to_uv<<<grid_for(cc.T), kBlock, 0, s>>>(cc.T, cc.pairs, tree_uv);
+    RST_LAUNCH(k_pairs_to_uv, grid_for(cc.T), kBlock, 0, s)(cc.T, cc.pairs, tree_uv);
     RST_CUDA(cudaGetLastError());
   }
   if (num_tree) *num_tree = cc.T;

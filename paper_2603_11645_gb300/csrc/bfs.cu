@@ -106,7 +106,8 @@ struct TdEdgeFn {
   int32_t* __restrict__ parent;
   int32_t* __restrict__ q2;
   unsigned long long* counter;
-  __device__ __forceinline__ void operator()(bool is_arc, int64_t row, int64_t arc) {
+  __device__ __forceinline__ void end_tile() {}
+  __device__ __forceinline__ void operator()(int, bool is_arc, int64_t row, int64_t arc) {
     bool fresh = false;
     int32_t v = 0;
     if (is_arc) {
@@ -156,7 +157,7 @@ __global__ void k_bfs_bu(const OffT* __restrict__ off, const int32_t* __restrict
         }
       }
     }
-    const long long slot = warp_reserve(&counters[BC_NEXT], fresh);
+    const unsigned long long slot = block_reserve<kBlock>(&counters[BC_NEXT], fresh ? 1u : 0u);
     if (fresh) q2[slot] = (int32_t)v;
   }
 }
@@ -203,7 +204,7 @@ static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64
   unsigned long long* cnt = dev_counter(0);
   RST_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
   const int gN = grid_for(n);
-  k_bfs_init<OffT><<<gN, kBlock, 0, s>>>(off, n, level, parent, cnt);
+  RST_LAUNCH(k_bfs_init<OffT>, gN, kBlock, 0, s)(off, n, level, parent, cnt);
   unsigned long long h[8];
   RST_TRY(fetch_u64(cnt, 8, h, s));
   const int64_t maxdeg = (int64_t)h[BC_MAXDEG];
@@ -216,7 +217,7 @@ static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64
     RST_CUDA(cudaStreamSynchronize(s));
     std::memcpy(&probe_level, st.hostbuf, sizeof(int32_t));
     if (probe_level == -1) {
-      k_bfs_seed<<<1, 1, 0, s>>>(src, level, parent, qa);
+      RST_LAUNCH(k_bfs_seed, 1, 1, 0, s)(src, level, parent, qa);
       int64_t nf = 1;
       int32_t L = 0;
       bool bottom_up = false;
@@ -226,11 +227,11 @@ static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64
         RST_CUDA(cudaMemsetAsync(&cnt[BC_NEXT], 0, sizeof(unsigned long long), s));
         const bool want_bu = nf > n / 20;
         if (want_bu) {
-          k_bfs_bu<OffT><<<gN, kBlock, 0, s>>>(off, col, n, L, level, parent, q2, cnt);
+          RST_LAUNCH(k_bfs_bu<OffT>, gN, kBlock, 0, s)(off, col, n, L, level, parent, q2, cnt);
         } else if (thread_td) {
-          k_bfs_td_thread<OffT><<<grid_for(nf), kBlock, 0, s>>>(off, col, q, nf, L, level, parent, q2, cnt);
+          RST_LAUNCH(k_bfs_td_thread<OffT>, grid_for(nf), kBlock, 0, s)(off, col, q, nf, L, level, parent, q2, cnt);
         } else {
-          k_bfs_fdeg<OffT><<<grid_for(nf), kBlock, 0, s>>>(off, q, nf, fo);
+          RST_LAUNCH(k_bfs_fdeg<OffT>, grid_for(nf), kBlock, 0, s)(off, q, nf, fo);
           RST_TRY(scan_exclusive_u64(fo, fo, nf, tmp, s));
           RST_CUDA(cudaMemcpyAsync(&cnt[BC_FEDGES], fo + nf, sizeof(unsigned long long),
                                    cudaMemcpyDeviceToDevice, s));
@@ -240,12 +241,12 @@ static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64
           const int64_t tiles = (nf + fe + kMpTile - 1) / kMpTile;
           const int g = (int)(tiles < (int64_t)device_info().sms * 8 ? (tiles > 0 ? tiles : 1)
                                                                       : (int64_t)device_info().sms * 8);
-          k_bfs_td_edges<OffT><<<g, kMpThreads, 0, s>>>(nf, fe, f);
+          RST_LAUNCH(k_bfs_td_edges<OffT>, g, kMpThreads, 0, s)(nf, fe, f);
         }
         RST_CUDA(cudaGetLastError());
         RST_TRY(fetch_u64(&cnt[BC_NEXT], 1, h, s));
         const int64_t nn = (int64_t)h[0];
-        if (want_bu && nn > 0) k_bfs_commit<<<grid_for(nn), kBlock, 0, s>>>(q2, nn, L, level);
+        if (want_bu && nn > 0) RST_LAUNCH(k_bfs_commit, grid_for(nn), kBlock, 0, s)(q2, nn, L, level);
         bottom_up = want_bu;
         std::swap(q, q2);
         nf = nn;
@@ -257,7 +258,7 @@ static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64
     }
     // next component: minimum unvisited vertex
     RST_CUDA(cudaMemsetAsync(&cnt[BC_MINUNV], 0xff, sizeof(unsigned long long), s));
-    k_bfs_min_unvisited<<<gN, kBlock, 0, s>>>(n, level, cnt);
+    RST_LAUNCH(k_bfs_min_unvisited, gN, kBlock, 0, s)(n, level, cnt);
     RST_CUDA(cudaGetLastError());
     RST_TRY(fetch_u64(&cnt[BC_MINUNV], 1, h, s));
     src = h[0] == ~0ull ? -1 : (int32_t)h[0];

@@ -165,7 +165,7 @@ __global__ void k_r1_resolve(const OffT* __restrict__ off, const int32_t* __rest
         }
       }
     }
-    long long slot = warp_reserve(&counters[CNT_PAIRS], emit);
+    const unsigned long long slot = block_reserve<kBlock>(&counters[CNT_PAIRS], emit ? 1u : 0u);
     if (emit) pairs[slot] = rec;
   }
 }
@@ -181,7 +181,7 @@ __global__ void k_r1_number(int64_t n, const int32_t* __restrict__ P,
     const int64_t v = base + threadIdx.x;
     bool is_root = false;
     if (v < n) is_root = (P[v] == (int32_t)v) && (J[v] != kNone);
-    long long id = warp_reserve(&counters[CNT_COMPS], is_root);
+    const unsigned long long id = block_reserve<kBlock>(&counters[CNT_COMPS], is_root ? 1u : 0u);
     if (is_root) {
       CID[v] = (int32_t)id;
       minv[id] = (int32_t)v;
@@ -210,27 +210,39 @@ struct BuildListFn {
   unsigned long long* counter;
   int64_t cap;
   uint32_t* status;
-  __device__ __forceinline__ void operator()(bool is_arc, int64_t row, int64_t arc) {
-    bool keep = false;
-    int32_t cu = 0, cv = 0;
+  // per-thread staging of one tile's kept entries (registers after unrolling)
+  int32_t bu[kMpItems], bv[kMpItems];
+  uint32_t bp[kMpItems];
+  uint32_t mask;
+  __device__ __forceinline__ void operator()(int it, bool is_arc, int64_t row, int64_t arc) {
+    if (it == 0) mask = 0;
     if (is_arc) {
       const int32_t v = col[arc];
       if (v < 0 || (int64_t)v >= n) {
         raise_error(status, DERR_INDEX);
       } else if (v > (int32_t)row) {
-        cu = C1[row];
-        cv = C1[v];
-        keep = (cu != cv);
+        const int32_t cu = C1[row];
+        const int32_t cv = C1[v];
+        bu[it] = cu;
+        bv[it] = cv;
+        bp[it] = (uint32_t)arc;
+        if (cu != cv) mask |= 1u << it;
       }
     }
-    long long slot = warp_reserve(counter, keep);
-    if (keep) {
-      if (slot < cap) {
-        Ecu[slot] = cu;
-        Ecv[slot] = cv;
-        Ep[slot] = (uint32_t)arc;
-      } else {
-        raise_error(status, DERR_CAPACITY);
+  }
+  __device__ __forceinline__ void end_tile() {
+    unsigned long long slot = block_reserve<kMpThreads>(counter, (unsigned)__popc(mask));
+#pragma unroll
+    for (int it = 0; it < kMpItems; ++it) {
+      if (mask & (1u << it)) {
+        if ((int64_t)slot < cap) {
+          Ecu[slot] = bu[it];
+          Ecv[slot] = bv[it];
+          Ep[slot] = bp[it];
+        } else {
+          raise_error(status, DERR_CAPACITY);
+        }
+        ++slot;
       }
     }
   }
@@ -331,7 +343,7 @@ __global__ void k_resolve(const OffT* __restrict__ off, const int32_t* __restric
         }
       }
     }
-    long long slot = warp_reserve(&counters[CNT_PAIRS], emit);
+    const unsigned long long slot = block_reserve<kBlock>(&counters[CNT_PAIRS], emit ? 1u : 0u);
     if (emit) pairs[slot] = rec;
   }
 }
@@ -369,8 +381,8 @@ __global__ void k_renumber(int64_t C, const int32_t* __restrict__ P2,
       fin = best[c] == ~0ull;
       live_root = !fin && P2[c] == (int32_t)c;
     }
-    long long id = warp_reserve(&counters[CNT_NEXT], live_root);
-    long long rid = warp_reserve(&counters[CNT_ROOTS], fin);
+    const unsigned long long id = block_reserve<kBlock>(&counters[CNT_NEXT], live_root ? 1u : 0u);
+    const unsigned long long rid = block_reserve<kBlock>(&counters[CNT_ROOTS], fin ? 1u : 0u);
     if (c < C) NID[c] = live_root ? (int32_t)id : -1;
     if (fin) roots[rid] = minv[c];
   }
@@ -410,7 +422,7 @@ __global__ void k_relabel(int64_t E, const int32_t* __restrict__ Ecu, const int3
       p = Ep[e];
       keep = nu != nv;
     }
-    long long slot = warp_reserve(counter, keep);
+    const unsigned long long slot = block_reserve<kBlock>(counter, keep ? 1u : 0u);
     if (keep) {
       Ocu[slot] = nu;
       Ocv[slot] = nv;
@@ -426,7 +438,7 @@ __global__ void k_all_final(int64_t C, const int32_t* __restrict__ minv, int32_t
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < C; base += stride) {
     const int64_t c = base + threadIdx.x;
     const bool ok = c < C;
-    long long rid = warp_reserve(&counters[CNT_ROOTS], ok);
+    const unsigned long long rid = block_reserve<kBlock>(&counters[CNT_ROOTS], ok ? 1u : 0u);
     if (ok) {
       roots[rid] = minv[c];
       next[c] = kFinal;
@@ -492,22 +504,31 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   RST_CUDA(cudaMemsetAsync(b.bits, 0, (A / 32 + 2) * sizeof(uint32_t), s));
 
   const int gN = grid_for(n);
-  k_r1_choose<OffT><<<gN, kBlock, 0, s>>>(off, col, n, b.P, b.J, status);
-  k_r1_resolve<OffT><<<gN, kBlock, 0, s>>>(off, col, n, b.P, b.J, b.pairs, b.bits, cnt, status);
-  k_r1_number<<<gN, kBlock, 0, s>>>(n, b.P, b.J, b.CID, b.minvpool, cnt);
-  k_r1_label<<<gN, kBlock, 0, s>>>(n, b.P, b.J, b.CID, b.C1);
+  prof_mark(s, "cc_setup");
+  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, status);
+  prof_mark(s, "k_r1_choose");
+  RST_LAUNCH(k_r1_resolve<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.pairs, b.bits, cnt, status);
+  prof_mark(s, "k_r1_resolve");
+  RST_LAUNCH(k_r1_number, gN, kBlock, 0, s)(n, b.P, b.J, b.CID, b.minvpool, cnt);
+  prof_mark(s, "k_r1_number");
+  RST_LAUNCH(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.CID, b.C1);
+  prof_mark(s, "k_r1_label");
   {
     BuildListFn<OffT> f{col, b.C1, n, b.Ecu[0], b.Ecv[0], b.Ep[0], &cnt[CNT_LIST], b.ecap, status};
     const int64_t tiles = (n + A + kMpTile - 1) / kMpTile;
     const int g = (int)(tiles < (int64_t)device_info().sms * 8 ? (tiles > 0 ? tiles : 1)
                                                                 : (int64_t)device_info().sms * 8);
-    k_build_list<OffT><<<g, kMpThreads, 0, s>>>(off, n, A, f);
+    RST_LAUNCH(k_build_list<OffT>, g, kMpThreads, 0, s)(off, n, A, f);
   }
+  prof_mark(s, "k_build_list");
   RST_CUDA(cudaGetLastError());
   unsigned long long h[8];
   RST_TRY(fetch_u64(cnt, 8, h, s));
+  prof_mark(s, "cc_sync");
   int64_t C = (int64_t)h[CNT_COMPS];
   int64_t E = (int64_t)h[CNT_LIST];
+  set_stat(STAT_C1, C);
+  set_stat(STAT_E2, E);
   if (E > b.ecap) return RST_ERR_DEVICE;
 
   RoundTable rt{};
@@ -521,28 +542,28 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
     rt.base[rt.nrounds++] = pool_at;
     const int gC = grid_for(C);
     if (E == 0) {
-      k_all_final<<<gC, kBlock, 0, s>>>(C, minv, next, b.roots, cnt);
+      RST_LAUNCH(k_all_final, gC, kBlock, 0, s)(C, minv, next, b.roots, cnt);
       RST_CUDA(cudaGetLastError());
       pool_at += C;
       break;
     }
     ++rounds;
     const int gE = grid_for(E);
-    k_fill_u64<<<gC, kBlock, 0, s>>>(b.best, C, ~0ull);
-    k_hook<<<gE, kBlock, 0, s>>>(E, b.Ecu[cur], b.Ecv[cur], b.Ep[cur], b.best);
-    k_resolve<OffT><<<gC, kBlock, 0, s>>>(off, col, C, b.best, b.P2, b.pairs, b.bits, cnt, status);
-    k_compress<<<gC, kBlock, 0, s>>>(C, b.P2, status);
+    RST_LAUNCH(k_fill_u64, gC, kBlock, 0, s)(b.best, C, ~0ull);
+    RST_LAUNCH(k_hook, gE, kBlock, 0, s)(E, b.Ecu[cur], b.Ecv[cur], b.Ep[cur], b.best);
+    RST_LAUNCH(k_resolve<OffT>, gC, kBlock, 0, s)(off, col, C, b.best, b.P2, b.pairs, b.bits, cnt, status);
+    RST_LAUNCH(k_compress, gC, kBlock, 0, s)(C, b.P2, status);
     RST_CUDA(cudaMemsetAsync(&cnt[CNT_NEXT], 0, sizeof(unsigned long long), s));
-    k_renumber<<<gC, kBlock, 0, s>>>(C, b.P2, b.best, minv, b.NID, b.roots, cnt);
+    RST_LAUNCH(k_renumber, gC, kBlock, 0, s)(C, b.P2, b.best, minv, b.NID, b.roots, cnt);
     RST_CUDA(cudaGetLastError());
     RST_TRY(fetch_u64(cnt, 8, h, s));
     const int64_t Cn = (int64_t)h[CNT_NEXT];
     int32_t* minv_next = b.minvpool + pool_at + C;
     if (pool_at + C + Cn > n + 1) return RST_ERR_DEVICE;
-    k_fill_i32<<<grid_for(Cn), kBlock, 0, s>>>(minv_next, Cn, INT_MAX);
-    k_map<<<gC, kBlock, 0, s>>>(C, b.P2, b.best, b.NID, minv, next, minv_next);
+    RST_LAUNCH(k_fill_i32, grid_for(Cn), kBlock, 0, s)(minv_next, Cn, INT_MAX);
+    RST_LAUNCH(k_map, gC, kBlock, 0, s)(C, b.P2, b.best, b.NID, minv, next, minv_next);
     RST_CUDA(cudaMemsetAsync(&cnt[CNT_LIST], 0, sizeof(unsigned long long), s));
-    k_relabel<<<gE, kBlock, 0, s>>>(E, b.Ecu[cur], b.Ecv[cur], b.Ep[cur], next, b.Ecu[cur ^ 1],
+    RST_LAUNCH(k_relabel, gE, kBlock, 0, s)(E, b.Ecu[cur], b.Ecv[cur], b.Ep[cur], next, b.Ecu[cur ^ 1],
                                     b.Ecv[cur ^ 1], b.Ep[cur ^ 1], &cnt[CNT_LIST]);
     RST_CUDA(cudaGetLastError());
     RST_TRY(fetch_u64(cnt, 8, h, s));
@@ -552,15 +573,16 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
     cur ^= 1;
   }
 
+  prof_mark(s, "cc_rounds");
   // labels
   if (labels_out) {
     for (int r = rt.nrounds - 2; r >= 0; --r) {
       const int64_t Cr = rt.base[r + 1] - rt.base[r];
-      k_label_back<<<grid_for(Cr), kBlock, 0, s>>>(Cr, b.nextpool + rt.base[r],
+      RST_LAUNCH(k_label_back, grid_for(Cr), kBlock, 0, s)(Cr, b.nextpool + rt.base[r],
                                                    b.minvpool + rt.base[r],
                                                    b.minvpool + rt.base[r + 1]);
     }
-    k_label_vertices<<<gN, kBlock, 0, s>>>(n, b.C1, b.minvpool, labels_out);
+    RST_LAUNCH(k_label_vertices, gN, kBlock, 0, s)(n, b.C1, b.minvpool, labels_out);
     RST_CUDA(cudaGetLastError());
   }
   out->root_label = -1;
@@ -571,17 +593,21 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
                                cudaMemcpyDeviceToDevice, s));
       RST_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(&cnt[CNT_ROOTLABEL]) + 4, 0, 4, s));
     } else {
-      k_root_label<<<1, 32, 0, s>>>(root, b.C1, b.nextpool, b.minvpool, rt, cnt);
+      RST_LAUNCH(k_root_label, 1, 32, 0, s)(root, b.C1, b.nextpool, b.minvpool, rt, cnt);
       RST_CUDA(cudaGetLastError());
     }
   }
   RST_TRY(fetch_u64(cnt, 8, h, s));
+  prof_mark(s, "cc_finish");
   out->T = (int64_t)h[CNT_PAIRS];
   out->pairs = b.pairs;
   out->bits = b.bits;
   out->nroots = (int64_t)h[CNT_ROOTS];
   out->roots = b.roots;
   out->rounds = rounds;
+  set_stat(STAT_ROUNDS, rounds);
+  set_stat(STAT_T, out->T);
+  set_stat(STAT_NROOTS, out->nroots);
   if (root >= 0) out->root_label = (int32_t)(uint32_t)h[CNT_ROOTLABEL];
   return RST_OK;
 }

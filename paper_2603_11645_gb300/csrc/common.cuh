@@ -42,6 +42,26 @@ enum DeviceError : uint32_t {
 
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
+// ------------------------------------------------------------------ instrumentation
+// Every kernel launch goes through RST_LAUNCH so that the library can report
+// how many of its kernels ran (rst_launch_count).
+void count_launch();
+#define RST_LAUNCH(k, ...) ::rst::count_launch(), k<<<__VA_ARGS__>>>
+// Stage marks: when profiling is on, records a CUDA event on `s` that ends the
+// stage `name` (a string literal); rst_profile_read returns the durations.
+void prof_mark(cudaStream_t s, const char* name);
+// Sizes seen by the last call (read through rst_last_stats).
+enum StatSlot : int {
+  STAT_ROUNDS = 0,   // hooking rounds
+  STAT_C1 = 1,       // components after round 1 that still have edges
+  STAT_E2 = 2,       // inter-component edges after round 1
+  STAT_T = 3,        // tree edges
+  STAT_NROOTS = 4,   // components with edges
+  STAT_LEVELS = 5,   // BFS levels (BFS) / list-ranking levels (CC+Euler)
+  STAT_COUNT = 8
+};
+void set_stat(int slot, long long v);
+
 // ------------------------------------------------------------------ launch
 constexpr int kBlock = 256;
 
@@ -131,9 +151,39 @@ __device__ __forceinline__ long long warp_reserve(unsigned long long* counter, b
   return pred ? (long long)(base + __popc(m & ((1u << lane) - 1u))) : -1;
 }
 
-template <class T>
-__device__ __forceinline__ T ld_stream(const T* p) {
-  return __ldcs(p);
+// Block-aggregated reservation: every thread of the block calls it (with its
+// own count, possibly 0); one atomicAdd per block.  Returns the first slot of
+// this thread's range.  Contains __syncthreads(): call from block-uniform code.
+template <int BLOCK>
+__device__ __forceinline__ unsigned long long block_reserve(unsigned long long* counter,
+                                                           unsigned int cnt) {
+  constexpr int kWarps = BLOCK / 32;
+  __shared__ unsigned int s_warp[kWarps];
+  __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned int x = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned int w = lane < kWarps ? s_warp[lane] : 0u;
+    unsigned int ws = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, ws, d);
+      if (lane >= d) ws += y;
+    }
+    if (lane < kWarps) s_warp[lane] = ws - w;
+    if (lane == kWarps - 1) s_base = ws ? atomicAdd(counter, (unsigned long long)ws) : 0ull;
+  }
+  __syncthreads();
+  const unsigned long long r = s_base + s_warp[warp] + (x - cnt);
+  __syncthreads();
+  return r;
 }
 
 // ------------------------------------------------------------------ scan

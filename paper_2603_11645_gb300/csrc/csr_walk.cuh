@@ -31,10 +31,11 @@ __device__ __forceinline__ int64_t mp_search(const OffT* __restrict__ off, int64
   return lo;
 }
 
-// Calls f(is_arc, row, arc) kMpItems times per thread per tile.  Every thread
-// of the block makes the same number of calls (is_arc = false for row-end and
-// padding items), so f may use warp-collective operations.  Grid-stride over
-// tiles; blockDim.x must be kMpThreads.
+// Calls f(it, is_arc, row, arc) for it = 0..kMpItems-1 per thread per tile,
+// then f.end_tile().  Every thread of the block makes the same calls (is_arc =
+// false for row-end and padding items), so f may use warp- and block-
+// collective operations; `it` is a compile-time index after unrolling.
+// Grid-stride over tiles; blockDim.x must be kMpThreads.
 template <class OffT, class F>
 __device__ __forceinline__ void csr_for_each_arc(const OffT* __restrict__ off, int64_t n,
                                                  int64_t A, F& f) {
@@ -79,8 +80,9 @@ __device__ __forceinline__ void csr_for_each_arc(const OffT* __restrict__ off, i
           ++arc;
         }
       }
-      f(is_arc, my_row, my_arc);
+      f(it, is_arc, my_row, my_arc);
     }
+    f.end_tile();
     __syncthreads();
   }
 }

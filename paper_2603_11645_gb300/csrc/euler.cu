@@ -16,28 +16,13 @@
 
 namespace rst {
 
-// ----------------------------------------------------------------- shared core
-
-__global__ void k_succ(int64_t T, const uint4* __restrict__ pairs, const uint32_t* __restrict__ toff,
-                       const uint8_t* __restrict__ is_root, int32_t* __restrict__ succ) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 r = pairs[t];  // {i, k, a, b}: i = a->b, k = b->a
-    const uint32_t i = r.x, k = r.y;
-    const int32_t a = (int32_t)r.z, b = (int32_t)r.w;
-    // succ(i): rev(i) = k in b's run
-    const uint32_t lastb = toff[b + 1] - 1u;
-    succ[i] = (k != lastb) ? (int32_t)(k + 1u) : (is_root[b] ? -1 : (int32_t)toff[b]);
-    const uint32_t lasta = toff[a + 1] - 1u;
-    succ[k] = (i != lasta) ? (int32_t)(i + 1u) : (is_root[a] ? -1 : (int32_t)toff[a]);
-  }
-}
+// ----------------------------------------------------------------- core
 
 __global__ void k_parent_from_rank(int64_t T, const uint4* __restrict__ pairs,
                                    const uint32_t* __restrict__ R, int32_t* __restrict__ parent) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 r = pairs[t];
+    const uint4 r = pairs[t];  // {i, k, a, b}: i = a->b, k = b->a
     const uint32_t ri = R[r.x], rk = R[r.y];
     if (ri < rk)
       parent[r.w] = (int32_t)r.z;  // a->b traversed first: a is b's parent
@@ -46,29 +31,10 @@ __global__ void k_parent_from_rank(int64_t T, const uint4* __restrict__ pairs,
   }
 }
 
-size_t euler_workspace_bytes(int64_t n, int64_t T, int64_t nheads) {
-  (void)n;
-  (void)nheads;
+static size_t euler_core_bytes(int64_t T) {
   const int64_t N = 2 * T;
-  return 2 * (((size_t)N * 4 + 255) / 256 * 256 + 256) + list_rank_workspace_upper(N);
-}
-
-rst_status euler_from_pairs(Arena& ar, int64_t n, int64_t T, uint4* pairs, const uint32_t* toff,
-                            const uint8_t* is_root, const int32_t* heads, int64_t nheads,
-                            int32_t* parent_out, uint32_t* rank_out, cudaStream_t s) {
-  (void)n;
-  if (T <= 0) return RST_OK;
-  const int64_t N = 2 * T;
-  int32_t* succ = ar.take<int32_t>(N);
-  uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
-  if (!succ || !R) return RST_ERR_OOM;
-  const int gT = grid_for(T);
-  k_succ<<<gT, kBlock, 0, s>>>(T, pairs, toff, is_root, succ);
-  RST_CUDA(cudaGetLastError());
-  RST_TRY(list_rank(ar, N, succ, nullptr, heads, nheads, R, s));
-  k_parent_from_rank<<<gT, kBlock, 0, s>>>(T, pairs, R, parent_out);
-  RST_CUDA(cudaGetLastError());
-  return RST_OK;
+  return ((size_t)N * 8 + 255) / 256 * 256 + 256 + ((size_t)N * 4 + 255) / 256 * 256 + 256 +
+         list_rank_workspace_upper(N);
 }
 
 // ----------------------------------------------------------------- CSR-bitmap front end
@@ -108,15 +74,26 @@ __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32
   }
 }
 
-// {p, q, a, b} (CSR positions) -> {i, k, a, b} (tree positions), in place.
-__global__ void k_pairs_to_tree(int64_t T, uint4* __restrict__ pairs, const uint32_t* __restrict__ bits,
-                                const uint32_t* __restrict__ wpre) {
+// {p, q, a, b} (CSR positions) -> {i, k, a, b} (tree positions), in place,
+// and the Euler successors of both arcs: succ(i) follows rev(i) = k in b's
+// run (wrapping to first[b]), succ(k) follows i in a's run; the arc that
+// wraps into a tree root's first arc is cut (succ = -1).
+__global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint32_t* __restrict__ bits,
+                             const uint32_t* __restrict__ wpre, const uint32_t* __restrict__ toff,
+                             const uint8_t* __restrict__ is_root, int32_t* __restrict__ succ) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
     uint4 r = pairs[t];
-    r.x = bit_rank(bits, wpre, r.x);
-    r.y = bit_rank(bits, wpre, r.y);
+    const uint32_t i = bit_rank(bits, wpre, r.x);
+    const uint32_t k = bit_rank(bits, wpre, r.y);
+    const int32_t a = (int32_t)r.z, b = (int32_t)r.w;
+    r.x = i;
+    r.y = k;
     pairs[t] = r;
+    const uint32_t lastb = toff[b + 1] - 1u;
+    succ[i] = (k != lastb) ? (int32_t)(k + 1u) : (is_root[b] ? -1 : (int32_t)toff[b]);
+    const uint32_t lasta = toff[a + 1] - 1u;
+    succ[k] = (i != lasta) ? (int32_t)(i + 1u) : (is_root[a] ? -1 : (int32_t)toff[a]);
   }
 }
 
@@ -125,7 +102,7 @@ size_t euler_cc_workspace_bytes(int64_t n, int64_t A, int64_t T, int64_t nroots)
   auto al = [](size_t b) { return (b + 255) / 256 * 256 + 256; };
   size_t b = al((W + 1) * 4) + al(scan_tmp_words(W) * 8) + al(n) + al((n + 1) * 4) +
              al(nroots * 4 + 4);
-  return b + euler_workspace_bytes(n, T, nroots);
+  return b + euler_core_bytes(T);
 }
 
 template <class OffT>
@@ -139,19 +116,33 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   int32_t* heads = ar.take<int32_t>(cc->nroots + 1);
   if (!wpre || !tmp || !is_root || !toff || !heads) return RST_ERR_OOM;
   RST_TRY(scan_popcount_words(cc->bits, wpre, W, tmp, s));
+  prof_mark(s, "eu_bitscan");
   RST_CUDA(cudaMemsetAsync(is_root, 0, n, s));
   if (cc->nroots > 0)
-    k_mark_roots<<<grid_for(cc->nroots), kBlock, 0, s>>>(cc->nroots, cc->roots, cc->root_label,
+    RST_LAUNCH(k_mark_roots, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label,
                                                          root, is_root);
-  k_toff<OffT><<<grid_for(n + 1), kBlock, 0, s>>>(off, n, cc->bits, wpre, is_root, toff, parent_out);
+  prof_mark(s, "eu_roots");
+  RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, cc->bits, wpre, is_root, toff, parent_out);
+  prof_mark(s, "k_toff");
   if (cc->nroots > 0)
-    k_heads<<<grid_for(cc->nroots), kBlock, 0, s>>>(cc->nroots, cc->roots, cc->root_label, root,
+    RST_LAUNCH(k_heads, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label, root,
                                                     toff, heads);
-  if (cc->T > 0)
-    k_pairs_to_tree<<<grid_for(cc->T), kBlock, 0, s>>>(cc->T, cc->pairs, cc->bits, wpre);
   RST_CUDA(cudaGetLastError());
-  return euler_from_pairs(ar, n, cc->T, cc->pairs, toff, is_root, heads, cc->nroots, parent_out,
-                          rank_out, s);
+  const int64_t T = cc->T;
+  if (T <= 0) return RST_OK;
+  const int64_t N = 2 * T;
+  int32_t* succ = ar.take<int32_t>(N);
+  uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
+  if (!succ || !R) return RST_ERR_OOM;
+  const int gT = grid_for(T);
+  RST_LAUNCH(k_pairs_succ, gT, kBlock, 0, s)(T, cc->pairs, cc->bits, wpre, toff, is_root, succ);
+  prof_mark(s, "k_pairs_succ");
+  RST_CUDA(cudaGetLastError());
+  RST_TRY(list_rank(ar, N, succ, nullptr, heads, cc->nroots, R, s));
+  RST_LAUNCH(k_parent_from_rank, gT, kBlock, 0, s)(T, cc->pairs, R, parent_out);
+  prof_mark(s, "k_parent_from_rank");
+  RST_CUDA(cudaGetLastError());
+  return RST_OK;
 }
 
 template rst_status euler_root_cc<int32_t>(Arena&, const int32_t*, int64_t, int64_t, int32_t, CcOut*,
@@ -217,13 +208,13 @@ rst_status euler_root_edges(Arena& ar, int64_t n, const int32_t* tree_uv, int64_
   if (!keys || !off || !tmp || !cols) return RST_ERR_OOM;
   uint32_t* status = state().status;
   if (T > 0) {
-    k_arc_keys<<<grid_for(T), kBlock, 0, s>>>(T, tree_uv, n, nb, keys, status);
+    RST_LAUNCH(k_arc_keys, grid_for(T), kBlock, 0, s)(T, tree_uv, n, nb, keys, status);
     RST_TRY(radix_sort_keys(ar, keys, N, 2 * nb, s));
   }
   RST_CUDA(cudaMemsetAsync(off, 0, (n + 1) * sizeof(unsigned long long), s));
   if (T > 0) {
-    k_count_src<<<grid_for(N), kBlock, 0, s>>>(N, keys, nb, off);
-    k_key_dst<<<grid_for(N), kBlock, 0, s>>>(N, keys, nb, cols);
+    RST_LAUNCH(k_count_src, grid_for(N), kBlock, 0, s)(N, keys, nb, off);
+    RST_LAUNCH(k_key_dst, grid_for(N), kBlock, 0, s)(N, keys, nb, cols);
   }
   RST_TRY(scan_exclusive_u64(off, off, n, tmp, s));
   RST_CUDA(cudaGetLastError());

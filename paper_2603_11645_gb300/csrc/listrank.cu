@@ -1,19 +1,21 @@
-// Parallel list ranking (Section III-D: "parallel list ranking assigns each
-// edge its position within its respective Euler tour").
+// Parallel list ranking (Section III-D: every arc gets its position in its
+// tree's Euler tour, each tree ranked independently).
 //
-// Sparse ruling set with recursion: every K-th element (by index) and every
-// list head is a splitter; one thread per splitter walks its sublist up to
-// the next splitter, recording (owner splitter, offset) for each element and
-// the weighted gap to the next splitter.  The splitters form a shorter
-// weighted list that is ranked the same way until it fits one block's shared
-// memory, where Wyllie pointer jumping finishes it.  A final pass adds the
-// splitter's position to each element's offset.
+// Sparse ruling set with recursion.  Every K-th element (by index) and every
+// list head is a splitter; one thread per splitter walks its sublist up to the
+// next splitter, reading the successor array (read-only) and writing one
+// 8-byte {owner splitter, offset} record per element to a separate array.
+// (Overwriting the successor record in place is several times slower on
+// GB300: the store to the address just loaded stalls the dependent chain.)
+// The splitters form a shorter weighted list, ranked the same way until it fits
+// one block's shared memory, where Wyllie pointer jumping finishes it.  A
+// final coalesced pass adds each owner's position to the element's offset.
 //
-// Indices of the successor array follow the lexicographic arc order, which is
-// unrelated to tour order, so the index-spaced splitters are a uniform random
-// sample of the tour: gaps average K.  Every walk is bounded by N steps; a
-// longer walk (a cycle without a head: the input was not a forest) sets an
-// error bit and stops.
+// Element indices follow the lexicographic arc order, unrelated to tour
+// order, so index-spaced splitters sample the tour uniformly: gaps average K.
+// Walks are bounded by N steps; the first level also counts visited elements,
+// so an element on a cycle without a head (the input was not a forest) is
+// reported instead of silently left unranked.
 #include "pipeline.cuh"
 
 namespace rst {
@@ -21,15 +23,15 @@ namespace rst {
 constexpr int kLrK = 16;                 // splitter spacing (power of two)
 constexpr int kLrBase = 4096;            // shared-memory Wyllie base case
 constexpr int kLrBaseThreads = 1024;
+constexpr int kLrWalkThreads = 128;
 
 struct LevelBufs {
-  int32_t* owner;   // N
-  uint32_t* local;  // N
-  int32_t* snext;   // S
-  uint32_t* slen;   // S
-  int32_t* sstart;  // S
+  int2* ol;         // N {owner, offset} records of this level
+  int32_t* snext;   // S successors of the next level
+  uint32_t* w_next; // S weights of the next level
+  int32_t* sstart;  // S (only the head slots are used)
   int32_t* shead;   // h
-  uint32_t* spos;   // S
+  uint32_t* spos;   // S positions of the splitters
 };
 
 static int64_t lr_splitters(int64_t N, int64_t h) { return (N + kLrK - 1) / kLrK + h; }
@@ -40,10 +42,9 @@ static void lr_layout(Arena& ar, int64_t N, int64_t h, std::vector<LevelBufs>* l
   while (N > kLrBase && h <= N / 4) {
     const int64_t S = lr_splitters(N, h);
     LevelBufs b;
-    b.owner = ar.take<int32_t>(N);
-    b.local = ar.take<uint32_t>(N);
+    b.ol = ar.take<int2>(N);
     b.snext = ar.take<int32_t>(S);
-    b.slen = ar.take<uint32_t>(S);
+    b.w_next = ar.take<uint32_t>(S);
     b.sstart = ar.take<int32_t>(S);
     b.shead = ar.take<int32_t>(h);
     b.spos = ar.take<uint32_t>(S);
@@ -94,27 +95,31 @@ __global__ void k_lr_heads(int64_t N, int64_t S0, const int32_t* __restrict__ he
   }
 }
 
-__global__ void k_lr_walk(int64_t N, int64_t S0, int64_t S, const int32_t* __restrict__ nxt,
-                          const uint32_t* __restrict__ w, const int32_t* __restrict__ sstart,
-                          int32_t* __restrict__ owner, uint32_t* __restrict__ local,
-                          int32_t* __restrict__ snext, uint32_t* __restrict__ slen,
-                          uint32_t* status) {
+// One thread per splitter: ol[x] = {owner splitter, weighted offset}.
+__global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S0, int64_t S,
+                                                            const int32_t* __restrict__ nxt,
+                                                            const uint32_t* __restrict__ w,
+                                                            const int32_t* __restrict__ sstart,
+                                                            int2* __restrict__ ol,
+                                                            int32_t* __restrict__ snext,
+                                                            uint32_t* __restrict__ w_next,
+                                                            unsigned long long* visited,
+                                                            uint32_t* status) {
+  unsigned long long seen = 0;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int64_t start = s < S0 ? s * kLrK : (int64_t)sstart[s];
     if (start < 0) {
       snext[s] = -1;
-      slen[s] = 0;
+      w_next[s] = 0;
       continue;
     }
-    owner[start] = (int32_t)s;
-    local[start] = 0;
+    ol[start] = make_int2((int32_t)s, 0);
     uint32_t acc = wget(w, start);
     int32_t x = nxt[start];
-    int64_t steps = 0;
+    int64_t steps = 1;
     while (x >= 0 && (x & (kLrK - 1)) != 0) {
-      owner[x] = (int32_t)s;
-      local[x] = acc;
+      ol[x] = make_int2((int32_t)s, (int32_t)acc);
       acc += wget(w, x);
       x = nxt[x];
       if (++steps > N) {
@@ -124,25 +129,28 @@ __global__ void k_lr_walk(int64_t N, int64_t S0, int64_t S, const int32_t* __res
       }
     }
     snext[s] = x < 0 ? -1 : x / kLrK;
-    slen[s] = acc;
+    w_next[s] = acc;
+    seen += (unsigned long long)steps;
+  }
+  if (visited) {
+    for (int d = 16; d > 0; d >>= 1) seen += __shfl_down_sync(0xffffffffu, seen, d);
+    if ((threadIdx.x & 31) == 0 && seen) atomicAdd(visited, seen);
   }
 }
 
-// Elements no walk reached: at the first level they lie on a cycle without a
-// head (the input was not a forest); at deeper levels they are the unused
-// slots of heads that coincided with a regular splitter, and are ignored.
-__global__ void k_lr_final(int64_t N, const int32_t* __restrict__ owner,
-                           const uint32_t* __restrict__ local, const uint32_t* __restrict__ spos,
-                           uint32_t* __restrict__ pos, int first_level, uint32_t* status) {
+// pos[x] = position of x's owner + x's offset.  At the first level every
+// element must have been visited (visited == N); at deeper levels the unused
+// slots of heads that coincided with a regular splitter are never visited and
+// their value is ignored.
+__global__ void k_lr_final(int64_t N, const int2* __restrict__ ol, const uint32_t* __restrict__ spos,
+                           uint32_t* __restrict__ pos, const unsigned long long* visited,
+                           uint32_t* status) {
+  if (visited && blockIdx.x == 0 && threadIdx.x == 0 && *visited != (unsigned long long)N)
+    raise_error(status, DERR_NOT_FOREST);
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
        x += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t o = owner[x];
-    if (o < 0) {
-      if (first_level) raise_error(status, DERR_NOT_FOREST);
-      pos[x] = kNone;
-    } else {
-      pos[x] = spos[o] + local[x];
-    }
+    const int2 r = ol[x];
+    pos[x] = (r.x >= 0) ? spos[r.x] + (uint32_t)r.y : kNone;
   }
 }
 
@@ -221,8 +229,8 @@ __global__ void k_wyl_round(int64_t N, const int32_t* __restrict__ pj, const uin
   if (any) *flag = 1;
 }
 
-rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w,
-                     const int32_t* heads, int64_t nheads, uint32_t* pos, cudaStream_t s) {
+rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w, const int32_t* heads,
+                     int64_t nheads, uint32_t* pos, cudaStream_t s) {
   if (N <= 0) return RST_OK;
   std::vector<LevelBufs> levels;
   int32_t* wpj = nullptr;
@@ -231,9 +239,10 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   lr_layout(ar, N, nheads, &levels, &wpj, &wval, &wflag);
   for (auto& b : levels)
     if (!b.spos) return RST_ERR_OOM;
+  set_stat(STAT_LEVELS, (long long)levels.size());
   uint32_t* status = state().status;
+  unsigned long long* visited = dev_counter(7);
 
-  // descend
   struct Frame {
     int64_t N;
     const int32_t* nxt;
@@ -247,45 +256,48 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     LevelBufs& b = levels[l];
     const int64_t S0 = (f.N + kLrK - 1) / kLrK;
     const int64_t S = S0 + nheads;
-    RST_CUDA(cudaMemsetAsync(b.owner, 0xff, f.N * sizeof(int32_t), s));
-    k_lr_heads<<<grid_for(nheads), kBlock, 0, s>>>(f.N, S0, f.heads, nheads, b.sstart, b.shead);
-    k_lr_walk<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(f.N, S0, S, f.nxt, f.w, b.sstart, b.owner,
-                                                    b.local, b.snext, b.slen, status);
+    if (l == 0) RST_CUDA(cudaMemsetAsync(visited, 0, sizeof(unsigned long long), s));
+    RST_LAUNCH(k_lr_heads, grid_for(nheads), kBlock, 0, s)(f.N, S0, f.heads, nheads, b.sstart, b.shead);
+    prof_mark(s, l == 0 ? "lr_prep1" : "lr_prep");
+    RST_LAUNCH(k_lr_walk, (unsigned)((S + kLrWalkThreads - 1) / kLrWalkThreads), kLrWalkThreads, 0, s)(
+        f.N, S0, S, f.nxt, f.w, b.sstart, b.ol, b.snext, b.w_next, l == 0 ? visited : nullptr, status);
+    prof_mark(s, l == 0 ? "k_lr_walk1" : "k_lr_walk");
     RST_CUDA(cudaGetLastError());
     frames.push_back(f);
-    f = Frame{S, b.snext, b.slen, b.shead, b.spos};
+    f = Frame{S, b.snext, b.w_next, b.shead, b.spos};
   }
-  // base
   if (f.N <= kLrBase) {
-    k_lr_base<<<1, kLrBaseThreads, 0, s>>>(f.N, f.nxt, f.w, f.pos);
+    RST_LAUNCH(k_lr_base, 1, kLrBaseThreads, 0, s)(f.N, f.nxt, f.w, f.pos);
   } else {
     RST_CUDA(cudaMemsetAsync(wpj, 0xff, f.N * sizeof(int32_t), s));
     RST_CUDA(cudaMemsetAsync(wval, 0, f.N * sizeof(uint32_t), s));
-    k_wyl_init<<<grid_for(f.N), kBlock, 0, s>>>(f.N, f.nxt, f.w, wpj, wval);
+    RST_LAUNCH(k_wyl_init, grid_for(f.N), kBlock, 0, s)(f.N, f.nxt, f.w, wpj, wval);
     int32_t* pa = wpj;
     int32_t* pb = wpj + f.N;
     uint32_t* va = wval;
     uint32_t* vb = wval + f.N;
     for (int round = 0; round < 40; ++round) {
       RST_CUDA(cudaMemsetAsync(wflag, 0, sizeof(int32_t), s));
-      k_wyl_round<<<grid_for(f.N), kBlock, 0, s>>>(f.N, pa, va, pb, vb, wflag);
+      RST_LAUNCH(k_wyl_round, grid_for(f.N), kBlock, 0, s)(f.N, pa, va, pb, vb, wflag);
       std::swap(pa, pb);
       std::swap(va, vb);
       int32_t hf = 0;
-      RST_CUDA(cudaMemcpyAsync(&hf, wflag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      RST_CUDA(cudaMemcpyAsync(state().hostbuf, wflag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       RST_CUDA(cudaStreamSynchronize(s));
+      std::memcpy(&hf, state().hostbuf, sizeof(int32_t));
       if (!hf) break;
       if (round == 39) return RST_ERR_NOT_CONVERGED;
     }
     RST_CUDA(cudaMemcpyAsync(f.pos, va, f.N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   }
+  prof_mark(s, "lr_base");
   RST_CUDA(cudaGetLastError());
-  // ascend
   for (int l = (int)levels.size() - 1; l >= 0; --l) {
     const Frame& fr = frames[l];
     LevelBufs& b = levels[l];
-    k_lr_final<<<grid_for(fr.N), kBlock, 0, s>>>(fr.N, b.owner, b.local, b.spos, fr.pos, l == 0,
-                                                  status);
+    RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, b.ol, b.spos, fr.pos,
+                                                         l == 0 ? visited : nullptr, status);
+    prof_mark(s, l == 0 ? "k_lr_final1" : "k_lr_final");
   }
   RST_CUDA(cudaGetLastError());
   return RST_OK;

@@ -50,18 +50,11 @@ struct EulerIn {
   int64_t nheads = 0;
 };
 
-// Tree arcs live in "tree positions" 0..2T-1 in lexicographic (src, dst)
-// order; pairs hold {i, k, a, b} with i the position of a->b and k of b->a;
-// toff[v] .. toff[v+1]-1 is v's run; is_root marks tree roots.  Builds succ,
-// ranks the tour and writes parents of every vertex that has a tree edge.
-rst_status euler_from_pairs(Arena& ar, int64_t n, int64_t T, uint4* pairs, const uint32_t* toff,
-                            const uint8_t* is_root, const int32_t* heads, int64_t nheads,
-                            int32_t* parent_out, uint32_t* rank_out, cudaStream_t s);
-size_t euler_workspace_bytes(int64_t n, int64_t T, int64_t nheads);
 
 // CSR-bitmap front end: converts CC output into tree positions, marks roots
 // (the requested root for its component, the minimum vertex otherwise), sets
-// P[v] = v for roots and singletons, then runs euler_from_pairs.
+// P[v] = v for roots and singletons, builds the Euler successors, ranks the
+// tours and sets every other parent from the ranks.
 template <class OffT>
 rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32_t root,
                          CcOut* cc, int32_t* parent_out, uint32_t* rank_out, cudaStream_t s);

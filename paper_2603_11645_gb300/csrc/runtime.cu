@@ -1,4 +1,5 @@
 // Runtime support: per-device workspace, status word, error reporting, scans.
+#include <atomic>
 #include <cstring>
 
 #include "common.cuh"
@@ -11,6 +12,33 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
   snprintf(g_last_error, sizeof(g_last_error), "%s at %s:%d: %s", cudaGetErrorString(e), file,
            line, what);
   if (getenv("RST_DEBUG")) fprintf(stderr, "[rst] %s\n", g_last_error);
+}
+
+static std::atomic<long long> g_launches{0};
+static long long g_stats[STAT_COUNT] = {0};
+void set_stat(int slot, long long v) {
+  if (slot >= 0 && slot < STAT_COUNT) g_stats[slot] = v;
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct Profiler {
+  bool on = false;
+  std::vector<std::pair<const char*, cudaEvent_t>> marks;
+  std::vector<cudaEvent_t> pool;
+};
+static Profiler g_prof;
+
+void prof_mark(cudaStream_t s, const char* name) {
+  if (!g_prof.on) return;
+  cudaEvent_t e;
+  if (g_prof.pool.empty()) {
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+  } else {
+    e = g_prof.pool.back();
+    g_prof.pool.pop_back();
+  }
+  cudaEventRecord(e, s);
+  g_prof.marks.emplace_back(name, e);
 }
 
 constexpr int kMaxDevices = 64;
@@ -223,9 +251,9 @@ static rst_status scan_impl(Load load, OutT* out, int64_t count, unsigned long l
                             cudaStream_t s) {
   int64_t blocks = (count + kScanTile - 1) / kScanTile;
   if (blocks < 1) blocks = 1;
-  k_scan_reduce<<<(unsigned)blocks, kScanThreads, 0, s>>>(load, count, tmp);
-  k_scan_partials<<<1, 1024, 0, s>>>(tmp, blocks);
-  k_scan_down<<<(unsigned)blocks, kScanThreads, 0, s>>>(load, count, tmp, out);
+  RST_LAUNCH(k_scan_reduce, (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp);
+  RST_LAUNCH(k_scan_partials, 1, 1024, 0, s)(tmp, blocks);
+  RST_LAUNCH(k_scan_down, (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp, out);
   RST_CUDA(cudaGetLastError());
   return RST_OK;
 }
@@ -241,3 +269,38 @@ rst_status scan_popcount_words(const uint32_t* words, uint32_t* out, int64_t cou
 }
 
 }  // namespace rst
+
+extern "C" {
+
+long long rst_launch_count(void) { return rst::g_launches.load(); }
+
+int rst_last_stats(long long* out, int max) {
+  int k = max < rst::STAT_COUNT ? max : rst::STAT_COUNT;
+  for (int i = 0; i < k; ++i) out[i] = rst::g_stats[i];
+  return k;
+}
+
+void rst_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(rst::call_lock());
+  for (auto& m : rst::g_prof.marks) rst::g_prof.pool.push_back(m.second);
+  rst::g_prof.marks.clear();
+  rst::g_prof.on = on != 0;
+}
+
+int rst_profile_read(float* ms_out, const char** names_out, int max_stages) {
+  std::lock_guard<std::mutex> g(rst::call_lock());
+  auto& marks = rst::g_prof.marks;
+  int k = 0;
+  if (!marks.empty()) cudaEventSynchronize(marks.back().second);
+  for (size_t i = 1; i < marks.size() && k < max_stages; ++i, ++k) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, marks[i - 1].second, marks[i].second);
+    if (ms_out) ms_out[k] = ms;
+    if (names_out) names_out[k] = marks[i].first;
+  }
+  for (auto& m : marks) rst::g_prof.pool.push_back(m.second);
+  marks.clear();
+  return k;
+}
+
+}  // extern "C"

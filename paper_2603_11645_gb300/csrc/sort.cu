@@ -92,9 +92,9 @@ rst_status radix_sort_keys(Arena& ar, uint64_t* keys, int64_t count, int key_bit
   uint64_t* dst = alt;
   int passes = 0;
   for (int shift = 0; shift < key_bits; shift += 8, ++passes) {
-    k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(src, count, shift, hist, tiles);
+    RST_LAUNCH(k_sort_hist, (unsigned)tiles, kSortThreads, 0, s)(src, count, shift, hist, tiles);
     RST_TRY(scan_exclusive_u64(hist, hist, hist_n, tmp, s));
-    k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(src, count, shift, hist, tiles, dst);
+    RST_LAUNCH(k_sort_scatter, (unsigned)tiles, kSortThreads, 0, s)(src, count, shift, hist, tiles, dst);
     std::swap(src, dst);
   }
   RST_CUDA(cudaGetLastError());

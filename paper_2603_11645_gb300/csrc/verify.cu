@@ -61,9 +61,10 @@ struct SpanFn {
   const int32_t* __restrict__ col;
   const int32_t* __restrict__ tr;
   bool bad;
-  __device__ __forceinline__ void operator()(bool is_arc, int64_t row, int64_t arc) {
+  __device__ __forceinline__ void operator()(int, bool is_arc, int64_t row, int64_t arc) {
     if (is_arc && tr[row] != tr[col[arc]]) bad = true;
   }
+  __device__ __forceinline__ void end_tile() {}
 };
 
 template <class OffT>
@@ -125,14 +126,14 @@ static rst_status verify_impl(const OffT* off, const int32_t* col, int64_t n, in
     std::memcpy(out, st.hostbuf, sizeof(int32_t));
     return RST_OK;
   };
-  k_fill_i32_v<<<1, 32, 0, s>>>(verdict, 1, INT_MAX);
+  RST_LAUNCH(k_fill_i32_v, 1, 32, 0, s)(verdict, 1, INT_MAX);
   int32_t v = INT_MAX;
   // phase 1-2
-  k_ver_range<<<g, kBlock, 0, s>>>(n, root, parent, verdict);
+  RST_LAUNCH(k_ver_range, g, kBlock, 0, s)(n, root, parent, verdict);
   RST_CUDA(cudaGetLastError());
   RST_TRY(fetch(&v));
   if (v == INT_MAX) {
-    k_ver_edges<OffT><<<g, kBlock, 0, s>>>(off, col, n, parent, verdict);
+    RST_LAUNCH(k_ver_edges<OffT>, g, kBlock, 0, s)(off, col, n, parent, verdict);
     RST_TRY(fetch(&v));
   }
   if (v == INT_MAX) {
@@ -140,10 +141,10 @@ static rst_status verify_impl(const OffT* off, const int32_t* col, int64_t n, in
     int rounds = 1;
     while (((int64_t)1 << rounds) <= n) ++rounds;
     for (int r = 0; r <= rounds; ++r) {
-      k_ver_double<<<g, kBlock, 0, s>>>(n, a0, a1);
+      RST_LAUNCH(k_ver_double, g, kBlock, 0, s)(n, a0, a1);
       std::swap(a0, a1);
     }
-    k_ver_cycle<<<g, kBlock, 0, s>>>(n, parent, a0, verdict);
+    RST_LAUNCH(k_ver_cycle, g, kBlock, 0, s)(n, parent, a0, verdict);
     RST_CUDA(cudaGetLastError());
     RST_TRY(fetch(&v));
   }
@@ -151,7 +152,7 @@ static rst_status verify_impl(const OffT* off, const int32_t* col, int64_t n, in
     const int64_t tiles = (n + A + kMpTile - 1) / kMpTile;
     const int gt = (int)(tiles < (int64_t)device_info().sms * 8 ? (tiles > 0 ? tiles : 1)
                                                                  : (int64_t)device_info().sms * 8);
-    k_ver_span<OffT><<<gt, kMpThreads, 0, s>>>(off, n, A, col, a0, verdict);
+    RST_LAUNCH(k_ver_span<OffT>, gt, kMpThreads, 0, s)(off, n, A, col, a0, verdict);
     RST_CUDA(cudaGetLastError());
     RST_TRY(fetch(&v));
   }
@@ -160,9 +161,9 @@ static rst_status verify_impl(const OffT* off, const int32_t* col, int64_t n, in
     RST_CUDA(cudaMemcpyAsync(st.hostbuf, a0 + root, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RST_CUDA(cudaStreamSynchronize(s));
     std::memcpy(&root_tree, st.hostbuf, sizeof(int32_t));
-    k_fill_i32_v<<<g, kBlock, 0, s>>>(mn, n, INT_MAX);
-    k_ver_minv<<<g, kBlock, 0, s>>>(n, a0, root_tree, mn);
-    k_ver_roots<<<g, kBlock, 0, s>>>(n, parent, a0, root_tree, mn, verdict);
+    RST_LAUNCH(k_fill_i32_v, g, kBlock, 0, s)(mn, n, INT_MAX);
+    RST_LAUNCH(k_ver_minv, g, kBlock, 0, s)(n, a0, root_tree, mn);
+    RST_LAUNCH(k_ver_roots, g, kBlock, 0, s)(n, parent, a0, root_tree, mn, verdict);
     RST_CUDA(cudaGetLastError());
     RST_TRY(fetch(&v));
   }
