@@ -147,6 +147,30 @@ rst_status rst_verify(const void *csr_offsets, int offsets_bits, const int32_t *
                       int64_t n, int64_t m, int32_t root, const int32_t *parent,
                       int32_t *verdict_out, rst_stream_t stream);
 
+/*
+ * rst_build_noalloc -- the CC+Euler rooted spanning tree of rst_build, for
+ * callers that cannot allocate memory: code running while a stream is being
+ * captured into a CUDA graph (cudaMalloc is not permitted then), or hosts
+ * whose device-memory budget is fixed in advance.  The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ *   Arguments and output are those of rst_build with RST_CC_EULER; the
+ *   caller still provides the graph and parent_out in device memory.
+ *   Limits: n <= 65,536 vertices and m <= 524,288 arcs; larger inputs return
+ *   RST_ERR_UNSUPPORTED before any GPU work.
+ *   Memory: it never calls cudaMalloc, cudaFree, cudaMallocHost or any other
+ *   allocating routine.  Its workspace is a 16 MiB array defined inside the
+ *   library that every GPU loading the library holds until process exit.
+ *   The first call on a device looks up that array's device address; make
+ *   that first call before starting any stream capture.
+ *   Sharing: every call on a device uses the same array, which keeps the
+ *   previous call's contents (the call clears what must start at zero).
+ *   Calls whose GPU work overlaps (different streams without ordering) race
+ *   on the array; host-side calls are serialised.
+ */
+rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols,
+                             int64_t n, int64_t m, int32_t root, int32_t *parent_out,
+                             rst_stream_t stream);
+
 /* ---- diagnostics (no counterpart in the paper) ----------------------------
  * rst_launch_count: number of kernels this library has launched since load.
  * rst_profile_enable(1) starts recording a CUDA event at each stage boundary

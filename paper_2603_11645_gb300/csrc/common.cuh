@@ -110,8 +110,11 @@ struct DeviceState {
   unsigned long long* hostbuf = nullptr;  // pinned host scratch (64 words)
 };
 
-// Per-device state and the process-wide call lock.
+// Per-device state and the process-wide call lock.  A call that must not
+// allocate installs its own DeviceState (fixed buffers) for the current host
+// thread with set_state_override; state() then returns it.
 DeviceState& state();
+void set_state_override(DeviceState* st);
 std::mutex& call_lock();
 rst_status ensure_workspace(size_t bytes);
 

@@ -25,6 +25,8 @@ constexpr int kLrBase = 4096;            // shared-memory Wyllie base case
 constexpr int kLrBaseThreads = 1024;
 constexpr int kLrWalkThreads = 128;
 
+constexpr int kLrMaxLevels = 24;  // N < 2^32 shrinks by ~K per level
+
 struct LevelBufs {
   int2* ol;         // N {owner, offset} records of this level
   int32_t* snext;   // S successors of the next level
@@ -37,7 +39,17 @@ struct LevelBufs {
 static int64_t lr_splitters(int64_t N, int64_t h) { return (N + kLrK - 1) / kLrK + h; }
 
 // Walks the workspace plan: identical calls for the counting pass and the run.
-static void lr_layout(Arena& ar, int64_t N, int64_t h, std::vector<LevelBufs>* levels,
+// Fixed-capacity level list (no host allocation on the ranking path).
+struct LevelList {
+  LevelBufs b[kLrMaxLevels];
+  int count = 0;
+  void push_back(const LevelBufs& x) {
+    if (count < kLrMaxLevels) b[count] = x;
+    ++count;
+  }
+};
+
+static void lr_layout(Arena& ar, int64_t N, int64_t h, LevelList* levels,
                       int32_t** wyl_pj, uint32_t** wyl_val, int32_t** wyl_flag) {
   while (N > kLrBase && h <= N / 4) {
     const int64_t S = lr_splitters(N, h);
@@ -232,14 +244,15 @@ __global__ void k_wyl_round(int64_t N, const int32_t* __restrict__ pj, const uin
 rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w, const int32_t* heads,
                      int64_t nheads, uint32_t* pos, cudaStream_t s) {
   if (N <= 0) return RST_OK;
-  std::vector<LevelBufs> levels;
+  LevelList levels;
   int32_t* wpj = nullptr;
   uint32_t* wval = nullptr;
   int32_t* wflag = nullptr;
   lr_layout(ar, N, nheads, &levels, &wpj, &wval, &wflag);
-  for (auto& b : levels)
-    if (!b.spos) return RST_ERR_OOM;
-  set_stat(STAT_LEVELS, (long long)levels.size());
+  if (levels.count > kLrMaxLevels) return RST_ERR_UNSUPPORTED;
+  for (int l = 0; l < levels.count; ++l)
+    if (!levels.b[l].spos) return RST_ERR_OOM;
+  set_stat(STAT_LEVELS, (long long)levels.count);
   uint32_t* status = state().status;
   unsigned long long* visited = dev_counter(7);
 
@@ -250,10 +263,10 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     const int32_t* heads;
     uint32_t* pos;
   };
-  std::vector<Frame> frames;
+  Frame frames[kLrMaxLevels];
   Frame f{N, nxt, w, heads, pos};
-  for (size_t l = 0; l < levels.size(); ++l) {
-    LevelBufs& b = levels[l];
+  for (int l = 0; l < levels.count; ++l) {
+    LevelBufs& b = levels.b[l];
     const int64_t S0 = (f.N + kLrK - 1) / kLrK;
     const int64_t S = S0 + nheads;
     if (l == 0) RST_CUDA(cudaMemsetAsync(visited, 0, sizeof(unsigned long long), s));
@@ -263,7 +276,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
         f.N, S0, S, f.nxt, f.w, b.sstart, b.ol, b.snext, b.w_next, l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_walk1" : "k_lr_walk");
     RST_CUDA(cudaGetLastError());
-    frames.push_back(f);
+    frames[l] = f;
     f = Frame{S, b.snext, b.w_next, b.shead, b.spos};
   }
   if (f.N <= kLrBase) {
@@ -292,9 +305,9 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   }
   prof_mark(s, "lr_base");
   RST_CUDA(cudaGetLastError());
-  for (int l = (int)levels.size() - 1; l >= 0; --l) {
+  for (int l = levels.count - 1; l >= 0; --l) {
     const Frame& fr = frames[l];
-    LevelBufs& b = levels[l];
+    LevelBufs& b = levels.b[l];
     RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, b.ol, b.spos, fr.pos,
                                                          l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_final1" : "k_lr_final");

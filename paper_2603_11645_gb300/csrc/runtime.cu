@@ -14,6 +14,9 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
   if (getenv("RST_DEBUG")) fprintf(stderr, "[rst] %s\n", g_last_error);
 }
 
+static thread_local DeviceState* g_state_override = nullptr;
+void set_state_override(DeviceState* st) { g_state_override = st; }
+
 static std::atomic<long long> g_launches{0};
 static long long g_stats[STAT_COUNT] = {0};
 void set_stat(int slot, long long v) {
@@ -29,7 +32,7 @@ struct Profiler {
 static Profiler g_prof;
 
 void prof_mark(cudaStream_t s, const char* name) {
-  if (!g_prof.on) return;
+  if (!g_prof.on || g_state_override) return;  // event creation may allocate
   cudaEvent_t e;
   if (g_prof.pool.empty()) {
     if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -65,7 +68,8 @@ const Device& device_info() {
   return info;
 }
 
-DeviceState& state() { return g_state[current_device()]; }
+
+DeviceState& state() { return g_state_override ? *g_state_override : g_state[current_device()]; }
 
 std::mutex& call_lock() {
   static std::mutex m;
