@@ -170,6 +170,7 @@ rst_status rst_verify(const void* csr_offsets, int offsets_bits, const int32_t* 
 
 rst_status rst_shutdown(void) {
   CallGuard g;
+  destroy_round_graphs();
   DeviceState& st = state();
   if (st.ws) cudaFree(st.ws);
   if (st.status) cudaFree(st.status);

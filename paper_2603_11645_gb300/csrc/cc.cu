@@ -33,6 +33,22 @@ namespace rst {
 constexpr int kMaxRounds = 64;
 constexpr int32_t kFinal = -1;
 
+// Round control in device memory, so that the contraction rounds run without
+// host involvement (and can be captured in a CUDA graph).  Round r reads
+// st[r] and produces st[r+1].
+struct RoundState {
+  unsigned long long C;        // components entering the round
+  unsigned long long E;        // list entries entering the round (previous round's ids)
+  unsigned long long pool_at;  // this round's slice of the next/minv pools
+  int rc;                      // the requested root's component (-1: none)
+  int pad;
+};
+struct CcCtl {
+  RoundState st[kMaxRounds + 1];
+  int cur;          // current round
+  int root_label;   // canonical label of the requested root (-1 until known)
+};
+
 struct CcBuffers {
   int32_t* P;        // n: round-1 hook target, then root
   uint32_t* J;       // n: CSR position of the arc to the first neighbour (kNone: isolated)
@@ -41,7 +57,7 @@ struct CcBuffers {
   int32_t* Ecu[2];   // list entries (ping-pong)
   int32_t* Ecv[2];
   uint32_t* Ep[2];
-  unsigned long long* best;  // n/2+1
+  unsigned long long* best[2];  // n/2+1 each: round parity
   int32_t* P2;       // n/2+1
   int32_t* NID;      // n/2+1
   int32_t* nextpool; // n+1: per-round component maps
@@ -49,6 +65,7 @@ struct CcBuffers {
   uint4* pairs;      // n
   uint32_t* bits;    // A/32 + 1
   int32_t* roots;    // n/2+1
+  struct CcCtl* ctl; // device-resident round control
   int64_t ecap;      // list capacity
 };
 
@@ -65,7 +82,8 @@ static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
     b.Ecv[k] = ar.take<int32_t>(b.ecap);
     b.Ep[k] = ar.take<uint32_t>(b.ecap);
   }
-  b.best = ar.take<unsigned long long>(half);
+  b.best[0] = ar.take<unsigned long long>(half);
+  b.best[1] = ar.take<unsigned long long>(half);
   b.P2 = ar.take<int32_t>(half);
   b.NID = ar.take<int32_t>(half);
   b.nextpool = ar.take<int32_t>(n + 1);
@@ -73,6 +91,7 @@ static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
   b.pairs = ar.take<uint4>(n + 1);
   b.bits = ar.take<uint32_t>(A / 32 + 2);
   b.roots = ar.take<int32_t>(half);
+  b.ctl = ar.take<CcCtl>(1);
   return b;
 }
 
@@ -255,28 +274,95 @@ __global__ void __launch_bounds__(kMpThreads) k_build_list(const OffT* __restric
 }
 
 // ------------------------------------------------------------------ rounds >= 2
+//
+// Round r on the contracted graph (components have dense ids 0..C-1):
+//  1 hook: map every list entry through the previous round's component map,
+//    drop entries inside one component, packed atomicMin on both endpoints,
+//    and append the survivors (the next round's list)
+//  2 resolve: final components, mutual pairs, hooks, tree-edge records
+//  3 compress: shortcut the hook forest
+//  4 renumber: dense ids for the surviving roots; final components join the
+//    list of component roots
+//  5 map: component -> next id; minimum vertex per new component
+//  6 advance: next round, loop condition
 
-__global__ void k_fill_u64(unsigned long long* p, int64_t count, unsigned long long v) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = v;
+struct CcPtrs {
+  const int32_t* col;
+  int32_t* Ecu[2];
+  int32_t* Ecv[2];
+  uint32_t* Ep[2];
+  unsigned long long* best[2];
+  int32_t* P2;
+  int32_t* NID;
+  int32_t* nextpool;
+  int32_t* minvpool;
+  uint4* pairs;
+  uint32_t* bits;
+  int32_t* roots;
+  CcCtl* ctl;
+  unsigned long long* counters;
+  uint32_t* status;
+  int64_t ecap;
+};
+
+__global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__ C1) {
+  const unsigned long long C = b.counters[CNT_COMPS];
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < (int64_t)C;
+       c += (int64_t)gridDim.x * blockDim.x)
+    b.best[0][c] = ~0ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    CcCtl* t = b.ctl;
+    t->st[0].C = C;
+    t->st[0].E = b.counters[CNT_LIST];
+    t->st[0].pool_at = 0;
+    const int32_t c1 = root >= 0 ? C1[root] : -1;
+    t->st[0].rc = c1;
+    t->root_label = (root >= 0 && c1 < 0) ? root : -1;
+    t->cur = 0;
+  }
 }
 
-__global__ void k_fill_i32(int32_t* p, int64_t count, int32_t v) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = v;
-}
-
-// Packed minimum-key hook: best[c] = min over incident edges of (key << 32 | other).
-__global__ void k_hook(int64_t E, const int32_t* __restrict__ Ecu, const int32_t* __restrict__ Ecv,
-                       const uint32_t* __restrict__ Ep, unsigned long long* __restrict__ best) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t cu = (uint32_t)Ecu[e], cv = (uint32_t)Ecv[e];
-    const unsigned long long key = (unsigned long long)Ep[e] << 32;
-    atomicMin(&best[cu], key | cv);
-    atomicMin(&best[cv], key | cu);
+__global__ void k_round_hook(CcPtrs b) {
+  CcCtl* t = b.ctl;
+  const int r = t->cur;
+  const int64_t E = (int64_t)t->st[r].E;
+  const int src = r & 1, dst = src ^ 1;
+  const int32_t* __restrict__ mp = r == 0 ? nullptr : b.nextpool + t->st[r - 1].pool_at;
+  unsigned long long* __restrict__ best = b.best[r & 1];
+  const int32_t* __restrict__ Icu = b.Ecu[src];
+  const int32_t* __restrict__ Icv = b.Ecv[src];
+  const uint32_t* __restrict__ Ip = b.Ep[src];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride) {
+    const int64_t e = base + threadIdx.x;
+    bool keep = false;
+    int32_t cu = 0, cv = 0;
+    uint32_t p = 0;
+    if (e < E) {
+      cu = Icu[e];
+      cv = Icv[e];
+      p = Ip[e];
+      if (mp) {
+        cu = mp[cu];
+        cv = mp[cv];
+      }
+      keep = cu != cv;
+      if (keep) {
+        const unsigned long long key = (unsigned long long)p << 32;
+        atomicMin(&best[cu], key | (uint32_t)cv);
+        atomicMin(&best[cv], key | (uint32_t)cu);
+      }
+    }
+    const unsigned long long slot = block_reserve<kBlock>(&t->st[r + 1].E, keep ? 1u : 0u);
+    if (keep) {
+      if ((int64_t)slot < b.ecap) {
+        b.Ecu[dst][slot] = cu;
+        b.Ecv[dst][slot] = cv;
+        b.Ep[dst][slot] = p;
+      } else {
+        raise_error(b.status, DERR_CAPACITY);
+      }
+    }
   }
 }
 
@@ -304,52 +390,56 @@ __device__ __forceinline__ bool twin_of_position(const OffT* __restrict__ off,
   return true;
 }
 
-// Resolve one round: a component with no incident edge is final; otherwise it
-// hooks onto the component its minimum-key edge reaches, except the smaller id
-// of a mutual pair, which stays a root.  Each hook records its tree edge.
+// A component with no incident edge is final; otherwise it hooks onto the
+// component its minimum-key edge reaches, except the smaller id of a mutual
+// pair, which stays a root.  Each hook records its tree edge.
 template <class OffT>
-__global__ void k_resolve(const OffT* __restrict__ off, const int32_t* __restrict__ col, int64_t C,
-                          const unsigned long long* __restrict__ best, int32_t* __restrict__ P2,
-                          uint4* __restrict__ pairs, uint32_t* __restrict__ bits,
-                          unsigned long long* counters, uint32_t* status) {
+__global__ void k_round_resolve(CcPtrs b, const OffT* __restrict__ off) {
+  CcCtl* t = b.ctl;
+  const int r = t->cur;
+  const int64_t C = (int64_t)t->st[r].C;
+  const unsigned long long* __restrict__ best = b.best[r & 1];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < C; base += stride) {
     const int64_t c = base + threadIdx.x;
     bool emit = false;
     uint4 rec = make_uint4(0, 0, 0, 0);
     if (c < C) {
-      const unsigned long long b = best[c];
-      if (b == ~0ull) {
-        P2[c] = (int32_t)c;
+      const unsigned long long bc = best[c];
+      if (bc == ~0ull) {
+        b.P2[c] = (int32_t)c;
       } else {
-        const int32_t c2 = (int32_t)(uint32_t)(b & 0xffffffffull);
-        const uint32_t p = (uint32_t)(b >> 32);
+        const int32_t c2 = (int32_t)(uint32_t)(bc & 0xffffffffull);
+        const uint32_t p = (uint32_t)(bc >> 32);
         const bool mutual = (uint32_t)(best[c2] >> 32) == p;
         if (mutual && (int32_t)c < c2) {
-          P2[c] = (int32_t)c;
+          b.P2[c] = (int32_t)c;
         } else {
-          P2[c] = c2;
-          const int32_t bb = col[p];
+          b.P2[c] = c2;
+          const int32_t bb = b.col[p];
           int32_t a = 0;
           int64_t q = 0;
-          if (twin_of_position(off, col, bb, (uint64_t)p, &a, &q)) {
+          if (twin_of_position(off, b.col, bb, (uint64_t)p, &a, &q)) {
             emit = true;
             rec = make_uint4(p, (uint32_t)q, (uint32_t)a, (uint32_t)bb);
-            atomicOr(&bits[p >> 5], 1u << (p & 31));
-            atomicOr(&bits[rec.y >> 5], 1u << (rec.y & 31));
+            atomicOr(&b.bits[p >> 5], 1u << (p & 31));
+            atomicOr(&b.bits[rec.y >> 5], 1u << (rec.y & 31));
           } else {
-            raise_error(status, DERR_INDEX);
+            raise_error(b.status, DERR_INDEX);
           }
         }
       }
     }
-    const unsigned long long slot = block_reserve<kBlock>(&counters[CNT_PAIRS], emit ? 1u : 0u);
-    if (emit) pairs[slot] = rec;
+    const unsigned long long slot = block_reserve<kBlock>(&b.counters[CNT_PAIRS], emit ? 1u : 0u);
+    if (emit) b.pairs[slot] = rec;
   }
 }
 
 // Pointer jumping over the component forest: shortcut every component to its root.
-__global__ void k_compress(int64_t C, int32_t* P2, uint32_t* status) {
+__global__ void k_round_compress(CcPtrs b) {
+  CcCtl* t = b.ctl;
+  const int64_t C = (int64_t)t->st[t->cur].C;
+  int32_t* P2 = b.P2;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
        c += (int64_t)gridDim.x * blockDim.x) {
     int32_t x = P2[c];
@@ -359,7 +449,7 @@ __global__ void k_compress(int64_t C, int32_t* P2, uint32_t* status) {
       if (y == x) break;
       x = y;
       if (++it > C) {
-        raise_error(status, DERR_ROUND_LIMIT);
+        raise_error(b.status, DERR_ROUND_LIMIT);
         break;
       }
     }
@@ -367,83 +457,77 @@ __global__ void k_compress(int64_t C, int32_t* P2, uint32_t* status) {
   }
 }
 
-// New dense ids for the roots that still have edges; components without edges
-// are final and their minimum vertex joins the list of component roots.
-__global__ void k_renumber(int64_t C, const int32_t* __restrict__ P2,
-                           const unsigned long long* __restrict__ best,
-                           const int32_t* __restrict__ minv, int32_t* __restrict__ NID,
-                           int32_t* __restrict__ roots, unsigned long long* counters) {
+// Dense ids for the roots that still have edges (their next-round hook slot
+// starts empty and their minimum vertex starts as their own); components
+// without edges are final and their minimum vertex joins the root list.
+__global__ void k_round_renumber(CcPtrs b) {
+  CcCtl* t = b.ctl;
+  const int r = t->cur;
+  const int64_t C = (int64_t)t->st[r].C;
+  const unsigned long long* __restrict__ best = b.best[r & 1];
+  unsigned long long* __restrict__ best_next = b.best[(r + 1) & 1];
+  const int32_t* __restrict__ minv = b.minvpool + t->st[r].pool_at;
+  int32_t* __restrict__ minv_next = b.minvpool + t->st[r].pool_at + C;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < C; base += stride) {
     const int64_t c = base + threadIdx.x;
     bool live_root = false, fin = false;
     if (c < C) {
       fin = best[c] == ~0ull;
-      live_root = !fin && P2[c] == (int32_t)c;
+      live_root = !fin && b.P2[c] == (int32_t)c;
     }
-    const unsigned long long id = block_reserve<kBlock>(&counters[CNT_NEXT], live_root ? 1u : 0u);
-    const unsigned long long rid = block_reserve<kBlock>(&counters[CNT_ROOTS], fin ? 1u : 0u);
-    if (c < C) NID[c] = live_root ? (int32_t)id : -1;
-    if (fin) roots[rid] = minv[c];
+    const unsigned long long id = block_reserve<kBlock>(&t->st[r + 1].C, live_root ? 1u : 0u);
+    const unsigned long long rid = block_reserve<kBlock>(&b.counters[CNT_ROOTS], fin ? 1u : 0u);
+    if (c < C) b.NID[c] = live_root ? (int32_t)id : -1;
+    if (fin) b.roots[rid] = minv[c];
+    if (live_root) {
+      best_next[id] = ~0ull;
+      minv_next[id] = minv[c];
+    }
   }
 }
 
-__global__ void k_map(int64_t C, const int32_t* __restrict__ P2,
-                      const unsigned long long* __restrict__ best,
-                      const int32_t* __restrict__ NID, const int32_t* __restrict__ minv,
-                      int32_t* __restrict__ next, int32_t* __restrict__ minv_next) {
+__global__ void k_round_map(CcPtrs b) {
+  CcCtl* t = b.ctl;
+  const int r = t->cur;
+  const int64_t C = (int64_t)t->st[r].C;
+  const unsigned long long* __restrict__ best = b.best[r & 1];
+  const int32_t* __restrict__ minv = b.minvpool + t->st[r].pool_at;
+  int32_t* __restrict__ minv_next = b.minvpool + t->st[r].pool_at + C;
+  int32_t* __restrict__ next = b.nextpool + t->st[r].pool_at;
+  const int rc = t->st[r].rc;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
        c += (int64_t)gridDim.x * blockDim.x) {
-    if (best[c] == ~0ull) {
-      next[c] = kFinal;
-    } else {
-      const int32_t nc = NID[P2[c]];
-      next[c] = nc;
-      atomicMin(&minv_next[nc], minv[c]);
+    const bool fin = best[c] == ~0ull;
+    int32_t nc = kFinal;
+    if (!fin) {
+      const int32_t root = b.P2[c];
+      nc = b.NID[root];
+      if (root != (int32_t)c) atomicMin(&minv_next[nc], minv[c]);
     }
+    next[c] = nc;
+    if ((int32_t)c == rc) {
+      t->st[r + 1].rc = nc;
+      if (fin) t->root_label = minv[c];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    t->st[r + 1].pool_at = t->st[r].pool_at + C;
+    if (rc < 0) t->st[r + 1].rc = -1;
   }
 }
 
-// Relabel the edge list into the next round's ids, dropping edges that now
-// join a component to itself.
-__global__ void k_relabel(int64_t E, const int32_t* __restrict__ Ecu, const int32_t* __restrict__ Ecv,
-                          const uint32_t* __restrict__ Ep, const int32_t* __restrict__ next,
-                          int32_t* __restrict__ Ocu, int32_t* __restrict__ Ocv,
-                          uint32_t* __restrict__ Op, unsigned long long* counter) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride) {
-    const int64_t e = base + threadIdx.x;
-    bool keep = false;
-    int32_t nu = 0, nv = 0;
-    uint32_t p = 0;
-    if (e < E) {
-      nu = next[Ecu[e]];
-      nv = next[Ecv[e]];
-      p = Ep[e];
-      keep = nu != nv;
-    }
-    const unsigned long long slot = block_reserve<kBlock>(counter, keep ? 1u : 0u);
-    if (keep) {
-      Ocu[slot] = nu;
-      Ocv[slot] = nv;
-      Op[slot] = p;
-    }
+// Next round; the loop continues while components remain.
+__global__ void k_round_advance(CcPtrs b, cudaGraphConditionalHandle h, int use_handle) {
+  CcCtl* t = b.ctl;
+  const int r = t->cur + 1;
+  t->cur = r;
+  bool more = t->st[r].C > 0;
+  if (more && r >= kMaxRounds) {
+    raise_error(b.status, DERR_ROUND_LIMIT);
+    more = false;
   }
-}
-
-// All components of the last round are final.
-__global__ void k_all_final(int64_t C, const int32_t* __restrict__ minv, int32_t* __restrict__ next,
-                            int32_t* __restrict__ roots, unsigned long long* counters) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < C; base += stride) {
-    const int64_t c = base + threadIdx.x;
-    const bool ok = c < C;
-    const unsigned long long rid = block_reserve<kBlock>(&counters[CNT_ROOTS], ok ? 1u : 0u);
-    if (ok) {
-      roots[rid] = minv[c];
-      next[c] = kFinal;
-    }
-  }
+  if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // Labels, backwards over rounds: lab_r[c] = minv_r[c] if final, else lab_{r+1}[next_r[c]].
@@ -465,30 +549,91 @@ __global__ void k_label_vertices(int64_t n, const int32_t* __restrict__ C1,
   }
 }
 
-struct RoundTable {
-  int64_t base[kMaxRounds];
-  int nrounds;
-};
+// ------------------------------------------------------------------ round graph
 
-// Canonical label of one vertex by following its component through the rounds.
-__global__ void k_root_label(int32_t v, const int32_t* __restrict__ C1,
-                             const int32_t* __restrict__ nextpool,
-                             const int32_t* __restrict__ minvpool, RoundTable rt,
-                             unsigned long long* counters) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  int32_t c = C1[v];
-  int32_t lab = v;
-  if (c >= 0) {
-    for (int r = 0; r < rt.nrounds; ++r) {
-      const int32_t nc = nextpool[rt.base[r] + c];
-      if (nc == kFinal) {
-        lab = minvpool[rt.base[r] + c];
-        break;
-      }
-      c = nc;
+// One instantiated graph per (workspace, graph) binding: a while-conditional
+// node whose body is the six round kernels.
+struct RoundGraph {
+  bool valid = false;
+  const void* key_off = nullptr;
+  const void* key_col = nullptr;
+  const void* key_ws = nullptr;
+  int64_t key_n = 0, key_A = 0;
+  int key_dev = -1;
+  cudaGraphExec_t exec = nullptr;
+};
+constexpr int kGraphCache = 8;
+static RoundGraph g_round_graphs[kGraphCache];
+static int g_round_graph_next = 0;
+static cudaStream_t g_capture_stream[64] = {};
+
+void destroy_round_graphs() {
+  for (auto& g : g_round_graphs) {
+    if (g.valid && g.exec) cudaGraphExecDestroy(g.exec);
+    g = RoundGraph{};
+  }
+}
+
+template <class OffT>
+static void launch_round_body(const CcPtrs& p, const OffT* off, cudaGraphConditionalHandle h,
+                              int use_handle, cudaStream_t s) {
+  const int g = device_info().sms * 8;
+  RST_LAUNCH(k_round_hook, g, kBlock, 0, s)(p);
+  RST_LAUNCH(k_round_resolve<OffT>, g, kBlock, 0, s)(p, off);
+  RST_LAUNCH(k_round_compress, g, kBlock, 0, s)(p);
+  RST_LAUNCH(k_round_renumber, g, kBlock, 0, s)(p);
+  RST_LAUNCH(k_round_map, g, kBlock, 0, s)(p);
+  RST_LAUNCH(k_round_advance, 1, 1, 0, s)(p, h, use_handle);
+}
+
+template <class OffT>
+static rst_status round_graph_for(const CcPtrs& p, const OffT* off, int64_t n, int64_t A,
+                                  cudaGraphExec_t* out) {
+  int dev = 0;
+  RST_CUDA(cudaGetDevice(&dev));
+  for (auto& g : g_round_graphs) {
+    if (g.valid && g.key_off == off && g.key_col == p.col && g.key_ws == (const void*)p.ctl &&
+        g.key_n == n && g.key_A == A && g.key_dev == dev) {
+      *out = g.exec;
+      return RST_OK;
     }
   }
-  counters[CNT_ROOTLABEL] = (unsigned long long)(uint32_t)lab;
+  if (dev < 0 || dev >= 64) return RST_ERR_UNSUPPORTED;
+  if (!g_capture_stream[dev])
+    RST_CUDA(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
+  cudaStream_t cs = g_capture_stream[dev];
+  cudaGraph_t graph = nullptr;
+  RST_CUDA(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h;
+  RST_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  RST_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  RST_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_round_body<OffT>(p, off, h, 1, cs);
+  cudaGraph_t captured = nullptr;
+  RST_CUDA(cudaStreamEndCapture(cs, &captured));
+  cudaGraphExec_t exec = nullptr;
+  RST_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  RST_CUDA(cudaGraphDestroy(graph));
+  RoundGraph& slot = g_round_graphs[g_round_graph_next];
+  g_round_graph_next = (g_round_graph_next + 1) % kGraphCache;
+  if (slot.valid && slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot.valid = true;
+  slot.key_off = off;
+  slot.key_col = p.col;
+  slot.key_ws = p.ctl;
+  slot.key_n = n;
+  slot.key_A = A;
+  slot.key_dev = dev;
+  slot.exec = exec;
+  *out = exec;
+  return RST_OK;
 }
 
 // ------------------------------------------------------------------ driver
@@ -497,11 +642,12 @@ template <class OffT>
 rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A,
                   int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s) {
   CcBuffers b = cc_layout(ar, n, A);
-  if (!b.P || !b.roots) return RST_ERR_OOM;
+  if (!b.P || !b.ctl) return RST_ERR_OOM;
   uint32_t* status = state().status;
   unsigned long long* cnt = dev_counter(0);
   RST_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
   RST_CUDA(cudaMemsetAsync(b.bits, 0, (A / 32 + 2) * sizeof(uint32_t), s));
+  RST_CUDA(cudaMemsetAsync(b.ctl, 0, sizeof(CcCtl), s));
 
   const int gN = grid_for(n);
   prof_mark(s, "cc_setup");
@@ -521,94 +667,82 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
     RST_LAUNCH(k_build_list<OffT>, g, kMpThreads, 0, s)(off, n, A, f);
   }
   prof_mark(s, "k_build_list");
+  CcPtrs p;
+  p.col = col;
+  for (int k = 0; k < 2; ++k) {
+    p.Ecu[k] = b.Ecu[k];
+    p.Ecv[k] = b.Ecv[k];
+    p.Ep[k] = b.Ep[k];
+    p.best[k] = b.best[k];
+  }
+  p.P2 = b.P2;
+  p.NID = b.NID;
+  p.nextpool = b.nextpool;
+  p.minvpool = b.minvpool;
+  p.pairs = b.pairs;
+  p.bits = b.bits;
+  p.roots = b.roots;
+  p.ctl = b.ctl;
+  p.counters = cnt;
+  p.status = status;
+  p.ecap = b.ecap;
+  RST_LAUNCH(k_round_init, grid_for(n / 2 + 1), kBlock, 0, s)(p, root, b.C1);
+  prof_mark(s, "k_round_init");
   RST_CUDA(cudaGetLastError());
+
+  // Contraction rounds: one graph launch (a device-side while loop), or,
+  // when this call must not allocate (no graph objects) or RST_EAGER is set,
+  // a host loop that reads the component count after every round.
+  static const bool eager_env = getenv("RST_EAGER") != nullptr;
+  const bool eager = eager_env || state_overridden();
+  if (!eager) {
+    cudaGraphExec_t exec = nullptr;
+    RST_TRY(round_graph_for<OffT>(p, off, n, A, &exec));
+    RST_CUDA(cudaGraphLaunch(exec, s));
+  } else {
+    for (int r = 0; r < kMaxRounds; ++r) {
+      launch_round_body<OffT>(p, off, cudaGraphConditionalHandle{}, 0, s);
+      RST_CUDA(cudaGetLastError());
+      unsigned long long c = 0;
+      RST_TRY(fetch_u64(&b.ctl->st[r + 1].C, 1, &c, s));
+      if (c == 0) break;
+    }
+  }
+  prof_mark(s, "cc_rounds");
+
+  // one read of the round control: counts for the Euler stage and labels
+  CcCtl* hctl = reinterpret_cast<CcCtl*>(host_scratch(sizeof(CcCtl)));
+  if (!hctl) return RST_ERR_OOM;
+  RST_CUDA(cudaMemcpyAsync(hctl, b.ctl, sizeof(CcCtl), cudaMemcpyDeviceToHost, s));
   unsigned long long h[8];
   RST_TRY(fetch_u64(cnt, 8, h, s));
-  prof_mark(s, "cc_sync");
-  int64_t C = (int64_t)h[CNT_COMPS];
-  int64_t E = (int64_t)h[CNT_LIST];
-  set_stat(STAT_C1, C);
-  set_stat(STAT_E2, E);
-  if (E > b.ecap) return RST_ERR_DEVICE;
-
-  RoundTable rt{};
-  int64_t pool_at = 0;  // start of the current round's slice in next/minv pools
-  int cur = 0;
-  int rounds = 1;
-  while (C > 0) {
-    if (rt.nrounds >= kMaxRounds) return RST_ERR_NOT_CONVERGED;
-    int32_t* minv = b.minvpool + pool_at;
-    int32_t* next = b.nextpool + pool_at;
-    rt.base[rt.nrounds++] = pool_at;
-    const int gC = grid_for(C);
-    if (E == 0) {
-      RST_LAUNCH(k_all_final, gC, kBlock, 0, s)(C, minv, next, b.roots, cnt);
-      RST_CUDA(cudaGetLastError());
-      pool_at += C;
-      break;
-    }
-    ++rounds;
-    const int gE = grid_for(E);
-    RST_LAUNCH(k_fill_u64, gC, kBlock, 0, s)(b.best, C, ~0ull);
-    RST_LAUNCH(k_hook, gE, kBlock, 0, s)(E, b.Ecu[cur], b.Ecv[cur], b.Ep[cur], b.best);
-    RST_LAUNCH(k_resolve<OffT>, gC, kBlock, 0, s)(off, col, C, b.best, b.P2, b.pairs, b.bits, cnt, status);
-    RST_LAUNCH(k_compress, gC, kBlock, 0, s)(C, b.P2, status);
-    RST_CUDA(cudaMemsetAsync(&cnt[CNT_NEXT], 0, sizeof(unsigned long long), s));
-    RST_LAUNCH(k_renumber, gC, kBlock, 0, s)(C, b.P2, b.best, minv, b.NID, b.roots, cnt);
-    RST_CUDA(cudaGetLastError());
-    RST_TRY(fetch_u64(cnt, 8, h, s));
-    const int64_t Cn = (int64_t)h[CNT_NEXT];
-    int32_t* minv_next = b.minvpool + pool_at + C;
-    if (pool_at + C + Cn > n + 1) return RST_ERR_DEVICE;
-    RST_LAUNCH(k_fill_i32, grid_for(Cn), kBlock, 0, s)(minv_next, Cn, INT_MAX);
-    RST_LAUNCH(k_map, gC, kBlock, 0, s)(C, b.P2, b.best, b.NID, minv, next, minv_next);
-    RST_CUDA(cudaMemsetAsync(&cnt[CNT_LIST], 0, sizeof(unsigned long long), s));
-    RST_LAUNCH(k_relabel, gE, kBlock, 0, s)(E, b.Ecu[cur], b.Ecv[cur], b.Ep[cur], next, b.Ecu[cur ^ 1],
-                                    b.Ecv[cur ^ 1], b.Ep[cur ^ 1], &cnt[CNT_LIST]);
-    RST_CUDA(cudaGetLastError());
-    RST_TRY(fetch_u64(cnt, 8, h, s));
-    E = (int64_t)h[CNT_LIST];
-    pool_at += C;
-    C = Cn;
-    cur ^= 1;
-  }
-
-  prof_mark(s, "cc_rounds");
-  // labels
+  const int rounds_done = hctl->cur;
   if (labels_out) {
-    for (int r = rt.nrounds - 2; r >= 0; --r) {
-      const int64_t Cr = rt.base[r + 1] - rt.base[r];
-      RST_LAUNCH(k_label_back, grid_for(Cr), kBlock, 0, s)(Cr, b.nextpool + rt.base[r],
-                                                   b.minvpool + rt.base[r],
-                                                   b.minvpool + rt.base[r + 1]);
+    for (int r = rounds_done - 2; r >= 0; --r) {
+      const int64_t Cr = (int64_t)hctl->st[r].C;
+      if (Cr == 0) continue;
+      const int64_t base = (int64_t)hctl->st[r].pool_at;
+      const int64_t nbase = (int64_t)hctl->st[r + 1].pool_at;
+      RST_LAUNCH(k_label_back, grid_for(Cr), kBlock, 0, s)(Cr, b.nextpool + base, b.minvpool + base,
+                                                          b.minvpool + nbase);
     }
     RST_LAUNCH(k_label_vertices, gN, kBlock, 0, s)(n, b.C1, b.minvpool, labels_out);
     RST_CUDA(cudaGetLastError());
   }
-  out->root_label = -1;
-  if (root >= 0) {
-    if (labels_out) {
-      // the backward pass overwrote minv with labels; read the root's label
-      RST_CUDA(cudaMemcpyAsync(&cnt[CNT_ROOTLABEL], labels_out + root, sizeof(int32_t),
-                               cudaMemcpyDeviceToDevice, s));
-      RST_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(&cnt[CNT_ROOTLABEL]) + 4, 0, 4, s));
-    } else {
-      RST_LAUNCH(k_root_label, 1, 32, 0, s)(root, b.C1, b.nextpool, b.minvpool, rt, cnt);
-      RST_CUDA(cudaGetLastError());
-    }
-  }
-  RST_TRY(fetch_u64(cnt, 8, h, s));
   prof_mark(s, "cc_finish");
+  set_stat(STAT_C1, (long long)hctl->st[0].C);
+  set_stat(STAT_E2, (long long)hctl->st[0].E);
+  if ((int64_t)h[CNT_LIST] > b.ecap) return RST_ERR_DEVICE;
   out->T = (int64_t)h[CNT_PAIRS];
   out->pairs = b.pairs;
   out->bits = b.bits;
   out->nroots = (int64_t)h[CNT_ROOTS];
   out->roots = b.roots;
-  out->rounds = rounds;
-  set_stat(STAT_ROUNDS, rounds);
+  out->rounds = rounds_done + 1;
+  out->root_label = root >= 0 ? hctl->root_label : -1;
+  set_stat(STAT_ROUNDS, out->rounds);
   set_stat(STAT_T, out->T);
   set_stat(STAT_NROOTS, out->nroots);
-  if (root >= 0) out->root_label = (int32_t)(uint32_t)h[CNT_ROOTLABEL];
   return RST_OK;
 }
 

@@ -115,6 +115,9 @@ struct DeviceState {
 // thread with set_state_override; state() then returns it.
 DeviceState& state();
 void set_state_override(DeviceState* st);
+bool state_overridden();
+// Host scratch for small device->host reads (static storage, calls are serialised).
+void* host_scratch(size_t bytes);
 std::mutex& call_lock();
 rst_status ensure_workspace(size_t bytes);
 

@@ -39,6 +39,8 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
                   int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s);
 template <class OffT>
 size_t cc_workspace_bytes(int64_t n, int64_t A);
+// Release cached round graphs (rst_shutdown).
+void destroy_round_graphs();
 
 // ----------------------------------------------------------------- Euler
 struct EulerIn {

@@ -16,6 +16,10 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
 
 static thread_local DeviceState* g_state_override = nullptr;
 void set_state_override(DeviceState* st) { g_state_override = st; }
+bool state_overridden() { return g_state_override != nullptr; }
+
+alignas(64) static unsigned char g_host_scratch[1 << 16];
+void* host_scratch(size_t bytes) { return bytes <= sizeof(g_host_scratch) ? g_host_scratch : nullptr; }
 
 static std::atomic<long long> g_launches{0};
 static long long g_stats[STAT_COUNT] = {0};
