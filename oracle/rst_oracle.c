@@ -385,3 +385,97 @@ int or_verify(int64_t n, const int64_t *off, const int32_t *col, int32_t root,
     free(tr); free(path); free(state);
     return verdict;
 }
+
+/* ---------------------------------------------------------------- PR-RST */
+
+/* rep[v] = root of v's tree in P, for all v, in O(n): walk up to the first
+ * vertex whose root is known, then write the root along the walked path. */
+static void tree_roots(int64_t n, const int32_t *P, int32_t *rep, int32_t *stack) {
+    for (int64_t v = 0; v < n; ++v) rep[v] = -1;
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t sp = 0;
+        int32_t x = (int32_t)v;
+        while (rep[x] < 0 && P[x] != x) { stack[sp++] = x; x = P[x]; }
+        int32_t r = rep[x] >= 0 ? rep[x] : x;
+        rep[x] = r;
+        while (sp) rep[stack[--sp]] = r;
+    }
+}
+
+/* Re-root the tree of P holding u at u and graft it under v (v == u: u just
+ * becomes the root).  Path reversal (Section III-C): along the tree path
+ * u = x0, x1 = P[x0], ..., xk = old root, every x_{i+1} takes x_i as parent;
+ * the path is read from P (the state at the start of the round) and written
+ * into Q. */
+static void reverse_and_graft(const int32_t *P, int32_t *Q, int32_t u, int32_t v) {
+    int32_t x = u;
+    while (P[x] != x) { Q[P[x]] = x; x = P[x]; }
+    Q[u] = v;
+}
+
+/*
+ * PR-RST (Section III-C), simulated round by round.  Rooted forest P, every
+ * vertex its own tree at the start.  Round t (t = 0, 1, ...) hooks with the
+ * minimum rule when t is even and the maximum rule when t is odd: an arc
+ * (u, v) whose trees have roots ru != rv is eligible for the tree ru when
+ * rv < ru (minimum rule) or rv > ru (maximum rule), and each tree takes its
+ * eligible arc with the smallest key (u, v).  A hooking tree is re-rooted at
+ * u by path reversal and grafted under v.  The loop ends after the first
+ * round without hooks.  Finally the tree of `root` is re-rooted at root and
+ * every other tree at its minimum vertex id.
+ *   rounds_out: number of rounds executed (the final hook-free one included)
+ * Returns 0, -1 for a bad root or id.
+ */
+int or_prrst(int64_t n, const int64_t *off, const int32_t *col, int32_t root,
+             int32_t *parent_out, int64_t *rounds_out) {
+    if (n <= 0) { *rounds_out = 0; return 0; }
+    if (root < 0 || root >= n) return -1;
+    int32_t *P = parent_out;
+    int32_t *Q = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *rep = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *stk = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    uint64_t *best = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    if (!Q || !rep || !best || !stk) { free(Q); free(rep); free(best); free(stk); return -3; }
+    for (int64_t v = 0; v < n; ++v) P[v] = (int32_t)v;
+    int64_t t = 0;
+    for (;; ++t) {
+        tree_roots(n, P, rep, stk);
+        for (int64_t v = 0; v < n; ++v) best[v] = UINT64_MAX;
+        for (int64_t u = 0; u < n; ++u) {
+            for (int64_t j = off[u]; j < off[u + 1]; ++j) {
+                int32_t v = col[j];
+                if (v < 0 || v >= n) { free(Q); free(rep); free(best); free(stk); return -1; }
+                int32_t ru = rep[u], rv = rep[v];
+                if (ru == rv) continue;
+                int eligible = (t % 2 == 0) ? (rv < ru) : (rv > ru);
+                if (!eligible) continue;
+                uint64_t key = ((uint64_t)(uint32_t)u << 32) | (uint32_t)v;
+                if (key < best[ru]) best[ru] = key;
+            }
+        }
+        int any = 0;
+        memcpy(Q, P, (size_t)n * sizeof(int32_t));
+        for (int64_t r = 0; r < n; ++r) {
+            if (rep[r] != r || best[r] == UINT64_MAX) continue;
+            any = 1;
+            reverse_and_graft(P, Q, (int32_t)(best[r] >> 32), (int32_t)(best[r] & 0xffffffffu));
+        }
+        memcpy(P, Q, (size_t)n * sizeof(int32_t));
+        if (!any) break;
+    }
+    /* final re-rooting */
+    tree_roots(n, P, rep, stk);
+    int32_t *minv = (int32_t *)best;   /* reuse storage: n int32 fit in n uint64 */
+    for (int64_t v = 0; v < n; ++v) minv[v] = INT32_MAX;
+    for (int64_t v = 0; v < n; ++v) if (v < minv[rep[v]]) minv[rep[v]] = (int32_t)v;
+    memcpy(Q, P, (size_t)n * sizeof(int32_t));
+    for (int64_t r = 0; r < n; ++r) {
+        if (rep[r] != r) continue;
+        int32_t target = (r == rep[root]) ? root : minv[r];
+        if (target != r) reverse_and_graft(P, Q, target, target);
+    }
+    memcpy(P, Q, (size_t)n * sizeof(int32_t));
+    *rounds_out = t + 1;
+    free(Q); free(rep); free(best); free(stk);
+    return 0;
+}

@@ -66,6 +66,7 @@ struct CcBuffers {
   uint32_t* bits;    // A/32 + 1
   int32_t* roots;    // n/2+1
   struct CcCtl* ctl; // device-resident round control
+  int32_t* tile_row; // row of the first arc of every arc tile
   int64_t ecap;      // list capacity
 };
 
@@ -92,6 +93,7 @@ static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
   b.bits = ar.take<uint32_t>(A / 32 + 2);
   b.roots = ar.take<int32_t>(half);
   b.ctl = ar.take<CcCtl>(1);
+  b.tile_row = ar.take<int32_t>(A / kArcTile + 2);
   return b;
 }
 
@@ -218,59 +220,64 @@ __global__ void k_r1_label(int64_t n, const int32_t* __restrict__ P, const uint3
 
 // The inter-component edges after round 1: every arc u->v with u < v whose
 // endpoints lie in different round-1 components, as {C1[u], C1[v], position}.
+// Arc-centric tiles: coalesced column loads, rows from a shared-memory scan,
+// independent label gathers, one slot reservation per tile.
 template <class OffT>
-struct BuildListFn {
-  const int32_t* __restrict__ col;
-  const int32_t* __restrict__ C1;
-  int64_t n;
-  int32_t* __restrict__ Ecu;
-  int32_t* __restrict__ Ecv;
-  uint32_t* __restrict__ Ep;
-  unsigned long long* counter;
-  int64_t cap;
-  uint32_t* status;
-  // per-thread staging of one tile's kept entries (registers after unrolling)
-  int32_t bu[kMpItems], bv[kMpItems];
-  uint32_t bp[kMpItems];
-  uint32_t mask;
-  __device__ __forceinline__ void operator()(int it, bool is_arc, int64_t row, int64_t arc) {
-    if (it == 0) mask = 0;
-    if (is_arc) {
-      const int32_t v = col[arc];
-      if (v < 0 || (int64_t)v >= n) {
-        raise_error(status, DERR_INDEX);
-      } else if (v > (int32_t)row) {
-        const int32_t cu = C1[row];
-        const int32_t cv = C1[v];
-        bu[it] = cu;
-        bv[it] = cv;
-        bp[it] = (uint32_t)arc;
-        if (cu != cv) mask |= 1u << it;
+__global__ void __launch_bounds__(kArcThreads) k_build_list(const OffT* __restrict__ off,
+                                                            const int32_t* __restrict__ col,
+                                                            int64_t n, int64_t A,
+                                                            const int32_t* __restrict__ C1,
+                                                            int32_t* __restrict__ Ecu,
+                                                            int32_t* __restrict__ Ecv,
+                                                            uint32_t* __restrict__ Ep,
+                                                            unsigned long long* counter, int64_t cap,
+                                                            const int32_t* __restrict__ tile_row,
+                                                            uint32_t* status) {
+  __shared__ int32_t s_row[kArcTile];
+  for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
+    const int cnt = (int)(A - a0 < kArcTile ? A - a0 : kArcTile);
+    const int64_t t = a0 / kArcTile;
+    arc_tile_rows(off, n, a0, cnt, s_row, tile_row[t], tile_row[t + 1]);
+    int32_t bu[kArcPer], bv[kArcPer];
+    uint32_t bp[kArcPer];
+    uint32_t mask = 0;
+#pragma unroll
+    for (int k = 0; k < kArcPer; ++k) {
+      const int i = k * kArcThreads + threadIdx.x;
+      bu[k] = 0;
+      bv[k] = 0;
+      bp[k] = 0;
+      if (i < cnt) {
+        const int32_t v = col[a0 + i];
+        const int32_t u = s_row[i];
+        if (v < 0 || (int64_t)v >= n) {
+          raise_error(status, DERR_INDEX);
+        } else if (v > u) {
+          const int32_t cu = C1[u];
+          const int32_t cv = C1[v];
+          bu[k] = cu;
+          bv[k] = cv;
+          bp[k] = (uint32_t)(a0 + i);
+          if (cu != cv) mask |= 1u << k;
+        }
       }
     }
-  }
-  __device__ __forceinline__ void end_tile() {
-    unsigned long long slot = block_reserve<kMpThreads>(counter, (unsigned)__popc(mask));
+    unsigned long long slot = block_reserve<kArcThreads>(counter, (unsigned)__popc(mask));
 #pragma unroll
-    for (int it = 0; it < kMpItems; ++it) {
-      if (mask & (1u << it)) {
+    for (int k = 0; k < kArcPer; ++k) {
+      if (mask & (1u << k)) {
         if ((int64_t)slot < cap) {
-          Ecu[slot] = bu[it];
-          Ecv[slot] = bv[it];
-          Ep[slot] = bp[it];
+          Ecu[slot] = bu[k];
+          Ecv[slot] = bv[k];
+          Ep[slot] = bp[k];
         } else {
           raise_error(status, DERR_CAPACITY);
         }
         ++slot;
       }
     }
+    __syncthreads();
   }
-};
-
-template <class OffT>
-__global__ void __launch_bounds__(kMpThreads) k_build_list(const OffT* __restrict__ off, int64_t n,
-                                                           int64_t A, BuildListFn<OffT> f) {
-  csr_for_each_arc(off, n, A, f);
 }
 
 // ------------------------------------------------------------------ rounds >= 2
@@ -659,12 +666,14 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   prof_mark(s, "k_r1_number");
   RST_LAUNCH(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.CID, b.C1);
   prof_mark(s, "k_r1_label");
-  {
-    BuildListFn<OffT> f{col, b.C1, n, b.Ecu[0], b.Ecv[0], b.Ep[0], &cnt[CNT_LIST], b.ecap, status};
-    const int64_t tiles = (n + A + kMpTile - 1) / kMpTile;
-    const int g = (int)(tiles < (int64_t)device_info().sms * 8 ? (tiles > 0 ? tiles : 1)
-                                                                : (int64_t)device_info().sms * 8);
-    RST_LAUNCH(k_build_list<OffT>, g, kMpThreads, 0, s)(off, n, A, f);
+  if (A > 0) {
+    // one tile per block: the row searches of many resident blocks overlap
+    const int64_t tiles = (A + kArcTile - 1) / kArcTile;
+    const unsigned g = (unsigned)tiles;
+    RST_LAUNCH(k_arc_tile_rows<OffT>, grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
+    RST_LAUNCH(k_build_list<OffT>, g, kArcThreads, 0, s)(off, col, n, A, b.C1, b.Ecu[0], b.Ecv[0],
+                                                         b.Ep[0], &cnt[CNT_LIST], b.ecap, b.tile_row,
+                                                         status);
   }
   prof_mark(s, "k_build_list");
   CcPtrs p;

@@ -87,6 +87,85 @@ __device__ __forceinline__ void csr_for_each_arc(const OffT* __restrict__ off, i
   }
 }
 
+// ------------------------------------------------------------------ arc tiles
+// Arc-centric traversal: a block takes kArcTile consecutive arc positions and
+// learns the row of every arc from one shared-memory max-scan (each row that
+// starts inside the tile marks its first position; the running maximum of the
+// marks is the row).  Threads then read arcs with fully coalesced loads and
+// independent gathers, which suits the light rows of meshes and the heavy rows
+// of power-law graphs alike.
+constexpr int kArcThreads = 256;
+constexpr int kArcPer = 8;
+constexpr int kArcTile = kArcThreads * kArcPer;
+
+// Last row r in [0, n) with off[r] <= a (the row holding arc a).
+template <class OffT>
+__device__ __forceinline__ int64_t row_of_arc(const OffT* __restrict__ off, int64_t n, int64_t a) {
+  int64_t lo = 0, hi = n;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)off[mid] <= a)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// tile_row[t] = row holding arc t * kArcTile (t <= tiles; the last entry is
+// n - 1 or the row of the last arc).  One thread per tile, all in parallel.
+template <class OffT>
+__global__ void k_arc_tile_rows(const OffT* __restrict__ off, int64_t n, int64_t A, int64_t tiles,
+                                int32_t* __restrict__ tile_row) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t * kArcTile < A ? t * kArcTile : A - 1;
+    tile_row[t] = (int32_t)row_of_arc(off, n, a < 0 ? 0 : a);
+  }
+}
+
+// Fills s_row[i] with the row of arc a0 + i for i < cnt, given r0 = the row
+// of arc a0 and r1 >= the row of arc a0 + cnt - 1 (from k_arc_tile_rows).
+// Call from all threads of a kArcThreads block; ends with __syncthreads().
+template <class OffT>
+__device__ __forceinline__ void arc_tile_rows(const OffT* __restrict__ off, int64_t n, int64_t a0,
+                                              int cnt, int32_t* s_row, int64_t r0, int64_t r1) {
+  __shared__ int32_t s_warp[kArcThreads / 32];
+  for (int i = threadIdx.x; i < kArcTile; i += kArcThreads) s_row[i] = -1;
+  __syncthreads();
+  for (int64_t r = r0 + 1 + threadIdx.x; r <= r1; r += kArcThreads) {
+    const int64_t pos = (int64_t)off[r] - a0;
+    if (pos >= 0 && pos < cnt) atomicMax(&s_row[pos], (int32_t)r);
+  }
+  if (threadIdx.x == 0) atomicMax(&s_row[0], (int32_t)r0);
+  __syncthreads();
+  // inclusive max-scan: kArcPer consecutive entries per thread, then across threads
+  const int base = threadIdx.x * kArcPer;
+  int32_t v[kArcPer];
+  int32_t run = -1;
+#pragma unroll
+  for (int k = 0; k < kArcPer; ++k) {
+    run = max(run, s_row[base + k]);
+    v[k] = run;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t x = run;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x = max(x, y);
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  int32_t carry = -1;
+  for (int w = 0; w < warp; ++w) carry = max(carry, s_warp[w]);
+  const int32_t prev = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane > 0) carry = max(carry, prev);
+#pragma unroll
+  for (int k = 0; k < kArcPer; ++k) s_row[base + k] = max(v[k], carry);
+  __syncthreads();
+}
+
 // Binary search of value w in the sorted row v: position or -1.
 template <class OffT>
 __device__ __forceinline__ int64_t row_find(const OffT* __restrict__ off,

@@ -1,17 +1,266 @@
-// Path-reversal RST (Section III-C).
+// Path-reversal rooted spanning tree, PR-RST (Section III-C).
+//
+// A rooted forest P (every vertex its own tree at the start) is grown by
+// rounds of hooking that alternate a minimum and a maximum rule: an arc (u,v)
+// whose trees have roots ru != rv is eligible for tree ru when rv < ru
+// (minimum rule, even rounds) or rv > ru (maximum rule, odd rounds), so the
+// hooks of a round never form a cycle; each tree takes its eligible arc with
+// the smallest key (u << 32 | v) by one 64-bit atomicMin.  A hooking tree is
+// re-rooted at u by reversing the tree path u -> root and grafted under v.
+//
+// The path is found with the special ancestors of the paper: pointer jumping
+// keeps its history anc[k][x] = 2^k-th ancestor of x (anc[0] = P), and the
+// marks spread from u over the levels k = K-1 .. 0 (x marked => anc[k][x]
+// marked), which reaches every ancestor of u in K passes.  Reversal is one
+// data-parallel pass: every marked x sets Q[P[x]] = x, the bottom vertex u
+// takes Q[u] = v, all other vertices keep P.  The last round has no hook.
+// Finally each tree is re-rooted at the requested root (its tree) or at its
+// minimum vertex id, with the same mark-and-reverse step.
+#include <climits>
+
+#include "csr_walk.cuh"
 #include "pipeline.cuh"
 #include "strategies.cuh"
 
 namespace rst {
 
-rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
-                     int32_t root, int32_t* parent, cudaStream_t s) {
-  (void)off; (void)offsets_bits; (void)cols; (void)n; (void)m; (void)root; (void)parent; (void)s;
-  return RST_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int kPrMaxLevels = 32;
+constexpr int kPrMaxRounds = 256;
+
+__global__ void k_pr_iota(int64_t n, int32_t* __restrict__ P) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    P[v] = (int32_t)v;
 }
 
-rst_strategy select_strategy_host(const void* off, int offsets_bits, const int32_t* cols, int64_t n,
-                                  int64_t m, int32_t root, cudaStream_t s) {
+// One pointer-jumping step with history: up[x] = low[low[x]]; flags a change.
+__global__ void k_pr_jump(int64_t n, const int32_t* __restrict__ low, int32_t* __restrict__ up, int32_t* changed) {
+  bool ch = false;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = low[x];
+    const int32_t b = low[a];
+    up[x] = b;
+    ch = ch || (b != a);
+  }
+  if (__any_sync(0xffffffffu, ch) && (threadIdx.x & 31) == 0) *changed = 1;
+}
+
+__global__ void k_pr_fill_u64(int64_t n, unsigned long long* __restrict__ p) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    p[v] = ~0ull;
+}
+
+// Eligible arcs propose themselves to their tree (arc-centric tiles).
+template <class OffT>
+__global__ void __launch_bounds__(kArcThreads) k_pr_hook(const OffT* __restrict__ off, const int32_t* __restrict__ col,
+                                                         int64_t n, int64_t A, const int32_t* __restrict__ tile_row,
+                                                         const int32_t* __restrict__ rep, int max_rule,
+                                                         unsigned long long* __restrict__ best) {
+  __shared__ int32_t s_row[kArcTile];
+  for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
+    const int cnt = (int)(A - a0 < kArcTile ? A - a0 : kArcTile);
+    const int64_t t = a0 / kArcTile;
+    arc_tile_rows(off, n, a0, cnt, s_row, tile_row[t], tile_row[t + 1]);
+#pragma unroll
+    for (int k = 0; k < kArcPer; ++k) {
+      const int i = k * kArcThreads + threadIdx.x;
+      if (i < cnt) {
+        const int32_t u = s_row[i];
+        const int32_t v = col[a0 + i];
+        const int32_t ru = rep[u], rv = rep[v];
+        if (ru != rv && (max_rule ? rv > ru : rv < ru))
+          atomicMin(&best[ru], ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Hooking roots start their paths: the bottom vertex u is marked and
+// remembers its graft target.
+__global__ void k_pr_start(int64_t n, const int32_t* __restrict__ P, const unsigned long long* __restrict__ best,
+                           uint8_t* __restrict__ mark, int32_t* __restrict__ graft, unsigned long long* hooks) {
+  unsigned long long cnt = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    if (P[r] != (int32_t)r) continue;
+    const unsigned long long b = best[r];
+    if (b == ~0ull) continue;
+    const int32_t u = (int32_t)(b >> 32), v = (int32_t)(b & 0xffffffffull);
+    mark[u] = 1;
+    graft[u] = v;
+    ++cnt;
+  }
+  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(hooks, cnt);
+}
+
+// Marks spread one level: x marked => its 2^k-th ancestor marked.
+__global__ void k_pr_spread(int64_t n, const int32_t* __restrict__ anc, uint8_t* __restrict__ mark) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    if (mark[x]) mark[anc[x]] = 1;
+}
+
+// Q[P[x]] = x for marked non-roots, Q[u] = graft target for path bottoms,
+// Q[x] = P[x] for unmarked vertices.  Clears the marks for the next round.
+__global__ void k_pr_reverse(int64_t n, const int32_t* __restrict__ P, int32_t* __restrict__ Q,
+                             uint8_t* __restrict__ mark, int32_t* __restrict__ graft) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = P[x];
+    if (!mark[x]) {
+      Q[x] = p;
+      continue;
+    }
+    if (p != (int32_t)x) Q[p] = (int32_t)x;
+    const int32_t g = graft[x];
+    if (g >= 0) {
+      Q[x] = g;
+      graft[x] = -1;
+    }
+    mark[x] = 0;
+  }
+}
+
+// Minimum vertex of every tree that does not contain the root.
+__global__ void k_pr_minv(int64_t n, const int32_t* __restrict__ rep, int32_t root_tree, int32_t* __restrict__ mn) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rep[v];
+    if (r != root_tree) atomicMin(&mn[r], (int32_t)v);
+  }
+}
+
+// Final re-rooting targets: root for its tree, the minimum vertex otherwise.
+__global__ void k_pr_targets(int64_t n, const int32_t* __restrict__ P, int32_t root, int32_t root_tree,
+                             const int32_t* __restrict__ mn, uint8_t* __restrict__ mark, int32_t* __restrict__ graft) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    if (P[r] != (int32_t)r) continue;
+    const int32_t t = (r == root_tree) ? root : mn[r];
+    if (t != (int32_t)r) {
+      mark[t] = 1;
+      graft[t] = t;
+    }
+  }
+}
+
+__global__ void k_pr_fill_i32(int64_t n, int32_t* __restrict__ p, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+struct PrBufs {
+  int32_t* anc[kPrMaxLevels];  // anc[0] is P
+  int32_t* Q;
+  unsigned long long* best;
+  uint8_t* mark;
+  int32_t* graft;
+  int32_t* mn;
+  int32_t* tile_row;
+  int32_t* flag;
+  int levels;
+};
+
+// anc[1..K] by pointer jumping until nothing changes; returns K (rep = anc[K]).
+static rst_status pr_history(PrBufs& b, int64_t n, cudaStream_t s, int* K_out) {
+  const int g = grid_for(n);
+  int k = 0;
+  while (true) {
+    if (k + 1 >= b.levels) return RST_ERR_NOT_CONVERGED;
+    RST_CUDA(cudaMemsetAsync(b.flag, 0, sizeof(int32_t), s));
+    RST_LAUNCH(k_pr_jump, g, kBlock, 0, s)(n, b.anc[k], b.anc[k + 1], b.flag);
+    ++k;
+    int32_t changed = 0;
+    RST_CUDA(cudaMemcpyAsync(host_scratch(4), b.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RST_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(&changed, host_scratch(4), sizeof(int32_t));
+    if (!changed) break;
+  }
+  *K_out = k;
+  return RST_OK;
+}
+
+// Spread the marks over levels K-1..0, then reverse into Q and swap P <-> Q.
+static rst_status pr_reverse(PrBufs& b, int64_t n, int K, cudaStream_t s) {
+  const int g = grid_for(n);
+  for (int k = K - 1; k >= 0; --k) RST_LAUNCH(k_pr_spread, g, kBlock, 0, s)(n, b.anc[k], b.mark);
+  RST_LAUNCH(k_pr_reverse, g, kBlock, 0, s)(n, b.anc[0], b.Q, b.mark, b.graft);
+  std::swap(b.anc[0], b.Q);
+  RST_CUDA(cudaGetLastError());
+  return RST_OK;
+}
+
+template <class OffT>
+rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root, int32_t* parent,
+                      cudaStream_t s) {
+  int levels = 2;
+  while (((int64_t)1 << (levels - 2)) < n + 1 && levels < kPrMaxLevels) ++levels;
+  const int64_t tiles = (A + kArcTile - 1) / kArcTile;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256 + 256; };
+  const size_t ws = al(n * 4) * (levels + 1) + al(n * 8) + al(n) + al(n * 4) * 2 + al((tiles + 2) * 4) + 256;
+  RST_TRY(ensure_workspace(ws));
+  RST_TRY(reset_device_error(s));
+  DeviceState& st = state();
+  Arena ar{st.ws, st.ws_cap, 0, false};
+  PrBufs b{};
+  b.levels = levels;
+  for (int k = 0; k < levels; ++k) b.anc[k] = ar.take<int32_t>(n);
+  b.Q = ar.take<int32_t>(n);
+  b.best = ar.take<unsigned long long>(n);
+  b.mark = ar.take<uint8_t>(n);
+  b.graft = ar.take<int32_t>(n);
+  b.mn = ar.take<int32_t>(n);
+  b.tile_row = ar.take<int32_t>(tiles + 2);
+  b.flag = ar.take<int32_t>(1);
+  if (!b.flag) return RST_ERR_OOM;
+  unsigned long long* hooks = dev_counter(0);
+  const int g = grid_for(n);
+  RST_LAUNCH(k_pr_iota, g, kBlock, 0, s)(n, b.anc[0]);
+  RST_CUDA(cudaMemsetAsync(b.mark, 0, n, s));
+  RST_LAUNCH(k_pr_fill_i32, g, kBlock, 0, s)(n, b.graft, -1);
+  if (A > 0)
+    RST_LAUNCH(k_arc_tile_rows<OffT>, grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
+  int round = 0;
+  for (;; ++round) {
+    if (round >= kPrMaxRounds) return RST_ERR_NOT_CONVERGED;
+    int K = 0;
+    RST_TRY(pr_history(b, n, s, &K));
+    const int32_t* rep = b.anc[K];
+    RST_LAUNCH(k_pr_fill_u64, g, kBlock, 0, s)(n, b.best);
+    if (A > 0)
+      RST_LAUNCH(k_pr_hook<OffT>, (unsigned)tiles, kArcThreads, 0, s)(off, col, n, A, b.tile_row, rep, round & 1,
+                                                                    b.best);
+    RST_CUDA(cudaMemsetAsync(hooks, 0, sizeof(unsigned long long), s));
+    RST_LAUNCH(k_pr_start, g, kBlock, 0, s)(n, b.anc[0], b.best, b.mark, b.graft, hooks);
+    unsigned long long h = 0;
+    RST_TRY(fetch_u64(hooks, 1, &h, s));
+    if (h == 0) break;
+    RST_TRY(pr_reverse(b, n, K, s));
+  }
+  // final re-rooting
+  int K = 0;
+  RST_TRY(pr_history(b, n, s, &K));
+  int32_t root_tree = 0;
+  RST_CUDA(cudaMemcpyAsync(host_scratch(4), b.anc[K] + root, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RST_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(&root_tree, host_scratch(4), sizeof(int32_t));
+  RST_LAUNCH(k_pr_fill_i32, g, kBlock, 0, s)(n, b.mn, INT_MAX);
+  RST_LAUNCH(k_pr_minv, g, kBlock, 0, s)(n, b.anc[K], root_tree, b.mn);
+  RST_LAUNCH(k_pr_targets, g, kBlock, 0, s)(n, b.anc[0], root, root_tree, b.mn, b.mark, b.graft);
+  RST_TRY(pr_reverse(b, n, K, s));
+  RST_CUDA(cudaMemcpyAsync(parent, b.anc[0], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  set_stat(STAT_ROUNDS, round + 1);
+  return read_device_error(s);
+}
+
+}  // namespace
+
+rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m, int32_t root,
+                     int32_t* parent, cudaStream_t s) {
+  if (offsets_bits == 32) return prrst_impl<int32_t>((const int32_t*)off, cols, n, m, root, parent, s);
+  return prrst_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, s);
+}
+
+rst_strategy select_strategy_host(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                                  int32_t root, cudaStream_t s) {
   (void)off; (void)offsets_bits; (void)cols; (void)n; (void)m; (void)root; (void)s;
   return RST_CC_EULER;
 }

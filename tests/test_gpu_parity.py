@@ -223,3 +223,26 @@ def test_rmat24_cc_euler(rmat24):
     assert np.array_equal(got.cpu().numpy(), want)
     bpar = rst.build(off, col, g.root, "bfs").cpu().numpy()
     assert np.array_equal(bpar, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+
+
+# ------------------------------------------------------------------ PR-RST
+
+@pytest.mark.parametrize("gi", range(N_SMALL))
+def test_prrst_matches_oracle(gi):
+    """Bit-exact against the oracle's round-by-round simulation of the same
+    hooking rule, and a valid RST."""
+    g = _small()[gi]
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    par = rst.build(off, col, g.root, "pr_rst")
+    want, rounds = oracle.prrst(g.n, g.offsets, g.cols, g.root)
+    assert np.array_equal(par.cpu().numpy(), want), g.name
+    assert rst.verify(off, col, g.root, par) == 0
+
+
+@pytest.mark.parametrize("g", edge_cases(), ids=_ids(edge_cases()))
+def test_prrst_edge_cases(g):
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    par = rst.build(off, col, g.root, "pr_rst").cpu().numpy()
+    assert np.array_equal(par, oracle.prrst(g.n, g.offsets, g.cols, g.root)[0])

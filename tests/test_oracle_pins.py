@@ -428,3 +428,34 @@ def test_euler_invariants(gi):
             assert down < up
             assert (up - down + 1) // 2 == size_of(v)
     del sub
+
+
+# ------------------------------------------------------------------ PR-RST
+
+def test_prrst_golden():
+    gold = load_golden("prrst_path4_root3.txt")
+    g = G(4, [(0, 2), (1, 2), (1, 3)], root=3)
+    par, rounds = oracle.prrst(4, g.offsets, g.cols, 3)
+    assert par.tolist() == gold["parent"][0]
+    assert rounds == gold["rounds"][0][0]
+
+
+@pytest.mark.parametrize("gi", range(5))
+def test_prrst_is_a_valid_rst(gi):
+    """PR-RST fixes no unique tree; its output must pass the exact verifier
+    (root rule for other components included) and the round count must stay
+    logarithmic."""
+    g = list(_families())[gi]
+    par, rounds = oracle.prrst(g.n, g.offsets, g.cols, g.root)
+    assert oracle.verify(g.n, g.offsets, g.cols, g.root, par) == oracle.VALID
+    assert rounds <= 4 * int(np.ceil(np.log2(g.n + 1))) + 2
+
+
+def test_prrst_path_and_star():
+    n = 9
+    g = G(n, [(i, i + 1) for i in range(n - 1)], root=4)
+    par, _ = oracle.prrst(n, g.offsets, g.cols, 4)
+    assert par.tolist() == [1, 2, 3, 4, 4, 4, 5, 6, 7]
+    g = G(n, [(0, j) for j in range(1, n)], root=5)
+    par, _ = oracle.prrst(n, g.offsets, g.cols, 5)
+    assert par.tolist() == [5] + [0] * 4 + [5] + [0] * 3
