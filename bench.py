@@ -289,6 +289,22 @@ def run_ours(args, rank, world, local_rank):
     bfs_med = statistics.median(bfs_ms)
     ms_step = total_ms / args.steps
 
+    # PR-RST on the same graph
+    pr_ms = []
+    step("pr_rst")
+    for _ in range(args.bfs_steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step("pr_rst")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pr_ms.append(e0.elapsed_time(e1))
+    pr_med = statistics.median(pr_ms)
+
+    batch = None if args.no_batch else run_batch(args, dev, stream, rst, graphs, torch)
+
     out = None
     if rank == 0:
         cpu = None
@@ -315,10 +331,58 @@ def run_ours(args, rank, world, local_rank):
             "bfs": {"value": g.m / (bfs_med / 1e3), "unit": "edges/s", "ms_per_step": bfs_med,
                     "levels": int(bfs_levels),
                     "cc_euler_speedup": bfs_med / ms_step},
+            "pr_rst": {"value": g.m / (pr_med / 1e3), "unit": "edges/s", "ms_per_step": pr_med,
+                       "cc_euler_speedup": pr_med / ms_step},
+            "batch": batch,
             "stats": st,
             "stage_ms": stage_summary,
         }
     return out
+
+
+def run_batch(args, dev, stream, rst, graphs, torch):
+    """4096 mixed graphs: one rst_build_batch call vs one rst_build call per graph."""
+    b = graphs.workload_batch()
+    off = torch.from_numpy(b.offsets).to(dev)
+    col = torch.from_numpy(b.cols).to(dev)
+    vo = torch.from_numpy(b.vtx_off).to(dev)
+    ao = torch.from_numpy(b.arc_off).to(dev)
+    roots = torch.from_numpy(b.roots).to(dev)
+    par = torch.empty(b.N, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        rst.build_batch(off, col, vo, ao, roots, out=par)
+    times = []
+    for _ in range(max(3, min(args.steps, 10))):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rst.build_batch(off, col, vo, ao, roots, out=par)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    batched = statistics.median(times)
+    # per-graph launches over the same resident data (zero-copy views)
+    views = []
+    for g_i, g in enumerate(b.graphs):
+        o0 = int(b.vtx_off[g_i]) + g_i
+        a0, a1 = int(b.arc_off[g_i]), int(b.arc_off[g_i + 1])
+        views.append((off[o0:o0 + g.n + 1], col[a0:a1], g.root, par[int(b.vtx_off[g_i]):int(b.vtx_off[g_i + 1])]))
+    for o, c, r, p in views[:64]:
+        rst.build(o, c, r, out=p)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for o, c, r, p in views:
+        rst.build(o, c, r, out=p)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    per_graph = e0.elapsed_time(e1)
+    return {"workload": f"{b.G} graphs (grid / chain+chords / R-MAT in turn), n log-uniform 1K-4K, "
+                        f"{b.N} vertices, {b.A} arcs, int32 packed CSR",
+            "graphs": b.G, "m": b.m, "batched_ms": batched, "per_graph_ms": per_graph,
+            "batched_value": b.m / (batched / 1e3), "per_graph_value": b.m / (per_graph / 1e3),
+            "unit": "edges/s", "speedup": per_graph / batched}
 
 
 # ----------------------------------------------------------------- reference arm (the oracle)
@@ -361,6 +425,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bfs-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

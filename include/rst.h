@@ -136,6 +136,30 @@ rst_status rst_euler_root(int64_t n, const int32_t *tree_uv, int64_t num_tree_ed
                           rst_stream_t stream);
 
 /*
+ * rst_build_batch -- rooted spanning trees of many independent graphs in one
+ * call.  The batch is processed as one disjoint union, so fixed per-call and
+ * per-launch costs are paid once per batch instead of once per graph (the
+ * launch cost is what the paper blames for BFS's slowness, Section IV-B).
+ *   Layout (all device memory):
+ *     packed_offsets: the graphs' CSR offset arrays concatenated; graph g's
+ *                     n_g + 1 LOCAL offsets (starting at 0) begin at index
+ *                     graph_vtx_off[g] + g; 32- or 64-bit (offsets_bits).
+ *     packed_cols:    the graphs' column arrays concatenated, LOCAL ids.
+ *     graph_vtx_off, graph_arc_off: num_graphs + 1 int64 each; prefix sums of
+ *                     the graphs' vertex and arc counts.
+ *     roots:          num_graphs int32, local root of each graph.
+ *     parent_out:     graph_vtx_off[num_graphs] int32; parent_out[
+ *                     graph_vtx_off[g] + v] = LOCAL parent of v in graph g.
+ *   strategy: RST_CC_EULER (RST_AUTO maps to it) or RST_BFS (one
+ *   multi-source search from all roots); RST_PR_RST returns
+ *   RST_ERR_UNSUPPORTED.  Each graph's result equals rst_build on that graph.
+ */
+rst_status rst_build_batch(const void *packed_offsets, int offsets_bits, const int32_t *packed_cols,
+                           const int64_t *graph_vtx_off, const int64_t *graph_arc_off,
+                           int32_t num_graphs, const int32_t *roots, rst_strategy strategy,
+                           int32_t *parent_out, rst_stream_t stream);
+
+/*
  * rst_verify -- exact validity check of a parent array (the RST definition of
  * Section I, extended to forests as in Section III-D).
  *   parent:      n int32 (device).

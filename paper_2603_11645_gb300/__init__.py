@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["build", "cc", "euler_root", "verify", "lib", "RstError", "STRATEGIES"]
+__all__ = ["build", "build_batch", "cc", "euler_root", "verify", "lib", "RstError", "STRATEGIES"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librst.so")
@@ -41,6 +41,7 @@ def lib():
         L.rst_cc.argtypes = [P, I, P, I64, I64, P, P, P, P]
         L.rst_euler_root.argtypes = [I64, P, I64, I32, P, P, P]
         L.rst_verify.argtypes = [P, I, P, I64, I64, I32, P, P, P]
+        L.rst_build_batch.argtypes = [P, I, P, P, P, I32, P, I, P, P]
         L.rst_status_string.argtypes = [I]
         L.rst_status_string.restype = ctypes.c_char_p
         L.rst_version.restype = I
@@ -86,6 +87,25 @@ def build(offsets, cols, root: int, strategy: str = "cc_euler", out=None, stream
                            _stream(stream))
     _check("rst_build", code)
     return parent[:n]
+
+
+def build_batch(offsets, cols, vtx_off, arc_off, roots, strategy: str = "cc_euler", out=None, stream=None):
+    """Rooted spanning trees of a packed batch (layout of include/rst.h):
+    returns the packed LOCAL parent array (int32 CUDA tensor)."""
+    import torch
+    for t in (offsets, cols, vtx_off, arc_off, roots):
+        assert t.is_cuda and t.is_contiguous()
+    assert vtx_off.dtype == torch.int64 and arc_off.dtype == torch.int64 and roots.dtype == torch.int32
+    G = roots.numel()
+    N = int(vtx_off[-1].item())
+    bits = 64 if offsets.dtype == torch.int64 else 32
+    parent = out if out is not None else torch.empty(max(N, 1), dtype=torch.int32, device=offsets.device)
+    code = lib().rst_build_batch(ctypes.c_void_p(offsets.data_ptr()), bits, ctypes.c_void_p(cols.data_ptr()),
+                                 ctypes.c_void_p(vtx_off.data_ptr()), ctypes.c_void_p(arc_off.data_ptr()), G,
+                                 ctypes.c_void_p(roots.data_ptr()), STRATEGIES[strategy],
+                                 ctypes.c_void_p(parent.data_ptr()), _stream(stream))
+    _check("rst_build_batch", code)
+    return parent[:N]
 
 
 def cc(offsets, cols, stream=None):

@@ -56,6 +56,26 @@ __global__ void k_bfs_seed(int32_t src, int32_t* __restrict__ level, int32_t* __
   q[0] = src;
 }
 
+// Several sources at once (one per graph of a disjoint union): each unvisited
+// source starts at level 0; already-settled ones (isolated) are skipped.
+__global__ void k_bfs_seed_many(const int32_t* __restrict__ seeds, int64_t ns, int32_t* __restrict__ level,
+                                int32_t* __restrict__ parent, int32_t* __restrict__ q,
+                                unsigned long long* counters) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ns; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool fresh = false;
+    int32_t s = -1;
+    if (i < ns) {
+      s = seeds[i];
+      if (s >= 0) fresh = atomicCAS(&level[s], -1, 0) == -1;
+      if (fresh) parent[s] = s;
+    }
+    const unsigned long long slot = block_reserve<kBlock>(&counters[BC_NEXT], fresh ? 1u : 0u);
+    if (fresh) q[slot] = s;
+  }
+}
+
 // Top-down, one thread per frontier vertex (small maximum degree).
 template <class OffT>
 __global__ void k_bfs_td_thread(const OffT* __restrict__ off, const int32_t* __restrict__ col,
@@ -186,15 +206,17 @@ __global__ void k_bfs_min_unvisited(int64_t n, const int32_t* __restrict__ level
   if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&counters[BC_MINUNV], best);
 }
 
-template <class OffT>
-static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
-                           int32_t* parent, int32_t* level_out, cudaStream_t s) {
+size_t bfs_workspace_bytes(int64_t n) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256 + 256; };
-  const size_t ws = al(n * 4) * 3 + al((n + 1) * 8) + al(scan_tmp_words(n + 1) * 8);
-  RST_TRY(ensure_workspace(ws));
-  RST_TRY(reset_device_error(s));
+  return al(n * 4) * 3 + al((n + 1) * 8) + al(scan_tmp_words(n + 1) * 8);
+}
+
+// The search itself; buffers come from `ar` (sized by bfs_workspace_bytes).
+template <class OffT>
+static rst_status bfs_core(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
+                           const int32_t* seeds, int64_t nseeds, int32_t* parent, int32_t* level_out,
+                           cudaStream_t s) {
   DeviceState& st = state();
-  Arena ar{st.ws, st.ws_cap, 0, false};
   int32_t* level = level_out ? level_out : ar.take<int32_t>(n);
   int32_t* qa = ar.take<int32_t>(n);
   int32_t* qb = ar.take<int32_t>(n);
@@ -209,16 +231,23 @@ static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64
   RST_TRY(fetch_u64(cnt, 8, h, s));
   const int64_t maxdeg = (int64_t)h[BC_MAXDEG];
   const bool thread_td = maxdeg <= 64;
-  int32_t src = root;
+  int32_t src = seeds ? -2 : root;  // -2: the multi-source first search
   int64_t levels_total = 0;
-  while (src >= 0) {
-    int32_t probe_level = 0;
-    RST_CUDA(cudaMemcpyAsync(st.hostbuf, level + src, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RST_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(&probe_level, st.hostbuf, sizeof(int32_t));
-    if (probe_level == -1) {
-      RST_LAUNCH(k_bfs_seed, 1, 1, 0, s)(src, level, parent, qa);
-      int64_t nf = 1;
+  while (src >= 0 || src == -2) {
+    int32_t probe_level = -1;
+    int64_t nf = 1;
+    if (src == -2) {
+      RST_CUDA(cudaMemsetAsync(&cnt[BC_NEXT], 0, sizeof(unsigned long long), s));
+      RST_LAUNCH(k_bfs_seed_many, grid_for(nseeds), kBlock, 0, s)(seeds, nseeds, level, parent, qa, cnt);
+      RST_TRY(fetch_u64(&cnt[BC_NEXT], 1, h, s));
+      nf = (int64_t)h[0];
+    } else {
+      RST_CUDA(cudaMemcpyAsync(st.hostbuf, level + src, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      RST_CUDA(cudaStreamSynchronize(s));
+      std::memcpy(&probe_level, st.hostbuf, sizeof(int32_t));
+      if (probe_level == -1) RST_LAUNCH(k_bfs_seed, 1, 1, 0, s)(src, level, parent, qa);
+    }
+    if (probe_level == -1 && nf > 0) {
       int32_t L = 0;
       bool bottom_up = false;
       int32_t* q = qa;
@@ -263,7 +292,18 @@ static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64
     RST_TRY(fetch_u64(&cnt[BC_MINUNV], 1, h, s));
     src = h[0] == ~0ull ? -1 : (int32_t)h[0];
   }
-  (void)levels_total;
+  set_stat(STAT_LEVELS, levels_total);
+  return RST_OK;
+}
+
+template <class OffT>
+static rst_status bfs_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
+                           int32_t* parent, int32_t* level_out, cudaStream_t s) {
+  RST_TRY(ensure_workspace(bfs_workspace_bytes(n)));
+  RST_TRY(reset_device_error(s));
+  DeviceState& st = state();
+  Arena ar{st.ws, st.ws_cap, 0, false};
+  RST_TRY(bfs_core<OffT>(ar, off, col, n, A, root, nullptr, 0, parent, level_out, s));
   return read_device_error(s);
 }
 
@@ -271,6 +311,13 @@ rst_status run_bfs(const void* off, int offsets_bits, const int32_t* cols, int64
                    int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s) {
   if (offsets_bits == 32) return bfs_impl<int32_t>((const int32_t*)off, cols, n, m, root, parent, level_out, s);
   return bfs_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, level_out, s);
+}
+
+rst_status bfs_multi_in(Arena& ar, const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                        const int32_t* seeds, int64_t nseeds, int32_t* parent, cudaStream_t s) {
+  if (offsets_bits == 32)
+    return bfs_core<int32_t>(ar, (const int32_t*)off, cols, n, m, -1, seeds, nseeds, parent, nullptr, s);
+  return bfs_core<int64_t>(ar, (const int64_t*)off, cols, n, m, -1, seeds, nseeds, parent, nullptr, s);
 }
 
 }  // namespace rst

@@ -39,14 +39,23 @@ static size_t euler_core_bytes(int64_t T) {
 
 // ----------------------------------------------------------------- CSR-bitmap front end
 
-__global__ void k_mark_roots(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
-                             int32_t root, uint8_t* __restrict__ is_root) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    int32_t r = roots[k];
-    if (r == root_label) r = root;
-    is_root[r] = 1;
+// Tree root of the component with canonical label L: the requested root of
+// that component, else L (its minimum vertex).
+__device__ __forceinline__ int32_t tree_root_for(int32_t L, int32_t root_label, int32_t root,
+                                                 const int32_t* __restrict__ rootof) {
+  if (rootof) {
+    const int32_t r = rootof[L];
+    return r >= 0 ? r : L;
   }
+  return L == root_label ? root : L;
+}
+
+__global__ void k_mark_roots(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
+                             int32_t root, const int32_t* __restrict__ rootof,
+                             uint8_t* __restrict__ is_root) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
+       k += (int64_t)gridDim.x * blockDim.x)
+    is_root[tree_root_for(roots[k], root_label, root, rootof)] = 1;
 }
 
 template <class OffT>
@@ -65,13 +74,11 @@ __global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint32_t* 
 }
 
 __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
-                        int32_t root, const uint32_t* __restrict__ toff, int32_t* __restrict__ heads) {
+                        int32_t root, const int32_t* __restrict__ rootof,
+                        const uint32_t* __restrict__ toff, int32_t* __restrict__ heads) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    int32_t r = roots[k];
-    if (r == root_label) r = root;
-    heads[k] = (int32_t)toff[r];
-  }
+       k += (int64_t)gridDim.x * blockDim.x)
+    heads[k] = (int32_t)toff[tree_root_for(roots[k], root_label, root, rootof)];
 }
 
 // {p, q, a, b} (CSR positions) -> {i, k, a, b} (tree positions), in place,
@@ -120,13 +127,13 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   RST_CUDA(cudaMemsetAsync(is_root, 0, n, s));
   if (cc->nroots > 0)
     RST_LAUNCH(k_mark_roots, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label,
-                                                         root, is_root);
+                                                         root, cc->rootof, is_root);
   prof_mark(s, "eu_roots");
   RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, cc->bits, wpre, is_root, toff, parent_out);
   prof_mark(s, "k_toff");
   if (cc->nroots > 0)
     RST_LAUNCH(k_heads, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label, root,
-                                                    toff, heads);
+                                                    cc->rootof, toff, heads);
   RST_CUDA(cudaGetLastError());
   const int64_t T = cc->T;
   if (T <= 0) return RST_OK;

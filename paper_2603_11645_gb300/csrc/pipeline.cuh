@@ -27,6 +27,10 @@ struct CcOut {
   int32_t* roots = nullptr;  // their minimum vertex ids (canonical labels)
   int rounds = 0;            // hooking rounds executed (round 1 included)
   int32_t root_label = -1;   // canonical label of the requested root (host value)
+  // Several requested roots (disjoint-union batches): rootof[L] is the root
+  // requested for the component whose canonical label is L, or -1.  When set
+  // it replaces root / root_label.
+  const int32_t* rootof = nullptr;
 };
 
 struct CcPlan;  // workspace layout, defined in cc.cu

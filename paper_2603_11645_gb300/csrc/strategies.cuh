@@ -10,6 +10,12 @@ namespace rst {
 rst_status run_bfs(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                    int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s);
 
+// BFS from several sources at once (the roots of a disjoint union), with
+// buffers taken from the caller's arena (bfs_workspace_bytes(n) of room).
+size_t bfs_workspace_bytes(int64_t n);
+rst_status bfs_multi_in(Arena& ar, const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                        const int32_t* seeds, int64_t nseeds, int32_t* parent, cudaStream_t s);
+
 // Path-reversal RST (Section III-C).
 rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                      int32_t root, int32_t* parent, cudaStream_t s);

@@ -252,11 +252,12 @@ def workload_rmat24(seed: int = 3) -> Graph:
 
 @dataclass
 class Batch:
-    """Disjoint graphs packed into one CSR.
+    """Disjoint graphs packed for rst_build_batch.
 
-    offsets: global row offsets over the union (length N+1, int32 or int64);
-    cols: LOCAL (per-graph) column ids; vtx_off / arc_off: int64 tables of
-    length G+1; roots: local root id per graph.
+    offsets: the graphs' LOCAL offset arrays concatenated (graph g's n_g + 1
+    entries start at vtx_off[g] + g); cols: the graphs' LOCAL column arrays
+    concatenated; vtx_off / arc_off: int64 prefix sums of vertex and arc
+    counts (length G+1); roots: local root of each graph.
     """
 
     graphs: list
@@ -267,6 +268,10 @@ class Batch:
     roots: np.ndarray
 
     @property
+    def G(self) -> int:
+        return len(self.graphs)
+
+    @property
     def N(self) -> int:
         return int(self.vtx_off[-1])
 
@@ -274,8 +279,23 @@ class Batch:
     def A(self) -> int:
         return int(self.arc_off[-1])
 
+    @property
+    def m(self) -> int:
+        return self.A // 2
 
-def pack_batch(graphs, offsets_bits: int | None = None) -> Batch:
+    @property
+    def offsets_bits(self) -> int:
+        return 64 if self.offsets.dtype == np.int64 else 32
+
+    def graph_offsets(self, g: int) -> np.ndarray:
+        v0 = int(self.vtx_off[g]) + g
+        return self.offsets[v0:v0 + self.graphs[g].n + 1]
+
+    def graph_cols(self, g: int) -> np.ndarray:
+        return self.cols[int(self.arc_off[g]):int(self.arc_off[g + 1])]
+
+
+def pack_batch(graphs, offsets_bits: int = 32) -> Batch:
     G = len(graphs)
     vtx_off = np.zeros(G + 1, dtype=np.int64)
     arc_off = np.zeros(G + 1, dtype=np.int64)
@@ -283,16 +303,13 @@ def pack_batch(graphs, offsets_bits: int | None = None) -> Batch:
         vtx_off[i + 1] = vtx_off[i] + g.n
         arc_off[i + 1] = arc_off[i] + g.A
     N, A = int(vtx_off[-1]), int(arc_off[-1])
-    if offsets_bits is None:
-        offsets_bits = 32 if A < 2**31 else 64
     dt = np.int64 if offsets_bits == 64 else np.int32
-    offsets = np.empty(N + 1, dtype=dt)
+    offsets = np.empty(N + G, dtype=dt)
     cols = np.empty(A, dtype=np.int32)
     for i, g in enumerate(graphs):
-        v0, a0 = int(vtx_off[i]), int(arc_off[i])
-        offsets[v0:v0 + g.n] = g.offsets[:g.n].astype(np.int64) + a0
+        v0, a0 = int(vtx_off[i]) + i, int(arc_off[i])
+        offsets[v0:v0 + g.n + 1] = g.offsets.astype(dt)
         cols[a0:a0 + g.A] = g.cols
-    offsets[N] = A
     roots = np.array([g.root for g in graphs], dtype=np.int32)
     return Batch(list(graphs), offsets, cols, vtx_off, arc_off, roots)
 
@@ -325,3 +342,11 @@ def batch_sizes(G: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """G vertex counts log-uniform in [lo, hi]."""
     r = uniform(G, 1 << 30, seed * 7 + 1).astype(np.float64) / (1 << 30)
     return np.exp(np.log(lo) + r * (np.log(hi) - np.log(lo))).astype(np.int64)
+
+
+def workload_batch(G: int = 4096, lo: int = 1024, hi: int = 4096, seed: int = 4) -> Batch:
+    """Mixed batch: G graphs, vertex counts log-uniform in [lo, hi], families in
+    turn grid (aspect 1-1024) / chain with chords (density 1e-5..1e-2) / R-MAT
+    (scale ~log2 n, connected), one seeded root per graph."""
+    sizes = batch_sizes(G, lo, hi, seed)
+    return pack_batch([batch_graph_family(i, seed, int(n)) for i, n in enumerate(sizes)])
