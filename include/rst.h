@@ -195,6 +195,52 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
                              int64_t n, int64_t m, int32_t root, int32_t *parent_out,
                              rst_stream_t stream);
 
+/* ---- learned strategy selector (no counterpart in the paper) ---------------
+ * The paper's comparison (Section IV) shows that the fastest strategy depends
+ * on the graph's depth.  The selector maps 12 cheap features to predicted
+ * natural-log times of BFS, CC+Euler and PR-RST with a 12-64-64-3 ReLU MLP and
+ * picks the smallest, falling back to CC+Euler when the predicted advantage of
+ * another strategy is below a margin.
+ *
+ * rst_selector_features: writes the 12 features (host float[12]) of a graph:
+ *   log2 n, log2 m, mean degree, degree CV, degree skewness, log2(1+max deg),
+ *   fraction of degree <= 2, log2(1+vertices reached by an 8-level BFS probe
+ *   from root), log2 frontier growth between probe levels 3 and 7, log2 of an
+ *   eccentricity estimate, log2(round-1 hook components / n), fraction of
+ *   vertices the probe reached.
+ * rst_selector_load: installs network parameters (host float[5187]: W1[64][12],
+ *   b1[64], W2[64][64], b2[64], W3[3][64], b3[3]), normalisation (host
+ *   float[30]: feature means[12], feature stds[12], target means[3], target
+ *   stds[3]) and the fallback margin (in log-time units).
+ * rst_select: features + prediction; choice_out (host) and pred_log_time_out
+ *   (host float[3], may be NULL).  Without loaded parameters it chooses
+ *   RST_CC_EULER.  rst_build with RST_AUTO uses the same choice.
+ * rst_mlp_forward / rst_mlp_loss_grad / rst_mlp_adam / rst_mlp_train: the
+ *   network's FP32 forward pass, mean-squared-error loss and gradient, Adam
+ *   step (Kingma & Ba) and a full-batch training loop, all on device arrays
+ *   (params[5187], X[batch][12] standardised, T[batch][3], grad[5187],
+ *   adam_m/adam_v[5187], loss_out float[1], loss_hist float[epochs]).
+ * rst_set_option: "bfs_max_levels" caps BFS at that many levels (0: no cap;
+ *   a capped search returns RST_ERR_NOT_CONVERGED) -- used to censor BFS
+ *   timings on very deep graphs when collecting selector training data. */
+rst_status rst_selector_features(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols,
+                                 int64_t n, int64_t m, int32_t root, float *features_out,
+                                 rst_stream_t stream);
+rst_status rst_selector_load(const float *params, const float *norm, float margin);
+rst_status rst_select(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols, int64_t n,
+                      int64_t m, int32_t root, rst_strategy *choice_out, float *pred_log_time_out,
+                      rst_stream_t stream);
+rst_status rst_mlp_forward(const float *params, const float *X, int batch, float *Y,
+                           rst_stream_t stream);
+rst_status rst_mlp_loss_grad(const float *params, const float *X, const float *T, int batch,
+                             float *grad, float *loss_out, rst_stream_t stream);
+rst_status rst_mlp_adam(float *params, const float *grad, float *m, float *v, int count, int step,
+                        float lr, float beta1, float beta2, float eps, rst_stream_t stream);
+rst_status rst_mlp_train(float *params, const float *X, const float *T, int batch, int epochs,
+                         float lr, float *adam_m, float *adam_v, float *loss_hist,
+                         rst_stream_t stream);
+rst_status rst_set_option(const char *key, long long value);
+
 /* ---- diagnostics (no counterpart in the paper) ----------------------------
  * rst_launch_count: number of kernels this library has launched since load.
  * rst_profile_enable(1) starts recording a CUDA event at each stage boundary

@@ -211,11 +211,16 @@ size_t bfs_workspace_bytes(int64_t n) {
   return al(n * 4) * 3 + al((n + 1) * 8) + al(scan_tmp_words(n + 1) * 8);
 }
 
+static long long g_bfs_max_levels = 0;  // 0: unlimited (rst_set_option "bfs_max_levels")
+void set_bfs_max_levels(long long v) { g_bfs_max_levels = v; }
+
 // The search itself; buffers come from `ar` (sized by bfs_workspace_bytes).
+// With a probe, only the root's search runs, for at most probe->max_levels
+// levels, and the frontier size of every level is recorded.
 template <class OffT>
 static rst_status bfs_core(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
                            const int32_t* seeds, int64_t nseeds, int32_t* parent, int32_t* level_out,
-                           cudaStream_t s) {
+                           cudaStream_t s, BfsProbe* probe = nullptr) {
   DeviceState& st = state();
   int32_t* level = level_out ? level_out : ar.take<int32_t>(n);
   int32_t* qa = ar.take<int32_t>(n);
@@ -253,6 +258,13 @@ static rst_status bfs_core(Arena& ar, const OffT* off, const int32_t* col, int64
       int32_t* q = qa;
       int32_t* q2 = qb;
       while (nf > 0) {
+        if (probe) {
+          if (L < BfsProbe::kMax) probe->frontier[L] = nf;
+          probe->reached += nf;
+          probe->levels = L + 1;
+          if (L + 1 >= probe->max_levels) break;
+        }
+        if (!probe && g_bfs_max_levels > 0 && L >= g_bfs_max_levels) return RST_ERR_NOT_CONVERGED;
         RST_CUDA(cudaMemsetAsync(&cnt[BC_NEXT], 0, sizeof(unsigned long long), s));
         const bool want_bu = nf > n / 20;
         if (want_bu) {
@@ -284,7 +296,13 @@ static rst_status bfs_core(Arena& ar, const OffT* off, const int32_t* col, int64
       }
       (void)bottom_up;
       levels_total += L;
+      if (probe) {
+        probe->finished = (nf == 0);
+        probe->last_frontier = nf;
+        break;
+      }
     }
+    if (probe) break;  // the probe only searches the root's component
     // next component: minimum unvisited vertex
     RST_CUDA(cudaMemsetAsync(&cnt[BC_MINUNV], 0xff, sizeof(unsigned long long), s));
     RST_LAUNCH(k_bfs_min_unvisited, gN, kBlock, 0, s)(n, level, cnt);
@@ -311,6 +329,13 @@ rst_status run_bfs(const void* off, int offsets_bits, const int32_t* cols, int64
                    int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s) {
   if (offsets_bits == 32) return bfs_impl<int32_t>((const int32_t*)off, cols, n, m, root, parent, level_out, s);
   return bfs_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, level_out, s);
+}
+
+rst_status bfs_probe_in(Arena& ar, const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                        int32_t root, int32_t* parent_scratch, BfsProbe* probe, cudaStream_t s) {
+  if (offsets_bits == 32)
+    return bfs_core<int32_t>(ar, (const int32_t*)off, cols, n, m, root, nullptr, 0, parent_scratch, nullptr, s, probe);
+  return bfs_core<int64_t>(ar, (const int64_t*)off, cols, n, m, root, nullptr, 0, parent_scratch, nullptr, s, probe);
 }
 
 rst_status bfs_multi_in(Arena& ar, const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,

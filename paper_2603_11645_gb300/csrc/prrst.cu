@@ -259,10 +259,4 @@ rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int
   return prrst_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, s);
 }
 
-rst_strategy select_strategy_host(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
-                                  int32_t root, cudaStream_t s) {
-  (void)off; (void)offsets_bits; (void)cols; (void)n; (void)m; (void)root; (void)s;
-  return RST_CC_EULER;
-}
-
 }  // namespace rst

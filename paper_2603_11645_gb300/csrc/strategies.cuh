@@ -10,6 +10,21 @@ namespace rst {
 rst_status run_bfs(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                    int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s);
 
+// A bounded BFS from the root (the selector's probe): frontier sizes of the
+// first levels, vertices reached, whether the search finished.
+struct BfsProbe {
+  static constexpr int kMax = 64;
+  int max_levels = 8;
+  int levels = 0;
+  bool finished = false;
+  long long reached = 0;
+  long long last_frontier = 0;
+  long long frontier[kMax] = {0};
+};
+rst_status bfs_probe_in(Arena& ar, const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                        int32_t root, int32_t* parent_scratch, BfsProbe* probe, cudaStream_t s);
+void set_bfs_max_levels(long long v);
+
 // BFS from several sources at once (the roots of a disjoint union), with
 // buffers taken from the caller's arena (bfs_workspace_bytes(n) of room).
 size_t bfs_workspace_bytes(int64_t n);

@@ -1,0 +1,169 @@
+"""Strategy selector: oracle pins (CPU), GPU kernels against the oracle, and
+the trained network's regret on held-out graphs."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import selector as OS
+from paper_2603_11645_gb300 import graphs
+
+
+def _batch(seed, B=37):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(B, OS.F))
+    T = rng.normal(size=(B, OS.O))
+    p = OS.he_init(seed) + rng.normal(0, 0.05, OS.NPARAM)
+    return p, X, T
+
+
+# ------------------------------------------------------------------ oracle pins
+
+def test_oracle_gradient_matches_finite_differences():
+    p, X, T = _batch(1)
+    loss, g = OS.loss_grad(p, X, T)
+    rng = np.random.default_rng(2)
+    idx = rng.choice(OS.NPARAM, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(OS.NPARAM)
+        e[i] = h
+        fd = (OS.loss_grad(p + e, X, T)[0] - OS.loss_grad(p - e, X, T)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9
+
+
+def test_oracle_adam_first_step_closed_form():
+    # with m = v = 0 at t = 1 the bias-corrected moments are g and g^2, so the
+    # step is lr * g / (|g| + eps)
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=50)
+    g = rng.normal(size=50)
+    q, m, v = OS.adam_step(p, g, np.zeros(50), np.zeros(50), 1, lr=0.01)
+    assert np.allclose(q, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-12)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_oracle_features_of_a_path():
+    n = 10
+    g = graphs.from_edges(n, list(range(n - 1)), list(range(1, n)), root=0)
+    f = OS.features(n, g.offsets, g.cols, 0)
+    mu = 18 / 10
+    var = (2 * 1 + 8 * 4) / 10 - mu * mu
+    assert f[0] == pytest.approx(math.log2(10))
+    assert f[1] == pytest.approx(math.log2(9))
+    assert f[2] == pytest.approx(mu)
+    assert f[3] == pytest.approx(math.sqrt(var) / mu)
+    assert f[5] == pytest.approx(math.log2(3))
+    assert f[6] == pytest.approx(1.0)
+    # probe: levels 0..7 hold one vertex each, not finished after 8 levels
+    assert f[7] == pytest.approx(math.log2(9))
+    assert f[8] == pytest.approx(0.0)
+    assert f[9] == pytest.approx(math.log2(1 + 8 + 2 / 1))
+    # round 1: only 0 and 1 choose each other
+    assert f[10] == pytest.approx(math.log2(1 / 10))
+    assert f[11] == pytest.approx(0.8)
+
+
+def test_oracle_features_of_a_star():
+    n = 9
+    g = graphs.from_edges(n, [0] * 8, list(range(1, n)), root=3)
+    f = OS.features(n, g.offsets, g.cols, 3)
+    # levels: {3}, {0}, {1,2,4,...,8}; finished after 3 levels
+    assert f[7] == pytest.approx(math.log2(10))
+    assert f[9] == pytest.approx(math.log2(1 + 3))
+    assert f[11] == pytest.approx(1.0)
+    # every leaf's first neighbour is 0, 0's first neighbour is 1: one mutual pair
+    assert f[10] == pytest.approx(math.log2(1 / 9))
+
+
+# ------------------------------------------------------------------ GPU kernels vs oracle
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.gpu
+def test_gpu_features_match_oracle():
+    from paper_2603_11645_gb300 import selector as S
+    cases = [graphs.grid(40, 30, seed=1, root="random"), graphs.chain_chords(5000, 0.001, seed=2),
+             graphs.rmat(12, 16, seed=3, connect=True, offsets_bits=32), graphs.random_4regular(3000, seed=4),
+             graphs.erdos_renyi(2000, 1500, seed=5), graphs.from_edges(5, [0, 1], [1, 2], root=4)]
+    for g in cases:
+        off = torch.from_numpy(g.offsets).cuda()
+        col = torch.from_numpy(g.cols).cuda()
+        got = S.features(off, col, g.root)
+        want = OS.features(g.n, g.offsets, g.cols, g.root)
+        assert np.allclose(got, want, rtol=2e-6, atol=2e-6), (g.name, got, want)
+
+
+@pytest.mark.gpu
+def test_gpu_mlp_matches_oracle():
+    import ctypes
+    from paper_2603_11645_gb300 import selector as S
+    L = S._lib()
+    p, X, T = _batch(7, B=513)
+    pd = torch.tensor(p, dtype=torch.float32, device="cuda")
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    Y = torch.zeros(513, 3, device="cuda")
+    S._check("fwd", L.rst_mlp_forward(ctypes.c_void_p(pd.data_ptr()), ctypes.c_void_p(Xd.data_ptr()), 513,
+                                      ctypes.c_void_p(Y.data_ptr()), S._stream()))
+    y_ref, _ = OS.forward(p.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64))
+    assert np.allclose(Y.cpu().numpy(), y_ref, rtol=1e-4, atol=1e-4)
+    G = torch.zeros(OS.NPARAM, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    S._check("grad", L.rst_mlp_loss_grad(ctypes.c_void_p(pd.data_ptr()), ctypes.c_void_p(Xd.data_ptr()),
+                                         ctypes.c_void_p(Td.data_ptr()), 513, ctypes.c_void_p(G.data_ptr()),
+                                         ctypes.c_void_p(loss.data_ptr()), S._stream()))
+    l_ref, g_ref = OS.loss_grad(p.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64),
+                                T.astype(np.float32).astype(np.float64))
+    g = G.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - l_ref) <= 1e-4 * abs(l_ref)
+    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+    # one Adam step
+    m = torch.zeros_like(pd)
+    v = torch.zeros_like(pd)
+    S._check("adam", L.rst_mlp_adam(ctypes.c_void_p(pd.data_ptr()), ctypes.c_void_p(G.data_ptr()),
+                                    ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()), OS.NPARAM, 1,
+                                    1e-3, 0.9, 0.999, 1e-8, S._stream()))
+    q_ref, _, _ = OS.adam_step(p.astype(np.float32).astype(np.float64), g, np.zeros(OS.NPARAM), np.zeros(OS.NPARAM),
+                               1, lr=1e-3)
+    assert np.allclose(pd.cpu().numpy(), q_ref, rtol=0, atol=2e-6)
+
+
+@pytest.mark.gpu
+def test_gpu_training_fits_a_smooth_target():
+    from paper_2603_11645_gb300 import selector as S
+    rng = np.random.default_rng(11)
+    X = rng.normal(size=(800, 12))
+    t = np.exp(np.stack([X[:, 0] + 0.5 * X[:, 1], np.sin(X[:, 2]), X[:, 3] * X[:, 4] * 0.3], 1))
+    model = S.train(X, t, epochs=1500, lr=3e-3, seed=1)
+    assert model["loss_last"] < 0.2 * model["loss_first"]
+
+
+# ------------------------------------------------------------------ regret of the trained selector
+
+def _trained():
+    from paper_2603_11645_gb300 import selector as S
+    if not os.path.exists(S.WEIGHTS_PATH):
+        pytest.skip("no trained selector weights in the repository")
+    with open(S.WEIGHTS_PATH) as fh:
+        model = json.load(fh)
+    data = os.path.join(os.path.dirname(S.__file__), "selector_data")
+    ho = [f for f in os.listdir(data) if f.startswith("heldout_")] if os.path.isdir(data) else []
+    if not ho:
+        pytest.skip("no held-out timing data in the repository")
+    return S, model, os.path.join(data, ho[0])
+
+
+def test_selector_regret_beats_always_cc_euler():
+    """What the network gains over the method without it (always CC+Euler),
+    measured on held-out graphs from stored GPU timings."""
+    S, model, path = _trained()
+    X, Tt, fam = S.load_dataset(path)
+    sel = S.choose(S.predict_host(model, X), model["margin"])
+    r_sel = S.regret(Tt, sel)
+    r_cc = S.regret(Tt, np.ones(len(Tt), dtype=int))
+    assert r_sel <= r_cc
+    assert r_sel <= 0.10
