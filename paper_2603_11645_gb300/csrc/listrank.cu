@@ -152,17 +152,18 @@ __global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S
 
 // pos[x] = position of x's owner + x's offset.  At the first level every
 // element must have been visited (visited == N); at deeper levels the unused
-// slots of heads that coincided with a regular splitter are never visited and
-// their value is ignored.
-__global__ void k_lr_final(int64_t N, const int2* __restrict__ ol, const uint32_t* __restrict__ spos,
-                           uint32_t* __restrict__ pos, const unsigned long long* visited,
-                           uint32_t* status) {
+// slots of heads that coincided with a regular splitter are never visited.
+// An unvisited element's record holds whatever the workspace held before, so
+// the owner index is bounds-checked (S = number of splitters) before use.
+__global__ void k_lr_final(int64_t N, int64_t S, const int2* __restrict__ ol,
+                           const uint32_t* __restrict__ spos, uint32_t* __restrict__ pos,
+                           const unsigned long long* visited, uint32_t* status) {
   if (visited && blockIdx.x == 0 && threadIdx.x == 0 && *visited != (unsigned long long)N)
     raise_error(status, DERR_NOT_FOREST);
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
        x += (int64_t)gridDim.x * blockDim.x) {
     const int2 r = ol[x];
-    pos[x] = (r.x >= 0) ? spos[r.x] + (uint32_t)r.y : kNone;
+    pos[x] = (r.x >= 0 && (int64_t)r.x < S) ? spos[r.x] + (uint32_t)r.y : kNone;
   }
 }
 
@@ -308,7 +309,8 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   for (int l = levels.count - 1; l >= 0; --l) {
     const Frame& fr = frames[l];
     LevelBufs& b = levels.b[l];
-    RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, b.ol, b.spos, fr.pos,
+    const int64_t S = (fr.N + kLrK - 1) / kLrK + nheads;
+    RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.spos, fr.pos,
                                                          l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_final1" : "k_lr_final");
   }

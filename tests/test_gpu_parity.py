@@ -246,3 +246,24 @@ def test_prrst_edge_cases(g):
     off, col = dev(g)
     par = rst.build(off, col, g.root, "pr_rst").cpu().numpy()
     assert np.array_equal(par, oracle.prrst(g.n, g.offsets, g.cols, g.root)[0])
+
+
+def test_list_ranking_head_on_a_splitter_after_other_calls():
+    """A path rooted at 0 puts the tour head at sorted position 0 (a regular
+    splitter of the list ranking) with enough arcs for several levels; run it
+    after calls that leave other data in the shared workspace."""
+    import paper_2603_11645_gb300 as rst
+    n = 100_000
+    g = graphs.from_edges(n, list(range(n - 1)), list(range(1, n)), root=0)
+    other = graphs.erdos_renyi(150_000, 300_000, seed=77)
+    oo, oc = dev(other)
+    rst.build(oo, oc, other.root, "bfs")
+    rst.build(oo, oc, other.root, "cc_euler")
+    off, col = dev(g)
+    par = rst.build(off, col, 0, "cc_euler").cpu().numpy()
+    assert par[0] == 0 and np.array_equal(par[1:], np.arange(n - 1))
+    uv = torch.from_numpy(np.stack([np.arange(n - 1), np.arange(1, n)], 1).astype(np.int32)).cuda()
+    p2, rank = rst.euler_root(n, uv, 0)
+    r = rank.cpu().numpy()
+    # sorted arcs: (0,1), then per vertex i >= 1: (i,i-1), (i,i+1)
+    assert r[0] == 0 and np.array_equal(p2.cpu().numpy(), par)
