@@ -49,7 +49,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -67,7 +67,7 @@ class ClockSampler:
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -104,9 +104,11 @@ class ClockSampler:
 
 def kernel_bytes(name, n, A, st, o):
     """Algorithmic bytes per launch: every element a kernel must read or write,
-    counted once (random accesses are not charged their sector size)."""
+    counted once (random accesses are not charged their sector size).
+    N = tree arcs list-ranked (after leaf pruning), T = tree edges."""
     T = st["T"]
-    N = 2 * T
+    N = st["lr_n"]
+    K = N // 2  # tree edges that are toured
     c1, E2 = st["c1"], st["E2"]
     models = {
         "k_r1_choose": (n + 1) * o + 4 * n + 8 * n,
@@ -114,18 +116,40 @@ def kernel_bytes(name, n, A, st, o):
         "k_r1_number": 8 * n + 8 * c1,
         "k_r1_label": 16 * n,
         "k_build_list": (n + 1) * o + 4 * A + 4 * n + 2 * A + 12 * E2,
-        "k_toff": (n + 1) * (o + 8 + 4) + n,
-        "k_pairs_succ": T * (16 + 16 + 16 + 16 + 8),
+        "k_toff": (n + 1) * (o + 8 + 4) + 2 * n,
+        "k_prune_leaves": 16 * T + 2 * T + 4 * (T - K),
+        "k_pairs_succ": 16 * T + K * (16 + 16 + 16 + 8),
         "k_lr_walk1": 16 * N + 12 * ((N + 15) // 16),
         "k_lr_final1": 8 * N + 4 * N + 4 * ((N + 15) // 16),
-        "k_parent_from_rank": 16 * T + 8 * T + 4 * T,
+        "k_parent_from_rank": 16 * T + K * (8 + 4),
     }
     return models.get(name)
 
 
-def traffic_for(kernel):
-    """Per-launch DRAM bytes from the committed ncu capture, or None when the
-    kernel's source changed since the counters were taken."""
+def _function_source(path, name):
+    """Text of the CUDA function `name` in `path` (from its definition to the
+    matching closing brace)."""
+    text = open(path).read()
+    i = text.find(f" {name}(")
+    if i < 0:
+        return None
+    start = text.rfind("\n", 0, i) + 1
+    j = text.find("{", i)
+    depth = 0
+    for k in range(j, len(text)):
+        if text[k] == "{":
+            depth += 1
+        elif text[k] == "}":
+            depth -= 1
+            if depth == 0:
+                return text[start:k + 1]
+    return None
+
+
+def traffic_for(kernel, units):
+    """Per-launch DRAM bytes (read + write) of `kernel` from the committed ncu
+    capture, scaled to `units` elements; None when the kernel's source text
+    changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -135,13 +159,10 @@ def traffic_for(kernel):
     e = d.get(kernel)
     if not e:
         return None
-    h = hashlib.sha256()
-    for rel in e["sources"]:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest() != e["sha256"]:
+    src = _function_source(os.path.join(ROOT, e["file"]), e["function"])
+    if src is None or hashlib.sha256(src.encode()).hexdigest() != e["sha256"]:
         return None
-    return e["bytes_per_launch"]
+    return int(e["bytes_per_unit"] * units)
 
 
 # ----------------------------------------------------------------- oracle (CPU baseline)
@@ -229,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
     stats = (ctypes.c_longlong * 8)()
     L.rst_last_stats(stats, 8)
     st = {"rounds": stats[0], "c1": stats[1], "E2": stats[2], "T": stats[3], "nroots": stats[4],
-          "lr_levels": stats[5]}
+          "lr_levels": stats[5], "lr_n": stats[6]}
     peak, peak_src = measured_peaks()
     roofline = None
     if dom:
@@ -238,7 +259,8 @@ def run_ours(args, rank, world, local_rank):
         if byts:
             achieved = byts / (per_launch_ms / 1e3) / 1e9
             roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(achieved / peak, 4), "traffic": traffic_for(dom),
+                        "frac": round(achieved / peak, 4),
+                        "traffic": traffic_for(dom, st["lr_n"] if dom.startswith("k_lr") else st["T"]),
                         "kernel": dom, "algorithmic_bytes": int(byts),
                         "launch_ms": round(per_launch_ms, 4), "peak_source": peak_src,
                         "share_of_step": round(sum(kern[dom]) / total_ms, 3) if world == 1 else None}
@@ -304,6 +326,8 @@ def run_ours(args, rank, world, local_rank):
     pr_med = statistics.median(pr_ms)
 
     batch = None if args.no_batch else run_batch(args, dev, stream, rst, graphs, torch)
+    families = None if args.no_families else run_families(args, dev, stream, rst, graphs, torch)
+    selector = run_selector_report(off, col, g.root, torch)
 
     out = None
     if rank == 0:
@@ -334,6 +358,8 @@ def run_ours(args, rank, world, local_rank):
             "pr_rst": {"value": g.m / (pr_med / 1e3), "unit": "edges/s", "ms_per_step": pr_med,
                        "cc_euler_speedup": pr_med / ms_step},
             "batch": batch,
+            "families": families,
+            "selector": selector,
             "stats": st,
             "stage_ms": stage_summary,
         }
@@ -385,6 +411,57 @@ def run_batch(args, dev, stream, rst, graphs, torch):
             "unit": "edges/s", "speedup": per_graph / batched}
 
 
+def _time(fn, reps, torch, dev, stream, flush=None):
+    fn()
+    torch.cuda.synchronize(dev)
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def run_families(args, dev, stream, rst, graphs, torch):
+    """The power-law family: R-MAT scale 22 (edge factor 16, connected, int64 offsets)."""
+    g = graphs.rmat(22, 16, seed=3, connect=True, offsets_bits=64)
+    off = torch.from_numpy(g.offsets).to(dev)
+    col = torch.from_numpy(g.cols).to(dev)
+    par = torch.empty(g.n, dtype=torch.int32, device=dev)
+    out = {"workload": f"R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), connected to 0, "
+                       f"int64 offsets, root 0: {g.n} vertices, {g.m} edges", "m": g.m}
+    for strat in ("cc_euler", "bfs", "pr_rst"):
+        ms = _time(lambda: rst.build(off, col, g.root, strat, out=par), 3, torch, dev, stream)
+        out[strat] = {"ms": ms, "value": g.m / (ms / 1e3), "unit": "edges/s"}
+    out["cc_euler_speedup_over_bfs"] = out["bfs"]["ms"] / out["cc_euler"]["ms"]
+    return {"rmat22": out}
+
+
+def run_selector_report(off, col, root, torch):
+    """Held-out regret of the trained selector (GPU timings stored with the
+    weights) and the cost of one rst_select call on the headline graph."""
+    from paper_2603_11645_gb300 import selector as S
+    model = S.load_default()
+    if model is None:
+        return None
+    t0 = time.perf_counter()
+    for _ in range(5):
+        choice, pred = S.select(off, col, root)
+    sel_ms = (time.perf_counter() - t0) / 5 * 1e3
+    rep = model.get("heldout_report", {})
+    return {"heldout_regret": rep.get("selector_regret"),
+            "always_cc_euler_regret": rep.get("always_cc_euler_regret"),
+            "heldout_graphs": rep.get("heldout_graphs"), "margin": model.get("margin"),
+            "choice_on_headline": choice, "select_ms": sel_ms,
+            "source": "paper_2603_11645_gb300/selector_weights.json (timings collected on GB300)"}
+
+
 # ----------------------------------------------------------------- reference arm (the oracle)
 
 def run_reference(args, rank, world):
@@ -420,12 +497,13 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bfs-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-families", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -251,8 +251,9 @@ rst_status rst_set_option(const char *key, long long value);
 long long rst_launch_count(void);
 /* Sizes seen by the last call (host array): hooking rounds, components with
  * edges after round 1, inter-component edges after round 1, tree edges,
- * components with edges, BFS levels or list-ranking levels.  Returns the
- * number of values written (at most max). */
+ * components with edges, BFS levels or list-ranking levels, tree arcs list-
+ * ranked (after leaf pruning).  Returns the number of values written (at most
+ * max). */
 int rst_last_stats(long long *out, int max);
 void rst_profile_enable(int on);
 int rst_profile_read(float *ms_out, const char **names_out, int max_stages);

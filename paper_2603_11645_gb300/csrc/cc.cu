@@ -220,6 +220,8 @@ __global__ void k_r1_label(int64_t n, const int32_t* __restrict__ P, const uint3
 
 // The inter-component edges after round 1: every arc u->v with u < v whose
 // endpoints lie in different round-1 components, as {C1[u], C1[v], position}.
+// The scan also performs the first contraction round's packed atomicMin hook,
+// so that round does not read the list again.
 // Arc-centric tiles: coalesced column loads, rows from a shared-memory scan,
 // independent label gathers, one slot reservation per tile.
 template <class OffT>
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(kArcThreads) k_build_list(const OffT* __restri
                                                             uint32_t* __restrict__ Ep,
                                                             unsigned long long* counter, int64_t cap,
                                                             const int32_t* __restrict__ tile_row,
+                                                            unsigned long long* __restrict__ best,
                                                             uint32_t* status) {
   __shared__ int32_t s_row[kArcTile];
   for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
@@ -258,7 +261,13 @@ __global__ void __launch_bounds__(kArcThreads) k_build_list(const OffT* __restri
           bu[k] = cu;
           bv[k] = cv;
           bp[k] = (uint32_t)(a0 + i);
-          if (cu != cv) mask |= 1u << k;
+          if (cu != cv) {
+            mask |= 1u << k;
+            // the first contraction round's hook, fused into the scan
+            const unsigned long long key = (unsigned long long)(uint32_t)(a0 + i) << 32;
+            atomicMin(&best[cu], key | (uint32_t)cv);
+            atomicMin(&best[cv], key | (uint32_t)cu);
+          }
         }
       }
     }
@@ -320,7 +329,7 @@ __global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     CcCtl* t = b.ctl;
     t->st[0].C = C;
-    t->st[0].E = b.counters[CNT_LIST];
+    t->st[0].E = 0;  // the list build already hooked round 0; its list is round 1's
     t->st[0].pool_at = 0;
     const int32_t c1 = root >= 0 ? C1[root] : -1;
     t->st[0].rc = c1;
@@ -666,16 +675,6 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   prof_mark(s, "k_r1_number");
   RST_LAUNCH(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.CID, b.C1);
   prof_mark(s, "k_r1_label");
-  if (A > 0) {
-    // one tile per block: the row searches of many resident blocks overlap
-    const int64_t tiles = (A + kArcTile - 1) / kArcTile;
-    const unsigned g = (unsigned)tiles;
-    RST_LAUNCH(k_arc_tile_rows<OffT>, grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
-    RST_LAUNCH(k_build_list<OffT>, g, kArcThreads, 0, s)(off, col, n, A, b.C1, b.Ecu[0], b.Ecv[0],
-                                                         b.Ep[0], &cnt[CNT_LIST], b.ecap, b.tile_row,
-                                                         status);
-  }
-  prof_mark(s, "k_build_list");
   CcPtrs p;
   p.col = col;
   for (int k = 0; k < 2; ++k) {
@@ -697,6 +696,17 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   p.ecap = b.ecap;
   RST_LAUNCH(k_round_init, grid_for(n / 2 + 1), kBlock, 0, s)(p, root, b.C1);
   prof_mark(s, "k_round_init");
+  if (A > 0) {
+    // one tile per block: the row searches of many resident blocks overlap;
+    // entries go to list buffer 1 (round 1 reads it) and are counted in st[1].E
+    const int64_t tiles = (A + kArcTile - 1) / kArcTile;
+    const unsigned g = (unsigned)tiles;
+    RST_LAUNCH(k_arc_tile_rows<OffT>, grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
+    RST_LAUNCH(k_build_list<OffT>, g, kArcThreads, 0, s)(off, col, n, A, b.C1, b.Ecu[1], b.Ecv[1],
+                                                         b.Ep[1], &b.ctl->st[1].E, b.ecap, b.tile_row,
+                                                         b.best[0], status);
+  }
+  prof_mark(s, "k_build_list");
   RST_CUDA(cudaGetLastError());
 
   // Contraction rounds: one graph launch (a device-side while loop), or,
@@ -726,6 +736,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   unsigned long long h[8];
   RST_TRY(fetch_u64(cnt, 8, h, s));
   const int rounds_done = hctl->cur;
+  if (!eager) count_launches(6LL * rounds_done);  // the round kernels the graph ran
   if (labels_out) {
     for (int r = rounds_done - 2; r >= 0; --r) {
       const int64_t Cr = (int64_t)hctl->st[r].C;
@@ -740,8 +751,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   }
   prof_mark(s, "cc_finish");
   set_stat(STAT_C1, (long long)hctl->st[0].C);
-  set_stat(STAT_E2, (long long)hctl->st[0].E);
-  if ((int64_t)h[CNT_LIST] > b.ecap) return RST_ERR_DEVICE;
+  set_stat(STAT_E2, (long long)hctl->st[1].E);
   out->T = (int64_t)h[CNT_PAIRS];
   out->pairs = b.pairs;
   out->bits = b.bits;

@@ -46,6 +46,7 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
 // Every kernel launch goes through RST_LAUNCH so that the library can report
 // how many of its kernels ran (rst_launch_count).
 void count_launch();
+void count_launches(long long k);  // kernels executed inside a graph launch
 #define RST_LAUNCH(k, ...) ::rst::count_launch(), k<<<__VA_ARGS__>>>
 // Stage marks: when profiling is on, records a CUDA event on `s` that ends the
 // stage `name` (a string literal); rst_profile_read returns the durations.
@@ -58,6 +59,7 @@ enum StatSlot : int {
   STAT_T = 3,        // tree edges
   STAT_NROOTS = 4,   // components with edges
   STAT_LEVELS = 5,   // BFS levels (BFS) / list-ranking levels (CC+Euler)
+  STAT_LR_N = 6,     // elements list-ranked (tree arcs left after leaf pruning)
   STAT_COUNT = 8
 };
 void set_stat(int slot, long long v);

@@ -23,6 +23,7 @@ __global__ void k_parent_from_rank(int64_t T, const uint4* __restrict__ pairs,
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
     const uint4 r = pairs[t];  // {i, k, a, b}: i = a->b, k = b->a
+    if (r.x == kNone) continue;  // a pruned leaf edge: parent already set
     const uint32_t ri = R[r.x], rk = R[r.y];
     if (ri < rk)
       parent[r.w] = (int32_t)r.z;  // a->b traversed first: a is b's parent
@@ -58,18 +59,43 @@ __global__ void k_mark_roots(int64_t nroots, const int32_t* __restrict__ roots, 
     is_root[tree_root_for(roots[k], root_label, root, rootof)] = 1;
 }
 
+// Tree-arc runs: toff[v] = first tree position of v.  With parent set, roots
+// and singletons also take P[v] = v; with leaf set, leaf[v] marks vertices of
+// tree degree 1 that are not tree roots.
 template <class OffT>
 __global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint32_t* __restrict__ bits,
                        const uint32_t* __restrict__ wpre, const uint8_t* __restrict__ is_root,
-                       uint32_t* __restrict__ toff, int32_t* __restrict__ parent) {
+                       uint32_t* __restrict__ toff, int32_t* __restrict__ parent, uint8_t* __restrict__ leaf) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t t0 = bit_rank(bits, wpre, (uint64_t)off[v]);
     toff[v] = t0;
-    if (v < n) {
+    if (v < n && (parent || leaf)) {
       const uint32_t t1 = bit_rank(bits, wpre, (uint64_t)off[v + 1]);
-      if (t0 == t1 || is_root[v]) parent[v] = (int32_t)v;
+      if (parent && (t0 == t1 || is_root[v])) parent[v] = (int32_t)v;
+      if (leaf) leaf[v] = (t1 - t0 == 1u && !is_root[v]) ? 1 : 0;
     }
+  }
+}
+
+// Leaf pruning (rake) before the tour: a non-root vertex of tree degree 1
+// has its single tree neighbour as parent.  Its edge leaves the tree that is
+// toured (both arcs' bits are cleared) and the pair is marked done.  Removing
+// leaves changes no ancestor relation among the remaining vertices.
+__global__ void k_prune_leaves(int64_t T, uint4* __restrict__ pairs, const uint8_t* __restrict__ leaf,
+                               uint32_t* __restrict__ bits, int32_t* __restrict__ parent) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    uint4 r = pairs[t];
+    const int32_t a = (int32_t)r.z, b = (int32_t)r.w;
+    const bool la = leaf[a], lb = leaf[b];
+    if (!la && !lb) continue;
+    if (lb) parent[b] = a;
+    if (la) parent[a] = b;
+    atomicAnd(&bits[r.x >> 5], ~(1u << (r.x & 31)));
+    atomicAnd(&bits[r.y >> 5], ~(1u << (r.y & 31)));
+    r.x = kNone;
+    pairs[t] = r;
   }
 }
 
@@ -77,8 +103,10 @@ __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32
                         int32_t root, const int32_t* __restrict__ rootof,
                         const uint32_t* __restrict__ toff, int32_t* __restrict__ heads) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
-       k += (int64_t)gridDim.x * blockDim.x)
-    heads[k] = (int32_t)toff[tree_root_for(roots[k], root_label, root, rootof)];
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = tree_root_for(roots[k], root_label, root, rootof);
+    heads[k] = toff[r + 1] > toff[r] ? (int32_t)toff[r] : -1;  // -1: nothing left to tour
+  }
 }
 
 // {p, q, a, b} (CSR positions) -> {i, k, a, b} (tree positions), in place,
@@ -91,6 +119,7 @@ __global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint32_
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
     uint4 r = pairs[t];
+    if (r.x == kNone) continue;  // pruned leaf edge
     const uint32_t i = bit_rank(bits, wpre, r.x);
     const uint32_t k = bit_rank(bits, wpre, r.y);
     const int32_t a = (int32_t)r.z, b = (int32_t)r.w;
@@ -107,8 +136,8 @@ __global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint32_
 size_t euler_cc_workspace_bytes(int64_t n, int64_t A, int64_t T, int64_t nroots) {
   const int64_t W = A / 32 + 1;
   auto al = [](size_t b) { return (b + 255) / 256 * 256 + 256; };
-  size_t b = al((W + 1) * 4) + al(scan_tmp_words(W) * 8) + al(n) + al((n + 1) * 4) +
-             al(nroots * 4 + 4);
+  size_t b = 2 * al((W + 1) * 4) + al(scan_tmp_words(W) * 8) + 2 * al(n) + 2 * al((n + 1) * 4) +
+             al(nroots * 4 + 4) + 256;
   return b + euler_core_bytes(T);
 }
 
@@ -129,15 +158,36 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
     RST_LAUNCH(k_mark_roots, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label,
                                                          root, cc->rootof, is_root);
   prof_mark(s, "eu_roots");
-  RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, cc->bits, wpre, is_root, toff, parent_out);
+  const int64_t T = cc->T;
+  // Without requested ranks the tour only has to order each edge's twins, so
+  // leaves are pruned first: their parent is their single tree neighbour.
+  const bool prune = rank_out == nullptr && T > 0;
+  uint8_t* leaf = prune ? ar.take<uint8_t>(n) : nullptr;
+  if (prune && !leaf) return RST_ERR_OOM;
+  RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, cc->bits, wpre, is_root, toff, parent_out,
+                                                          leaf);
   prof_mark(s, "k_toff");
+  int64_t N = 2 * T;
+  if (prune) {
+    RST_LAUNCH(k_prune_leaves, grid_for(T), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
+    prof_mark(s, "k_prune_leaves");
+    RST_TRY(scan_popcount_words(cc->bits, wpre, W, tmp, s));
+    RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, cc->bits, wpre, is_root, toff, nullptr,
+                                                            nullptr);
+    unsigned long long left = 0;
+    RST_CUDA(cudaMemcpyAsync(host_scratch(8), wpre + W, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    RST_CUDA(cudaStreamSynchronize(s));
+    uint32_t left32 = 0;
+    std::memcpy(&left32, host_scratch(8), sizeof(uint32_t));
+    left = left32;
+    N = (int64_t)left;
+    prof_mark(s, "eu_reduced");
+  }
   if (cc->nroots > 0)
     RST_LAUNCH(k_heads, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label, root,
                                                     cc->rootof, toff, heads);
   RST_CUDA(cudaGetLastError());
-  const int64_t T = cc->T;
-  if (T <= 0) return RST_OK;
-  const int64_t N = 2 * T;
+  if (T <= 0 || N <= 0) return RST_OK;
   int32_t* succ = ar.take<int32_t>(N);
   uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
   if (!succ || !R) return RST_ERR_OOM;

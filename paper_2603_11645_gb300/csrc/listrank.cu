@@ -97,7 +97,10 @@ __global__ void k_lr_heads(int64_t N, int64_t S0, const int32_t* __restrict__ he
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < h;
        j += (int64_t)gridDim.x * blockDim.x) {
     const int32_t x = heads[j];
-    if ((x & (kLrK - 1)) == 0) {
+    if (x < 0) {  // a list without elements: no splitter
+      shead[j] = -1;
+      sstart[S0 + j] = -1;
+    } else if ((x & (kLrK - 1)) == 0) {
       shead[j] = x / kLrK;
       sstart[S0 + j] = -1;
     } else {
@@ -254,6 +257,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   for (int l = 0; l < levels.count; ++l)
     if (!levels.b[l].spos) return RST_ERR_OOM;
   set_stat(STAT_LEVELS, (long long)levels.count);
+  set_stat(STAT_LR_N, N);
   uint32_t* status = state().status;
   unsigned long long* visited = dev_counter(7);
 
@@ -310,6 +314,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     const Frame& fr = frames[l];
     LevelBufs& b = levels.b[l];
     const int64_t S = (fr.N + kLrK - 1) / kLrK + nheads;
+
     RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.spos, fr.pos,
                                                          l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_final1" : "k_lr_final");

@@ -27,6 +27,7 @@ void set_stat(int slot, long long v) {
   if (slot >= 0 && slot < STAT_COUNT) g_stats[slot] = v;
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 struct Profiler {
   bool on = false;

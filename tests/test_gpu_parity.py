@@ -56,6 +56,10 @@ def edge_cases():
     cases.append(graphs.from_edges(6, [0, 1, 2, 3, 4], [1, 2, 3, 4, 5], name="path-root-mid", root=2))
     g = graphs.from_edges(5, [0, 0, 0, 0], [1, 2, 3, 4], name="star64", root=4, offsets_bits=64)
     cases.append(g)
+    cases.append(graphs.from_edges(9, [0] * 8, list(range(1, 9)), name="star-centre-root", root=0))
+    cases.append(graphs.from_edges(9, [0] * 8, list(range(1, 9)), name="star-leaf-root", root=5))
+    cases.append(graphs.from_edges(2, [0], [1], name="pair-root0", root=0))
+    cases.append(graphs.from_edges(8, [0, 1, 2, 4, 5, 6], [1, 2, 3, 5, 6, 7], name="two-paths", root=3))
     return cases
 
 
