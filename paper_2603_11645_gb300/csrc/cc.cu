@@ -45,8 +45,9 @@ struct RoundState {
 };
 struct CcCtl {
   RoundState st[kMaxRounds + 1];
-  int cur;          // current round
-  int root_label;   // canonical label of the requested root (-1 until known)
+  int cur;             // current round
+  int root_label;      // canonical label of the requested root (-1 until known)
+  unsigned int done;   // blocks of the round's last kernel that have finished
 };
 
 struct CcBuffers {
@@ -296,11 +297,10 @@ __global__ void __launch_bounds__(kArcThreads) k_build_list(const OffT* __restri
 //    drop entries inside one component, packed atomicMin on both endpoints,
 //    and append the survivors (the next round's list)
 //  2 resolve: final components, mutual pairs, hooks, tree-edge records
-//  3 compress: shortcut the hook forest
-//  4 renumber: dense ids for the surviving roots; final components join the
-//    list of component roots
-//  5 map: component -> next id; minimum vertex per new component
-//  6 advance: next round, loop condition
+//  3 settle: shortcut the hook forest; dense ids for the surviving roots;
+//    final components join the list of component roots
+//  4 map: component -> next id; minimum vertex per new component; the last
+//    block advances the round and sets the loop condition
 
 struct CcPtrs {
   const int32_t* col;
@@ -364,9 +364,13 @@ __global__ void k_round_hook(CcPtrs b) {
       }
       keep = cu != cv;
       if (keep) {
+        // read before the atomic: a value already below the key (possibly
+        // stale, values only decrease) makes the atomic unnecessary, which
+        // removes most of the contention once few components remain
         const unsigned long long key = (unsigned long long)p << 32;
-        atomicMin(&best[cu], key | (uint32_t)cv);
-        atomicMin(&best[cv], key | (uint32_t)cu);
+        const unsigned long long ku = key | (uint32_t)cv, kv = key | (uint32_t)cu;
+        if (__ldcg(&best[cu]) > ku) atomicMin(&best[cu], ku);
+        if (__ldcg(&best[cv]) > kv) atomicMin(&best[cv], kv);
       }
     }
     const unsigned long long slot = block_reserve<kBlock>(&t->st[r + 1].E, keep ? 1u : 0u);
@@ -451,32 +455,14 @@ __global__ void k_round_resolve(CcPtrs b, const OffT* __restrict__ off) {
   }
 }
 
-// Pointer jumping over the component forest: shortcut every component to its root.
-__global__ void k_round_compress(CcPtrs b) {
-  CcCtl* t = b.ctl;
-  const int64_t C = (int64_t)t->st[t->cur].C;
-  int32_t* P2 = b.P2;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int32_t x = P2[c];
-    int64_t it = 0;
-    while (true) {
-      const int32_t y = P2[x];
-      if (y == x) break;
-      x = y;
-      if (++it > C) {
-        raise_error(b.status, DERR_ROUND_LIMIT);
-        break;
-      }
-    }
-    P2[c] = x;
-  }
-}
-
-// Dense ids for the roots that still have edges (their next-round hook slot
-// starts empty and their minimum vertex starts as their own); components
-// without edges are final and their minimum vertex joins the root list.
-__global__ void k_round_renumber(CcPtrs b) {
+// Pointer jumping over the component forest (every component shortcut to its
+// root, in place: only thread c writes P2[c], and any value another thread
+// reads is an ancestor), and dense ids for the roots that still have edges
+// (their next-round hook slot starts empty and their minimum vertex starts as
+// their own); components without edges are final and their minimum vertex
+// joins the root list.  Roots are fixed points, so the root test does not
+// depend on the shortcut.
+__global__ void k_round_settle(CcPtrs b) {
   CcCtl* t = b.ctl;
   const int r = t->cur;
   const int64_t C = (int64_t)t->st[r].C;
@@ -490,7 +476,19 @@ __global__ void k_round_renumber(CcPtrs b) {
     bool live_root = false, fin = false;
     if (c < C) {
       fin = best[c] == ~0ull;
-      live_root = !fin && b.P2[c] == (int32_t)c;
+      int32_t x = b.P2[c];
+      live_root = !fin && x == (int32_t)c;
+      int64_t it = 0;
+      while (true) {
+        const int32_t y = b.P2[x];
+        if (y == x) break;
+        x = y;
+        if (++it > C) {
+          raise_error(b.status, DERR_ROUND_LIMIT);
+          break;
+        }
+      }
+      b.P2[c] = x;
     }
     const unsigned long long id = block_reserve<kBlock>(&t->st[r + 1].C, live_root ? 1u : 0u);
     const unsigned long long rid = block_reserve<kBlock>(&b.counters[CNT_ROOTS], fin ? 1u : 0u);
@@ -503,7 +501,10 @@ __global__ void k_round_renumber(CcPtrs b) {
   }
 }
 
-__global__ void k_round_map(CcPtrs b) {
+// Component -> next id and minimum vertex per new component.  The last block
+// to finish advances the round and sets the loop condition (no separate
+// kernel; every block has read the round index before it counts itself done).
+__global__ void k_round_map(CcPtrs b, cudaGraphConditionalHandle h, int use_handle) {
   CcCtl* t = b.ctl;
   const int r = t->cur;
   const int64_t C = (int64_t)t->st[r].C;
@@ -527,23 +528,27 @@ __global__ void k_round_map(CcPtrs b) {
       if (fin) t->root_label = minv[c];
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&t->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    t->done = 0;
     t->st[r + 1].pool_at = t->st[r].pool_at + C;
     if (rc < 0) t->st[r + 1].rc = -1;
+    const int nr = r + 1;
+    bool more = t->st[nr].C > 0;
+    if (more && nr >= kMaxRounds) {
+      raise_error(b.status, DERR_ROUND_LIMIT);
+      more = false;
+    }
+    t->cur = nr;
+    if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
   }
-}
-
-// Next round; the loop continues while components remain.
-__global__ void k_round_advance(CcPtrs b, cudaGraphConditionalHandle h, int use_handle) {
-  CcCtl* t = b.ctl;
-  const int r = t->cur + 1;
-  t->cur = r;
-  bool more = t->st[r].C > 0;
-  if (more && r >= kMaxRounds) {
-    raise_error(b.status, DERR_ROUND_LIMIT);
-    more = false;
-  }
-  if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // Labels, backwards over rounds: lab_r[c] = minv_r[c] if final, else lab_{r+1}[next_r[c]].
@@ -596,10 +601,8 @@ static void launch_round_body(const CcPtrs& p, const OffT* off, cudaGraphConditi
   const int g = device_info().sms * 8;
   RST_LAUNCH(k_round_hook, g, kBlock, 0, s)(p);
   RST_LAUNCH(k_round_resolve<OffT>, g, kBlock, 0, s)(p, off);
-  RST_LAUNCH(k_round_compress, g, kBlock, 0, s)(p);
-  RST_LAUNCH(k_round_renumber, g, kBlock, 0, s)(p);
-  RST_LAUNCH(k_round_map, g, kBlock, 0, s)(p);
-  RST_LAUNCH(k_round_advance, 1, 1, 0, s)(p, h, use_handle);
+  RST_LAUNCH(k_round_settle, g, kBlock, 0, s)(p);
+  RST_LAUNCH(k_round_map, g, kBlock, 0, s)(p, h, use_handle);
 }
 
 template <class OffT>
@@ -736,7 +739,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   unsigned long long h[8];
   RST_TRY(fetch_u64(cnt, 8, h, s));
   const int rounds_done = hctl->cur;
-  if (!eager) count_launches(6LL * rounds_done);  // the round kernels the graph ran
+  if (!eager) count_launches(4LL * rounds_done);  // the round kernels the graph ran
   if (labels_out) {
     for (int r = rounds_done - 2; r >= 0; --r) {
       const int64_t Cr = (int64_t)hctl->st[r].C;
