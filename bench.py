@@ -462,6 +462,25 @@ def run_selector_report(off, col, root, torch):
             "source": "paper_2603_11645_gb300/selector_weights.json (timings collected on GB300)"}
 
 
+def run_profile_case(args):
+    """The CC+Euler step alone on a SIDE x SIDE permuted grid (seed 2), for
+    profiler captures: no timing, no oracle, no other strategies."""
+    import torch
+
+    import paper_2603_11645_gb300 as rst
+    from paper_2603_11645_gb300 import graphs
+    side = args.profile_case
+    g = graphs.grid(side, side, seed=2, permute=True, root="random")
+    off = torch.from_numpy(g.offsets).cuda()
+    col = torch.from_numpy(g.cols).cuda()
+    par = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        rst.build(off, col, g.root, "cc_euler", out=par)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": f"grid {side}x{side}", "n": g.n, "A": g.A,
+                      "launches": args.warmup + args.steps}))
+
+
 # ----------------------------------------------------------------- reference arm (the oracle)
 
 def run_reference(args, rank, world):
@@ -504,7 +523,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-families", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="SIDE",
+                    help="only run the CC+Euler step (W warm-up + K steps, no timing) on a SIDE x SIDE "
+                         "grid of the headline family; the command the ncu captures use")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))

@@ -41,7 +41,7 @@ struct RoundState {
   unsigned long long E;        // list entries entering the round (previous round's ids)
   unsigned long long pool_at;  // this round's slice of the next/minv pools
   int rc;                      // the requested root's component (-1: none)
-  int pad;
+  int bs;                      // stride between this round's hook slots (1 or kSpread)
 };
 struct CcCtl {
   RoundState st[kMaxRounds + 1];
@@ -69,6 +69,7 @@ struct CcBuffers {
   struct CcCtl* ctl; // device-resident round control
   int32_t* tile_row; // row of the first arc of every arc tile
   int64_t ecap;      // list capacity
+  int64_t bcap;      // slots in each best[] buffer
 };
 
 static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
@@ -84,6 +85,7 @@ static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
     b.Ecv[k] = ar.take<int32_t>(b.ecap);
     b.Ep[k] = ar.take<uint32_t>(b.ecap);
   }
+  b.bcap = half;
   b.best[0] = ar.take<unsigned long long>(half);
   b.best[1] = ar.take<unsigned long long>(half);
   b.P2 = ar.take<int32_t>(half);
@@ -226,7 +228,7 @@ __global__ void k_r1_label(int64_t n, const int32_t* __restrict__ P, const uint3
 // Arc-centric tiles: coalesced column loads, rows from a shared-memory scan,
 // independent label gathers, one slot reservation per tile.
 template <class OffT>
-__global__ void __launch_bounds__(kArcThreads) k_build_list(const OffT* __restrict__ off,
+__global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __restrict__ off,
                                                             const int32_t* __restrict__ col,
                                                             int64_t n, int64_t A,
                                                             const int32_t* __restrict__ C1,
@@ -237,20 +239,20 @@ __global__ void __launch_bounds__(kArcThreads) k_build_list(const OffT* __restri
                                                             const int32_t* __restrict__ tile_row,
                                                             unsigned long long* __restrict__ best,
                                                             uint32_t* status) {
-  __shared__ int32_t s_row[kArcTile];
+  __shared__ __align__(16) int32_t s_row[kArcTile];
   for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
     const int cnt = (int)(A - a0 < kArcTile ? A - a0 : kArcTile);
     const int64_t t = a0 / kArcTile;
     arc_tile_rows(off, n, a0, cnt, s_row, tile_row[t], tile_row[t + 1]);
+    // Survivors are written warp-contiguously per unrolled step (order in
+    // the list does not matter), so every store instruction is coalesced.
     int32_t bu[kArcPer], bv[kArcPer];
-    uint32_t bp[kArcPer];
     uint32_t mask = 0;
 #pragma unroll
     for (int k = 0; k < kArcPer; ++k) {
       const int i = k * kArcThreads + threadIdx.x;
       bu[k] = 0;
       bv[k] = 0;
-      bp[k] = 0;
       if (i < cnt) {
         const int32_t v = col[a0 + i];
         const int32_t u = s_row[i];
@@ -261,30 +263,39 @@ __global__ void __launch_bounds__(kArcThreads) k_build_list(const OffT* __restri
           const int32_t cv = C1[v];
           bu[k] = cu;
           bv[k] = cv;
-          bp[k] = (uint32_t)(a0 + i);
           if (cu != cv) {
             mask |= 1u << k;
-            // the first contraction round's hook, fused into the scan
+            // the first contraction round's hook, fused into the scan (a slot
+            // already below the key needs no atomic; slots only decrease)
             const unsigned long long key = (unsigned long long)(uint32_t)(a0 + i) << 32;
-            atomicMin(&best[cu], key | (uint32_t)cv);
-            atomicMin(&best[cv], key | (uint32_t)cu);
+            const unsigned long long ku = key | (uint32_t)cv, kv = key | (uint32_t)cu;
+            if (__ldcg(&best[cu]) > ku) atomicMin(&best[cu], ku);
+            if (__ldcg(&best[cv]) > kv) atomicMin(&best[cv], kv);
           }
         }
       }
     }
-    unsigned long long slot = block_reserve<kArcThreads>(counter, (unsigned)__popc(mask));
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned wtot = 0;
+#pragma unroll
+    for (int k = 0; k < kArcPer; ++k) wtot += __popc(__ballot_sync(0xffffffffu, (mask >> k) & 1u));
+    const unsigned long long mine = block_reserve<kArcThreads>(counter, lane == 0 ? wtot : 0u);
+    unsigned long long run = __shfl_sync(0xffffffffu, mine, 0);
 #pragma unroll
     for (int k = 0; k < kArcPer; ++k) {
-      if (mask & (1u << k)) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (mask >> k) & 1u);
+      if ((mask >> k) & 1u) {
+        const unsigned long long slot = run + __popc(bal & lt);
         if ((int64_t)slot < cap) {
           Ecu[slot] = bu[k];
           Ecv[slot] = bv[k];
-          Ep[slot] = bp[k];
+          Ep[slot] = (uint32_t)(a0 + k * kArcThreads + threadIdx.x);
         } else {
           raise_error(status, DERR_CAPACITY);
         }
-        ++slot;
       }
+      run += __popc(bal);
     }
     __syncthreads();
   }
@@ -301,6 +312,16 @@ __global__ void __launch_bounds__(kArcThreads) k_build_list(const OffT* __restri
 //    final components join the list of component roots
 //  4 map: component -> next id; minimum vertex per new component; the last
 //    block advances the round and sets the loop condition
+
+// Once few components remain, every list entry hits one of a few hook slots;
+// packed together they fall on a handful of L2 lines (and slices), which then
+// serialise the atomics.  Rounds entering with at most kSpreadMaxC components
+// give every slot its own 128-byte line when the buffer has room.
+constexpr int kSpread = 16;
+constexpr int64_t kSpreadMaxC = 1 << 16;
+__device__ __forceinline__ int64_t next_round_stride(int64_t C, int64_t cap) {
+  return (C <= kSpreadMaxC && C * kSpread <= cap) ? kSpread : 1;
+}
 
 struct CcPtrs {
   const int32_t* col;
@@ -319,6 +340,7 @@ struct CcPtrs {
   unsigned long long* counters;
   uint32_t* status;
   int64_t ecap;
+  int64_t bcap;  // slots in each best[] buffer
 };
 
 __global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__ C1) {
@@ -331,6 +353,7 @@ __global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__
     t->st[0].C = C;
     t->st[0].E = 0;  // the list build already hooked round 0; its list is round 1's
     t->st[0].pool_at = 0;
+    t->st[0].bs = 1;
     const int32_t c1 = root >= 0 ? C1[root] : -1;
     t->st[0].rc = c1;
     t->root_label = (root >= 0 && c1 < 0) ? root : -1;
@@ -338,13 +361,25 @@ __global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__
   }
 }
 
+// With at most kHookLocal components, entries first meet in a block-local
+// copy of the hook slots (shared memory) and each block then offers one key
+// per touched slot, instead of every entry contending on a few global slots.
+constexpr int kHookLocal = 1024;
 __global__ void k_round_hook(CcPtrs b) {
+  __shared__ unsigned long long s_best[kHookLocal];
   CcCtl* t = b.ctl;
   const int r = t->cur;
   const int64_t E = (int64_t)t->st[r].E;
+  const int64_t Cr = (int64_t)t->st[r].C;
+  const bool local = Cr <= kHookLocal;
+  if (local) {
+    for (int c = threadIdx.x; c < Cr; c += blockDim.x) s_best[c] = ~0ull;
+    __syncthreads();
+  }
   const int src = r & 1, dst = src ^ 1;
   const int32_t* __restrict__ mp = r == 0 ? nullptr : b.nextpool + t->st[r - 1].pool_at;
   unsigned long long* __restrict__ best = b.best[r & 1];
+  const int64_t bs = t->st[r].bs;
   const int32_t* __restrict__ Icu = b.Ecu[src];
   const int32_t* __restrict__ Icv = b.Ecv[src];
   const uint32_t* __restrict__ Ip = b.Ep[src];
@@ -369,8 +404,15 @@ __global__ void k_round_hook(CcPtrs b) {
         // removes most of the contention once few components remain
         const unsigned long long key = (unsigned long long)p << 32;
         const unsigned long long ku = key | (uint32_t)cv, kv = key | (uint32_t)cu;
-        if (__ldcg(&best[cu]) > ku) atomicMin(&best[cu], ku);
-        if (__ldcg(&best[cv]) > kv) atomicMin(&best[cv], kv);
+        if (local) {
+          atomicMin(&s_best[cu], ku);
+          atomicMin(&s_best[cv], kv);
+        } else {
+          unsigned long long* su = &best[cu * bs];
+          unsigned long long* sv = &best[cv * bs];
+          if (__ldcg(su) > ku) atomicMin(su, ku);
+          if (__ldcg(sv) > kv) atomicMin(sv, kv);
+        }
       }
     }
     const unsigned long long slot = block_reserve<kBlock>(&t->st[r + 1].E, keep ? 1u : 0u);
@@ -382,6 +424,14 @@ __global__ void k_round_hook(CcPtrs b) {
       } else {
         raise_error(b.status, DERR_CAPACITY);
       }
+    }
+  }
+  if (local) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < Cr; c += blockDim.x) {
+      const unsigned long long k = s_best[c];
+      unsigned long long* g = &best[c * bs];
+      if (k != ~0ull && __ldcg(g) > k) atomicMin(g, k);
     }
   }
 }
@@ -419,24 +469,25 @@ __global__ void k_round_resolve(CcPtrs b, const OffT* __restrict__ off) {
   const int r = t->cur;
   const int64_t C = (int64_t)t->st[r].C;
   const unsigned long long* __restrict__ best = b.best[r & 1];
+  const int64_t bs = t->st[r].bs;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < C; base += stride) {
     const int64_t c = base + threadIdx.x;
     bool emit = false;
     uint4 rec = make_uint4(0, 0, 0, 0);
     if (c < C) {
-      const unsigned long long bc = best[c];
+      const unsigned long long bc = best[c * bs];
       if (bc == ~0ull) {
         b.P2[c] = (int32_t)c;
       } else {
         const int32_t c2 = (int32_t)(uint32_t)(bc & 0xffffffffull);
         const uint32_t p = (uint32_t)(bc >> 32);
-        const bool mutual = (uint32_t)(best[c2] >> 32) == p;
+        const int32_t bb = b.col[p];  // issued with the partner's slot read
+        const bool mutual = (uint32_t)(best[(int64_t)c2 * bs] >> 32) == p;
         if (mutual && (int32_t)c < c2) {
           b.P2[c] = (int32_t)c;
         } else {
           b.P2[c] = c2;
-          const int32_t bb = b.col[p];
           int32_t a = 0;
           int64_t q = 0;
           if (twin_of_position(off, b.col, bb, (uint64_t)p, &a, &q)) {
@@ -468,6 +519,7 @@ __global__ void k_round_settle(CcPtrs b) {
   const int64_t C = (int64_t)t->st[r].C;
   const unsigned long long* __restrict__ best = b.best[r & 1];
   unsigned long long* __restrict__ best_next = b.best[(r + 1) & 1];
+  const int64_t bs = t->st[r].bs, bsn = next_round_stride(C, b.bcap);
   const int32_t* __restrict__ minv = b.minvpool + t->st[r].pool_at;
   int32_t* __restrict__ minv_next = b.minvpool + t->st[r].pool_at + C;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -475,7 +527,7 @@ __global__ void k_round_settle(CcPtrs b) {
     const int64_t c = base + threadIdx.x;
     bool live_root = false, fin = false;
     if (c < C) {
-      fin = best[c] == ~0ull;
+      fin = best[c * bs] == ~0ull;
       int32_t x = b.P2[c];
       live_root = !fin && x == (int32_t)c;
       int64_t it = 0;
@@ -495,7 +547,7 @@ __global__ void k_round_settle(CcPtrs b) {
     if (c < C) b.NID[c] = live_root ? (int32_t)id : -1;
     if (fin) b.roots[rid] = minv[c];
     if (live_root) {
-      best_next[id] = ~0ull;
+      best_next[(int64_t)id * bsn] = ~0ull;
       minv_next[id] = minv[c];
     }
   }
@@ -513,9 +565,14 @@ __global__ void k_round_map(CcPtrs b, cudaGraphConditionalHandle h, int use_hand
   int32_t* __restrict__ minv_next = b.minvpool + t->st[r].pool_at + C;
   int32_t* __restrict__ next = b.nextpool + t->st[r].pool_at;
   const int rc = t->st[r].rc;
+  const int64_t bs = t->st[r].bs;
+  // blocks past the work neither map nor count themselves done
+  const int64_t want = (C + blockDim.x - 1) / blockDim.x;
+  const unsigned nb = want < 1 ? 1u : (want < (int64_t)gridDim.x ? (unsigned)want : gridDim.x);
+  if (blockIdx.x >= nb) return;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const bool fin = best[c] == ~0ull;
+    const bool fin = best[c * bs] == ~0ull;
     int32_t nc = kFinal;
     if (!fin) {
       const int32_t root = b.P2[c];
@@ -532,13 +589,14 @@ __global__ void k_round_map(CcPtrs b, cudaGraphConditionalHandle h, int use_hand
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = atomicAdd(&t->done, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(&t->done, 1u) == nb - 1;
   }
   __syncthreads();
   if (s_last && threadIdx.x == 0) {
     __threadfence();
     t->done = 0;
     t->st[r + 1].pool_at = t->st[r].pool_at + C;
+    t->st[r + 1].bs = (int)next_round_stride(C, b.bcap);
     if (rc < 0) t->st[r + 1].rc = -1;
     const int nr = r + 1;
     bool more = t->st[nr].C > 0;
@@ -697,6 +755,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   p.counters = cnt;
   p.status = status;
   p.ecap = b.ecap;
+  p.bcap = b.bcap;
   RST_LAUNCH(k_round_init, grid_for(n / 2 + 1), kBlock, 0, s)(p, root, b.C1);
   prof_mark(s, "k_round_init");
   if (A > 0) {

@@ -126,7 +126,8 @@ __global__ void k_arc_tile_rows(const OffT* __restrict__ off, int64_t n, int64_t
 
 // Fills s_row[i] with the row of arc a0 + i for i < cnt, given r0 = the row
 // of arc a0 and r1 >= the row of arc a0 + cnt - 1 (from k_arc_tile_rows).
-// Call from all threads of a kArcThreads block; ends with __syncthreads().
+// Call from all threads of a kArcThreads block; s_row must be 16-byte
+// aligned.  Ends with __syncthreads().
 template <class OffT>
 __device__ __forceinline__ void arc_tile_rows(const OffT* __restrict__ off, int64_t n, int64_t a0,
                                               int cnt, int32_t* s_row, int64_t r0, int64_t r1) {
@@ -139,13 +140,20 @@ __device__ __forceinline__ void arc_tile_rows(const OffT* __restrict__ off, int6
   }
   if (threadIdx.x == 0) atomicMax(&s_row[0], (int32_t)r0);
   __syncthreads();
-  // inclusive max-scan: kArcPer consecutive entries per thread, then across threads
-  const int base = threadIdx.x * kArcPer;
+  // inclusive max-scan: kArcPer consecutive entries per thread (two 16-byte
+  // shared loads, free of bank conflicts), then across threads
+  static_assert(kArcPer == 8, "the scan reads two int4 per thread");
   int32_t v[kArcPer];
+  {
+    const int4 lo4 = reinterpret_cast<const int4*>(s_row)[2 * threadIdx.x];
+    const int4 hi4 = reinterpret_cast<const int4*>(s_row)[2 * threadIdx.x + 1];
+    v[0] = lo4.x; v[1] = lo4.y; v[2] = lo4.z; v[3] = lo4.w;
+    v[4] = hi4.x; v[5] = hi4.y; v[6] = hi4.z; v[7] = hi4.w;
+  }
   int32_t run = -1;
 #pragma unroll
   for (int k = 0; k < kArcPer; ++k) {
-    run = max(run, s_row[base + k]);
+    run = max(run, v[k]);
     v[k] = run;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -161,8 +169,10 @@ __device__ __forceinline__ void arc_tile_rows(const OffT* __restrict__ off, int6
   for (int w = 0; w < warp; ++w) carry = max(carry, s_warp[w]);
   const int32_t prev = __shfl_up_sync(0xffffffffu, x, 1);
   if (lane > 0) carry = max(carry, prev);
-#pragma unroll
-  for (int k = 0; k < kArcPer; ++k) s_row[base + k] = max(v[k], carry);
+  reinterpret_cast<int4*>(s_row)[2 * threadIdx.x] =
+      make_int4(max(v[0], carry), max(v[1], carry), max(v[2], carry), max(v[3], carry));
+  reinterpret_cast<int4*>(s_row)[2 * threadIdx.x + 1] =
+      make_int4(max(v[4], carry), max(v[5], carry), max(v[6], carry), max(v[7], carry));
   __syncthreads();
 }
 

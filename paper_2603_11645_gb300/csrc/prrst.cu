@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kArcThreads) k_pr_hook(const OffT* __restrict_
                                                          int64_t n, int64_t A, const int32_t* __restrict__ tile_row,
                                                          const int32_t* __restrict__ rep, int max_rule,
                                                          unsigned long long* __restrict__ best) {
-  __shared__ int32_t s_row[kArcTile];
+  __shared__ __align__(16) int32_t s_row[kArcTile];
   for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
     const int cnt = (int)(A - a0 < kArcTile ? A - a0 : kArcTile);
     const int64_t t = a0 / kArcTile;
