@@ -196,6 +196,8 @@ def run_ours(args, rank, world, local_rank):
     L.rst_last_stats.argtypes = [ctypes.c_void_p, ctypes.c_int]
 
     g = graphs.workload_grid4096()
+    from paper_2603_11645_gb300 import autotune
+    tuning = autotune.apply(g.n, g.A)  # the tuned knobs of this size bucket (defaults if untuned)
     off = torch.from_numpy(g.offsets).to(dev)
     col = torch.from_numpy(g.cols).to(dev)
     par = torch.empty(g.n, dtype=torch.int32, device=dev)
@@ -325,6 +327,12 @@ def run_ours(args, rank, world, local_rank):
         pr_ms.append(e0.elapsed_time(e1))
     pr_med = statistics.median(pr_ms)
 
+    # tree shape (Fig. 2): heights of the trees each strategy returns
+    heights = {}
+    for strat in ("cc_euler", "bfs", "pr_rst"):
+        step(strat)
+        heights[strat] = rst.tree_depth(par, want_depths=False)[1]
+
     batch = None if args.no_batch else run_batch(args, dev, stream, rst, graphs, torch)
     families = None if args.no_families else run_families(args, dev, stream, rst, graphs, torch)
     selector = run_selector_report(off, col, g.root, torch)
@@ -344,7 +352,7 @@ def run_ours(args, rank, world, local_rank):
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "strategy": "cc_euler",
                        "l2": "L2 flushed (258 MB write) before every timed step; inputs also exceed L2",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU", "tuning": tuning},
             "e2e": {"value": e2e_value, "unit": "edges/s",
                     "h2d_bytes_per_step": int(g.offsets.nbytes + g.cols.nbytes),
                     "d2h_bytes_per_step": int(4 * g.n)},
@@ -357,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
                     "cc_euler_speedup": bfs_med / ms_step},
             "pr_rst": {"value": g.m / (pr_med / 1e3), "unit": "edges/s", "ms_per_step": pr_med,
                        "cc_euler_speedup": pr_med / ms_step},
+            "tree_height": heights,
             "batch": batch,
             "families": families,
             "selector": selector,
@@ -369,6 +378,8 @@ def run_ours(args, rank, world, local_rank):
 def run_batch(args, dev, stream, rst, graphs, torch):
     """4096 mixed graphs: one rst_build_batch call vs one rst_build call per graph."""
     b = graphs.workload_batch()
+    from paper_2603_11645_gb300 import autotune
+    autotune.apply(b.N, b.A)
     off = torch.from_numpy(b.offsets).to(dev)
     col = torch.from_numpy(b.cols).to(dev)
     vo = torch.from_numpy(b.vtx_off).to(dev)
@@ -431,6 +442,8 @@ def _time(fn, reps, torch, dev, stream, flush=None):
 def run_families(args, dev, stream, rst, graphs, torch):
     """The power-law family: R-MAT scale 22 (edge factor 16, connected, int64 offsets)."""
     g = graphs.rmat(22, 16, seed=3, connect=True, offsets_bits=64)
+    from paper_2603_11645_gb300 import autotune
+    autotune.apply(g.n, g.A)
     off = torch.from_numpy(g.offsets).to(dev)
     col = torch.from_numpy(g.cols).to(dev)
     par = torch.empty(g.n, dtype=torch.int32, device=dev)

@@ -171,6 +171,21 @@ rst_status rst_verify(const void *csr_offsets, int offsets_bits, const int32_t *
                       int64_t n, int64_t m, int32_t root, const int32_t *parent,
                       int32_t *verdict_out, rst_stream_t stream);
 
+/* rst_tree_depth -- depth of every vertex of a rooted forest, and its height
+ * (Section IV-B, Fig. 2: the trees of connectivity-based strategies are
+ * deeper than BFS trees; this measures that trade-off on any parent array).
+ *   parent     device int32[n], parent[v] == v exactly at roots (the output of
+ *              rst_build with any strategy).
+ *   depth_out  device int32[n] or NULL: edges from v up to its root.  Used as
+ *              scratch during the call.
+ *   max_out    host int64 or NULL: the largest depth (0 for an edgeless forest).
+ * Pointer jumping with distances, about log2(height) + 1 rounds.  Returns
+ * RST_ERR_INVALID_ARG for a parent outside [0, n) and RST_ERR_NOT_CONVERGED
+ * when some parent chain never reaches a root (a cycle).  Synchronises
+ * `stream` once per round. */
+rst_status rst_tree_depth(const int32_t *parent, int64_t n, int32_t *depth_out, int64_t *max_out,
+                          rst_stream_t stream);
+
 /*
  * rst_build_noalloc -- the CC+Euler rooted spanning tree of rst_build, for
  * callers that cannot allocate memory: code running while a stream is being
@@ -222,7 +237,20 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *   adam_m/adam_v[5187], loss_out float[1], loss_hist float[epochs]).
  * rst_set_option: "bfs_max_levels" caps BFS at that many levels (0: no cap;
  *   a capped search returns RST_ERR_NOT_CONVERGED) -- used to censor BFS
- *   timings on very deep graphs when collecting selector training data. */
+ *   timings on very deep graphs when collecting selector training data.
+ *   The other keys change speed only, never a result.  They play the part of
+ *   the launch-granularity choice Section III-C makes for PR-RST (several
+ *   pointer jumps per global synchronisation, chosen empirically); the
+ *   package's autotune module searches them offline per size bucket:
+ *     "lr_spacing"            list-ranking splitter spacing K, a power of two
+ *                             in [16, 512] (default 16);
+ *     "round_blocks_per_sm"   grid of the contraction-round kernels, in resident
+ *                             256-thread blocks per SM, [1, 16] (default 8);
+ *     "bfs_bottom_up_divisor" BFS steps bottom-up while the frontier holds more
+ *                             than n / divisor vertices, [1, 10^6] (default 20).
+ *   Out-of-range values and unknown keys return RST_ERR_INVALID_ARG and change
+ *   nothing.  Options are process-wide: set them between calls, not during.
+ * rst_get_option: reads the current value of any key above into *value (host). */
 rst_status rst_selector_features(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols,
                                  int64_t n, int64_t m, int32_t root, float *features_out,
                                  rst_stream_t stream);
@@ -240,6 +268,7 @@ rst_status rst_mlp_train(float *params, const float *X, const float *T, int batc
                          float lr, float *adam_m, float *adam_v, float *loss_hist,
                          rst_stream_t stream);
 rst_status rst_set_option(const char *key, long long value);
+rst_status rst_get_option(const char *key, long long *value);
 
 /* ---- diagnostics (no counterpart in the paper) ----------------------------
  * rst_launch_count: number of kernels this library has launched since load.

@@ -16,6 +16,8 @@ Parity status per function (what pins each one, see tests/test_oracle_pins.py):
 * ``verify``       pinned: Kirchhoff spanning-tree counts (n <= 6), mutations.
 * ``prrst``        parity unpinned for its edge set (the paper fixes no unique
                    tree); its output is pinned only through ``verify``.
+* ``tree_depths``  pinned: closed forms (path, star, grid comb), BFS-tree
+                   depth equals the BFS level, cycle and range rejection.
 """
 from __future__ import annotations
 
@@ -136,3 +138,34 @@ def prrst(n, offsets, cols, root):
     if rc != 0:
         raise ValueError(f"or_prrst failed: {rc}")
     return par[:n].copy(), rounds.value
+
+
+def tree_depths(n, parent):
+    """Depth of every vertex of a rooted forest (edges up to the root; roots
+    have parent[v] == v) by walking each parent chain once, remembering the
+    depths already known.  Raises ValueError for a parent outside [0, n) or a
+    chain that returns to a vertex of its own walk (a cycle).  The tree-shape
+    measure of Section IV-B / Fig. 2."""
+    par = np.asarray(parent, dtype=np.int64)
+    if n and (par.min() < 0 or par.max() >= n):
+        raise ValueError("parent out of range")
+    depth = np.full(n, -1, dtype=np.int64)
+    for v in range(n):
+        if depth[v] >= 0:
+            continue
+        chain = []
+        on_chain = set()
+        x = v
+        while depth[x] < 0 and par[x] != x:
+            if x in on_chain:
+                raise ValueError("cycle")
+            on_chain.add(x)
+            chain.append(x)
+            x = int(par[x])
+        d = 0 if depth[x] < 0 else int(depth[x])  # x is a root or already known
+        if depth[x] < 0:
+            depth[x] = 0
+        for y in reversed(chain):
+            d += 1
+            depth[y] = d
+    return depth

@@ -10,7 +10,8 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["build", "build_batch", "cc", "euler_root", "verify", "lib", "RstError", "STRATEGIES"]
+__all__ = ["build", "build_batch", "cc", "euler_root", "verify", "tree_depth", "set_option", "get_option", "lib",
+           "RstError", "STRATEGIES"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librst.so")
@@ -42,10 +43,14 @@ def lib():
         L.rst_euler_root.argtypes = [I64, P, I64, I32, P, P, P]
         L.rst_verify.argtypes = [P, I, P, I64, I64, I32, P, P, P]
         L.rst_build_batch.argtypes = [P, I, P, P, P, I32, P, I, P, P]
+        L.rst_tree_depth.argtypes = [P, I64, P, P, P]
+        L.rst_set_option.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
+        L.rst_get_option.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong)]
         L.rst_status_string.argtypes = [I]
         L.rst_status_string.restype = ctypes.c_char_p
         L.rst_version.restype = I
-        for fn in ("rst_build", "rst_cc", "rst_euler_root", "rst_verify", "rst_shutdown"):
+        for fn in ("rst_build", "rst_cc", "rst_euler_root", "rst_verify", "rst_shutdown", "rst_set_option", "rst_tree_depth",
+                   "rst_get_option"):
             getattr(L, fn).restype = I
         for fn in ("rst_build_batch", "rst_select", "rst_build_batch_graph"):
             if hasattr(L, fn):
@@ -57,6 +62,18 @@ def lib():
 def _check(fn, code):
     if code != 0:
         raise RstError(fn, code)
+
+
+def set_option(key: str, value: int) -> None:
+    """rst_set_option: a tuning knob ("lr_spacing", "round_blocks_per_sm",
+    "bfs_bottom_up_divisor") or the BFS level cap ("bfs_max_levels")."""
+    _check("rst_set_option", lib().rst_set_option(key.encode(), int(value)))
+
+
+def get_option(key: str) -> int:
+    v = ctypes.c_longlong(0)
+    _check("rst_get_option", lib().rst_get_option(key.encode(), ctypes.byref(v)))
+    return int(v.value)
 
 
 def _stream(stream=None):
@@ -148,3 +165,18 @@ def verify(offsets, cols, root: int, parent, stream=None) -> int:
                             int(root), ctypes.c_void_p(parent.data_ptr()), ctypes.byref(v), _stream(stream))
     _check("rst_verify", code)
     return int(v.value)
+
+
+def tree_depth(parent, want_depths: bool = True, stream=None):
+    """Depth of every vertex of a rooted forest (device int32 tensor, or None)
+    and the forest's height."""
+    import torch
+    assert parent.is_cuda and parent.dtype == torch.int32 and parent.is_contiguous()
+    n = parent.numel()
+    depth = torch.empty(n, dtype=torch.int32, device=parent.device) if want_depths else None
+    mx = ctypes.c_int64(0)
+    code = lib().rst_tree_depth(ctypes.c_void_p(parent.data_ptr()), n,
+                                ctypes.c_void_p(depth.data_ptr()) if depth is not None else None,
+                                ctypes.byref(mx), _stream(stream))
+    _check("rst_tree_depth", code)
+    return depth, int(mx.value)

@@ -168,6 +168,21 @@ rst_status rst_verify(const void* csr_offsets, int offsets_bits, const int32_t* 
   return run_verify(csr_offsets, offsets_bits, csr_cols, n, m, root, parent, verdict_out, s);
 }
 
+rst_status rst_tree_depth(const int32_t* parent, int64_t n, int32_t* depth_out, int64_t* max_out,
+                          rst_stream_t stream) {
+  if (n < 0 || n >= ((int64_t)1 << 30)) return RST_ERR_INVALID_ARG;
+  if (n > 0 && !parent) return RST_ERR_INVALID_ARG;
+  if (n == 0) {
+    if (max_out) *max_out = 0;
+    return RST_OK;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CallGuard g;
+  RST_TRY(ensure_workspace(depth_workspace_bytes(n)));
+  RST_TRY(reset_device_error(s));
+  return tree_depth(parent, n, depth_out, max_out, s);
+}
+
 rst_status rst_shutdown(void) {
   CallGuard g;
   destroy_round_graphs();

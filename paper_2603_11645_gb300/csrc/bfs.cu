@@ -213,6 +213,7 @@ size_t bfs_workspace_bytes(int64_t n) {
 
 static long long g_bfs_max_levels = 0;  // 0: unlimited (rst_set_option "bfs_max_levels")
 void set_bfs_max_levels(long long v) { g_bfs_max_levels = v; }
+long long get_bfs_max_levels() { return g_bfs_max_levels; }
 
 // The search itself; buffers come from `ar` (sized by bfs_workspace_bytes).
 // With a probe, only the root's search runs, for at most probe->max_levels
@@ -266,7 +267,7 @@ static rst_status bfs_core(Arena& ar, const OffT* off, const int32_t* col, int64
         }
         if (!probe && g_bfs_max_levels > 0 && L >= g_bfs_max_levels) return RST_ERR_NOT_CONVERGED;
         RST_CUDA(cudaMemsetAsync(&cnt[BC_NEXT], 0, sizeof(unsigned long long), s));
-        const bool want_bu = nf > n / 20;
+        const bool want_bu = nf > n / tuning().bfs_bu_div;
         if (want_bu) {
           RST_LAUNCH(k_bfs_bu<OffT>, gN, kBlock, 0, s)(off, col, n, L, level, parent, q2, cnt);
         } else if (thread_td) {

@@ -630,8 +630,8 @@ __global__ void k_label_vertices(int64_t n, const int32_t* __restrict__ C1,
 
 // ------------------------------------------------------------------ round graph
 
-// One instantiated graph per (workspace, graph) binding: a while-conditional
-// node whose body is the six round kernels.
+// One instantiated graph per (workspace, graph, round grid) binding: a
+// while-conditional node whose body is the four round kernels.
 struct RoundGraph {
   bool valid = false;
   const void* key_off = nullptr;
@@ -639,6 +639,7 @@ struct RoundGraph {
   const void* key_ws = nullptr;
   int64_t key_n = 0, key_A = 0;
   int key_dev = -1;
+  int key_grid = 0;
   cudaGraphExec_t exec = nullptr;
 };
 constexpr int kGraphCache = 8;
@@ -656,7 +657,7 @@ void destroy_round_graphs() {
 template <class OffT>
 static void launch_round_body(const CcPtrs& p, const OffT* off, cudaGraphConditionalHandle h,
                               int use_handle, cudaStream_t s) {
-  const int g = device_info().sms * 8;
+  const int g = device_info().sms * tuning().round_bps;
   RST_LAUNCH(k_round_hook, g, kBlock, 0, s)(p);
   RST_LAUNCH(k_round_resolve<OffT>, g, kBlock, 0, s)(p, off);
   RST_LAUNCH(k_round_settle, g, kBlock, 0, s)(p);
@@ -670,7 +671,7 @@ static rst_status round_graph_for(const CcPtrs& p, const OffT* off, int64_t n, i
   RST_CUDA(cudaGetDevice(&dev));
   for (auto& g : g_round_graphs) {
     if (g.valid && g.key_off == off && g.key_col == p.col && g.key_ws == (const void*)p.ctl &&
-        g.key_n == n && g.key_A == A && g.key_dev == dev) {
+        g.key_n == n && g.key_A == A && g.key_dev == dev && g.key_grid == tuning().round_bps) {
       *out = g.exec;
       return RST_OK;
     }
@@ -708,6 +709,7 @@ static rst_status round_graph_for(const CcPtrs& p, const OffT* off, int64_t n, i
   slot.key_n = n;
   slot.key_A = A;
   slot.key_dev = dev;
+  slot.key_grid = tuning().round_bps;
   slot.exec = exec;
   *out = exec;
   return RST_OK;

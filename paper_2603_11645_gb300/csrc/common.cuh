@@ -74,6 +74,16 @@ struct Device {
 };
 const Device& device_info();
 
+// Launch and sampling parameters that change no result, only speed; set by
+// rst_set_option (an offline tuner picks them per size bucket).  Process-wide:
+// change them only between calls.
+struct Tuning {
+  int lr_shift = 4;     // list ranking: one splitter per 2^lr_shift elements (16..512)
+  int round_bps = 8;    // contraction-round kernels: resident blocks per SM in the grid (1..16)
+  int bfs_bu_div = 20;  // BFS steps bottom-up while the frontier exceeds n / bfs_bu_div
+};
+Tuning& tuning();
+
 // Grid for a grid-stride loop over `work` items: at most `waves` resident
 // blocks per SM, at least 1 block.
 inline int grid_for(int64_t work, int block = kBlock, int waves = 8) {

@@ -1,8 +1,9 @@
 // Parallel list ranking (Section III-D: every arc gets its position in its
 // tree's Euler tour, each tree ranked independently).
 //
-// Sparse ruling set with recursion.  Every K-th element (by index) and every
-// list head is a splitter; one thread per splitter walks its sublist up to the
+// Sparse ruling set with recursion.  Every K-th element by index (K = 2^sh,
+// 16 unless rst_set_option("lr_spacing") changes it) and every list head is a
+// splitter; one thread per splitter walks its sublist up to the
 // next splitter, reading the successor array (read-only) and writing one
 // 8-byte {owner splitter, offset} record per element to a separate array.
 // (Overwriting the successor record in place is several times slower on
@@ -20,7 +21,7 @@
 
 namespace rst {
 
-constexpr int kLrK = 16;                 // splitter spacing (power of two)
+constexpr int kLrMinShift = 4, kLrMaxShift = 9;  // splitter spacing 2^sh: 16 (default) .. 512
 constexpr int kLrBase = 4096;            // shared-memory Wyllie base case
 constexpr int kLrBaseThreads = 1024;
 constexpr int kLrWalkThreads = 128;
@@ -36,7 +37,7 @@ struct LevelBufs {
   uint32_t* spos;   // S positions of the splitters
 };
 
-static int64_t lr_splitters(int64_t N, int64_t h) { return (N + kLrK - 1) / kLrK + h; }
+static int64_t lr_splitters(int64_t N, int64_t h, int sh) { return ((N + (1LL << sh) - 1) >> sh) + h; }
 
 // Walks the workspace plan: identical calls for the counting pass and the run.
 // Fixed-capacity level list (no host allocation on the ranking path).
@@ -49,10 +50,10 @@ struct LevelList {
   }
 };
 
-static void lr_layout(Arena& ar, int64_t N, int64_t h, LevelList* levels,
+static void lr_layout(Arena& ar, int64_t N, int64_t h, int sh, LevelList* levels,
                       int32_t** wyl_pj, uint32_t** wyl_val, int32_t** wyl_flag) {
   while (N > kLrBase && h <= N / 4) {
-    const int64_t S = lr_splitters(N, h);
+    const int64_t S = lr_splitters(N, h, sh);
     LevelBufs b;
     b.ol = ar.take<int2>(N);
     b.snext = ar.take<int32_t>(S);
@@ -70,14 +71,20 @@ static void lr_layout(Arena& ar, int64_t N, int64_t h, LevelList* levels,
   }
 }
 
+// Bytes for any allowed spacing (the largest of the layouts), so the spacing
+// can change between calls without resizing.
 size_t list_rank_workspace_bytes(int64_t N, int64_t nheads) {
-  Arena a;
-  a.counting = true;
-  int32_t* p = nullptr;
-  uint32_t* v = nullptr;
-  int32_t* f = nullptr;
-  lr_layout(a, N, nheads, nullptr, &p, &v, &f);
-  return a.used;
+  size_t most = 0;
+  for (int sh = kLrMinShift; sh <= kLrMaxShift; ++sh) {
+    Arena a;
+    a.counting = true;
+    int32_t* p = nullptr;
+    uint32_t* v = nullptr;
+    int32_t* f = nullptr;
+    lr_layout(a, N, nheads, sh, nullptr, &p, &v, &f);
+    if (a.used > most) most = a.used;
+  }
+  return most;
 }
 
 size_t list_rank_workspace_upper(int64_t N) {
@@ -92,16 +99,17 @@ size_t list_rank_workspace_upper(int64_t N) {
 
 __device__ __forceinline__ uint32_t wget(const uint32_t* w, int64_t x) { return w ? w[x] : 1u; }
 
-__global__ void k_lr_heads(int64_t N, int64_t S0, const int32_t* __restrict__ heads, int64_t h,
+__global__ void k_lr_heads(int64_t N, int64_t S0, int sh, const int32_t* __restrict__ heads, int64_t h,
                            int32_t* __restrict__ sstart, int32_t* __restrict__ shead) {
+  const int32_t mask = (1 << sh) - 1;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < h;
        j += (int64_t)gridDim.x * blockDim.x) {
     const int32_t x = heads[j];
     if (x < 0) {  // a list without elements: no splitter
       shead[j] = -1;
       sstart[S0 + j] = -1;
-    } else if ((x & (kLrK - 1)) == 0) {
-      shead[j] = x / kLrK;
+    } else if ((x & mask) == 0) {
+      shead[j] = x >> sh;
       sstart[S0 + j] = -1;
     } else {
       shead[j] = (int32_t)(S0 + j);
@@ -111,7 +119,7 @@ __global__ void k_lr_heads(int64_t N, int64_t S0, const int32_t* __restrict__ he
 }
 
 // One thread per splitter: ol[x] = {owner splitter, weighted offset}.
-__global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S0, int64_t S,
+__global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S0, int64_t S, int sh,
                                                             const int32_t* __restrict__ nxt,
                                                             const uint32_t* __restrict__ w,
                                                             const int32_t* __restrict__ sstart,
@@ -121,9 +129,10 @@ __global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S
                                                             unsigned long long* visited,
                                                             uint32_t* status) {
   unsigned long long seen = 0;
+  const int32_t mask = (1 << sh) - 1;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
        s += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t start = s < S0 ? s * kLrK : (int64_t)sstart[s];
+    const int64_t start = s < S0 ? s << sh : (int64_t)sstart[s];
     if (start < 0) {
       snext[s] = -1;
       w_next[s] = 0;
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S
     uint32_t acc = wget(w, start);
     int32_t x = nxt[start];
     int64_t steps = 1;
-    while (x >= 0 && (x & (kLrK - 1)) != 0) {
+    while (x >= 0 && (x & mask) != 0) {
       ol[x] = make_int2((int32_t)s, (int32_t)acc);
       acc += wget(w, x);
       x = nxt[x];
@@ -143,7 +152,7 @@ __global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S
         break;
       }
     }
-    snext[s] = x < 0 ? -1 : x / kLrK;
+    snext[s] = x < 0 ? -1 : x >> sh;
     w_next[s] = acc;
     seen += (unsigned long long)steps;
   }
@@ -252,7 +261,8 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   int32_t* wpj = nullptr;
   uint32_t* wval = nullptr;
   int32_t* wflag = nullptr;
-  lr_layout(ar, N, nheads, &levels, &wpj, &wval, &wflag);
+  const int sh = tuning().lr_shift;
+  lr_layout(ar, N, nheads, sh, &levels, &wpj, &wval, &wflag);
   if (levels.count > kLrMaxLevels) return RST_ERR_UNSUPPORTED;
   for (int l = 0; l < levels.count; ++l)
     if (!levels.b[l].spos) return RST_ERR_OOM;
@@ -272,13 +282,13 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   Frame f{N, nxt, w, heads, pos};
   for (int l = 0; l < levels.count; ++l) {
     LevelBufs& b = levels.b[l];
-    const int64_t S0 = (f.N + kLrK - 1) / kLrK;
+    const int64_t S0 = (f.N + (1LL << sh) - 1) >> sh;
     const int64_t S = S0 + nheads;
     if (l == 0) RST_CUDA(cudaMemsetAsync(visited, 0, sizeof(unsigned long long), s));
-    RST_LAUNCH(k_lr_heads, grid_for(nheads), kBlock, 0, s)(f.N, S0, f.heads, nheads, b.sstart, b.shead);
+    RST_LAUNCH(k_lr_heads, grid_for(nheads), kBlock, 0, s)(f.N, S0, sh, f.heads, nheads, b.sstart, b.shead);
     prof_mark(s, l == 0 ? "lr_prep1" : "lr_prep");
     RST_LAUNCH(k_lr_walk, (unsigned)((S + kLrWalkThreads - 1) / kLrWalkThreads), kLrWalkThreads, 0, s)(
-        f.N, S0, S, f.nxt, f.w, b.sstart, b.ol, b.snext, b.w_next, l == 0 ? visited : nullptr, status);
+        f.N, S0, S, sh, f.nxt, f.w, b.sstart, b.ol, b.snext, b.w_next, l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_walk1" : "k_lr_walk");
     RST_CUDA(cudaGetLastError());
     frames[l] = f;
@@ -313,7 +323,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   for (int l = levels.count - 1; l >= 0; --l) {
     const Frame& fr = frames[l];
     LevelBufs& b = levels.b[l];
-    const int64_t S = (fr.N + kLrK - 1) / kLrK + nheads;
+    const int64_t S = ((fr.N + (1LL << sh) - 1) >> sh) + nheads;
 
     RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.spos, fr.pos,
                                                          l == 0 ? visited : nullptr, status);

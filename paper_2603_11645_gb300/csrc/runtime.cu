@@ -59,6 +59,11 @@ static int current_device() {
   return d < kMaxDevices ? d : 0;
 }
 
+Tuning& tuning() {
+  static Tuning t;
+  return t;
+}
+
 const Device& device_info() {
   int d = current_device();
   Device& info = g_dev[d];

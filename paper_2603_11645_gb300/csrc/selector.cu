@@ -449,10 +449,41 @@ rst_status rst_mlp_train(float* params, const float* X, const float* T, int batc
 rst_status rst_set_option(const char* key, long long value) {
   if (!key) return RST_ERR_INVALID_ARG;
   if (std::strcmp(key, "bfs_max_levels") == 0) {
+    if (value < 0) return RST_ERR_INVALID_ARG;
     set_bfs_max_levels(value);
     return RST_OK;
   }
+  Tuning& t = tuning();
+  if (std::strcmp(key, "lr_spacing") == 0) {
+    for (int sh = 4; sh <= 9; ++sh)
+      if (value == (1LL << sh)) {
+        t.lr_shift = sh;
+        return RST_OK;
+      }
+    return RST_ERR_INVALID_ARG;
+  }
+  if (std::strcmp(key, "round_blocks_per_sm") == 0) {
+    if (value < 1 || value > 16) return RST_ERR_INVALID_ARG;
+    t.round_bps = (int)value;
+    return RST_OK;
+  }
+  if (std::strcmp(key, "bfs_bottom_up_divisor") == 0) {
+    if (value < 1 || value > 1000000) return RST_ERR_INVALID_ARG;
+    t.bfs_bu_div = (int)value;
+    return RST_OK;
+  }
   return RST_ERR_INVALID_ARG;
+}
+
+rst_status rst_get_option(const char* key, long long* value) {
+  if (!key || !value) return RST_ERR_INVALID_ARG;
+  const Tuning& t = tuning();
+  if (std::strcmp(key, "bfs_max_levels") == 0) *value = get_bfs_max_levels();
+  else if (std::strcmp(key, "lr_spacing") == 0) *value = 1LL << t.lr_shift;
+  else if (std::strcmp(key, "round_blocks_per_sm") == 0) *value = t.round_bps;
+  else if (std::strcmp(key, "bfs_bottom_up_divisor") == 0) *value = t.bfs_bu_div;
+  else return RST_ERR_INVALID_ARG;
+  return RST_OK;
 }
 
 }  // extern "C"

@@ -24,6 +24,7 @@ struct BfsProbe {
 rst_status bfs_probe_in(Arena& ar, const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                         int32_t root, int32_t* parent_scratch, BfsProbe* probe, cudaStream_t s);
 void set_bfs_max_levels(long long v);
+long long get_bfs_max_levels();
 
 // BFS from several sources at once (the roots of a disjoint union), with
 // buffers taken from the caller's arena (bfs_workspace_bytes(n) of room).
@@ -36,6 +37,11 @@ rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int
                      int32_t root, int32_t* parent, cudaStream_t s);
 
 // Exact verdict of a parent array.
+// Depth of every vertex of a rooted forest (depth.cu); the workspace must
+// hold depth_workspace_bytes(n).
+size_t depth_workspace_bytes(int64_t n);
+rst_status tree_depth(const int32_t* parent, int64_t n, int32_t* depth_out, int64_t* max_out,
+                      cudaStream_t s);
 rst_status run_verify(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                       int32_t root, const int32_t* parent, int32_t* verdict_out, cudaStream_t s);
 

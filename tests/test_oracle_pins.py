@@ -459,3 +459,49 @@ def test_prrst_path_and_star():
     g = G(n, [(0, j) for j in range(1, n)], root=5)
     par, _ = oracle.prrst(n, g.offsets, g.cols, 5)
     assert par.tolist() == [5] + [0] * 4 + [5] + [0] * 3
+
+
+# ------------------------------------------------------------------ tree depth
+
+@pytest.mark.parametrize("n,r", [(1, 0), (10, 0), (10, 4), (10, 9)])
+def test_tree_depths_path_closed_form(n, r):
+    # path 0-1-...-(n-1) rooted at r: depth(i) = |i - r|
+    parent = [i + 1 if i < r else (i - 1 if i > r else i) for i in range(n)]
+    assert np.array_equal(oracle.tree_depths(n, parent), np.abs(np.arange(n) - r))
+
+
+def test_tree_depths_star_and_forest():
+    # star with centre 0 rooted at leaf 3: the leaf 0, the centre 1, the rest 2
+    parent = [3, 0, 0, 3, 0, 0]
+    assert list(oracle.tree_depths(6, parent)) == [1, 2, 2, 0, 2, 2]
+    # two trees and a singleton
+    assert list(oracle.tree_depths(6, [0, 0, 1, 3, 3, 5])) == [0, 1, 2, 0, 1, 0]
+
+
+@pytest.mark.parametrize("W,H", [(5, 4), (7, 1), (1, 6)])
+def test_tree_depths_of_the_grid_comb(W, H):
+    # identity-labelled grid rooted at 0: the Kruskal tree is the comb (row 0
+    # plus every vertical edge), so vertex (i, j) sits at depth i + j
+    g = graphs.grid(W, H, permute=False, root=0)
+    par = oracle.rst(g.n, g.offsets, g.cols, 0)
+    want = np.array([i + j for i in range(H) for j in range(W)])
+    assert np.array_equal(oracle.tree_depths(g.n, par), want)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bfs_tree_depth_is_the_bfs_level(seed):
+    # every BFS parent sits one level up, so depth in the BFS tree = level
+    g = graphs.erdos_renyi(400, 700, seed=seed)
+    lev, par = oracle.bfs(g.n, g.offsets, g.cols, g.root)
+    d = oracle.tree_depths(g.n, par)
+    reached = lev >= 0
+    assert np.array_equal(d[reached], lev[reached])
+
+
+def test_tree_depths_rejects_cycles_and_range():
+    with pytest.raises(ValueError):
+        oracle.tree_depths(3, [1, 2, 0])
+    with pytest.raises(ValueError):
+        oracle.tree_depths(4, [0, 2, 3, 1])  # 1 -> 2 -> 3 -> 1
+    with pytest.raises(ValueError):
+        oracle.tree_depths(3, [0, 5, 0])
