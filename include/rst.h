@@ -61,7 +61,8 @@ typedef enum {
     RST_AUTO = 0,      /* learned selector picks one of the three below        */
     RST_BFS = 1,       /* level-synchronous, direction-optimising BFS (III-A)  */
     RST_CC_EULER = 2,  /* hook/compress connectivity + Euler-tour rooting      */
-    RST_PR_RST = 3     /* path-reversal RST (III-C)                            */
+    RST_PR_RST = 3,    /* path-reversal RST (III-C)                            */
+    RST_CC_FAST = 4    /* sampled union-find connectivity + Euler rooting      */
 } rst_strategy;
 
 /* Verdict codes written by rst_verify (the smallest failing code wins). */
@@ -90,9 +91,17 @@ int rst_version(void);
  *               III-D), RST_BFS (Section III-A), RST_PR_RST (Section III-C) or
  *               RST_AUTO (rst_select's choice).
  *   parent_out: n int32 (device), receives P.
+ *               RST_CC_FAST: connectivity by sampled union-find hooking
+ *               (Section III-B leaves the hooking rule open; this one links
+ *               every vertex with its first two neighbours, then only the
+ *               vertices outside the largest component with the rest of
+ *               their rows, merging by compare-and-swap), then the same
+ *               Euler-tour rooting.
  * CC+Euler and BFS results are unique: CC+Euler roots the minimum spanning
  * forest under edge keys (min(u,v), max(u,v)); BFS takes for every vertex the
- * minimum-id neighbour on the previous level.  PR-RST returns a valid RST.
+ * minimum-id neighbour on the previous level.  PR-RST and RST_CC_FAST return
+ * a valid RST (components and tree roots fixed, the tree edges chosen by
+ * races: not reproducible run to run).
  */
 rst_status rst_build(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols,
                      int64_t n, int64_t m, int32_t root, rst_strategy strategy,

@@ -49,6 +49,21 @@ rst_status build_cc_euler(const OffT* off, const int32_t* cols, int64_t n, int64
   return st;
 }
 
+template <class OffT>
+rst_status build_cc_fast(const OffT* off, const int32_t* cols, int64_t n, int64_t m, int32_t root,
+                         int32_t* parent, cudaStream_t s) {
+  const size_t ws = ccfast_workspace_bytes<OffT>(n, m) + euler_cc_workspace_bytes(n, m, n, n / 2 + 1);
+  Arena ar;
+  prof_mark(s, "start");
+  RST_TRY(begin(ws, s, &ar));
+  CcOut cc;
+  RST_TRY(ccfast_run<OffT>(ar, off, cols, n, m, root, nullptr, &cc, s));
+  RST_TRY(euler_root_cc<OffT>(ar, off, n, m, root, &cc, parent, nullptr, s));
+  rst_status st = read_device_error(s);
+  prof_mark(s, "end");
+  return st;
+}
+
 __global__ void k_pairs_to_uv(int64_t T, const uint4* __restrict__ pairs, int32_t* __restrict__ uv) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -115,6 +130,10 @@ rst_status rst_build(const void* csr_offsets, int offsets_bits, const int32_t* c
       return run_bfs(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, nullptr, s);
     case RST_PR_RST:
       return run_prrst(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, s);
+    case RST_CC_FAST:
+      if (offsets_bits == 32)
+        return build_cc_fast<int32_t>((const int32_t*)csr_offsets, csr_cols, n, m, root, parent_out, s);
+      return build_cc_fast<int64_t>((const int64_t*)csr_offsets, csr_cols, n, m, root, parent_out, s);
     default:
       return RST_ERR_INVALID_ARG;
   }

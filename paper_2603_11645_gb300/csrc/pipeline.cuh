@@ -45,6 +45,13 @@ template <class OffT>
 size_t cc_workspace_bytes(int64_t n, int64_t A);
 // Release cached round graphs (rst_shutdown).
 void destroy_round_graphs();
+// The same outputs from sampled union-find hooking (ccfast.cu): a valid
+// spanning forest with the same components, chosen by races (not unique).
+template <class OffT>
+rst_status ccfast_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A,
+                      int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s);
+template <class OffT>
+size_t ccfast_workspace_bytes(int64_t n, int64_t A);
 
 // ----------------------------------------------------------------- Euler
 struct EulerIn {
