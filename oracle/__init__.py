@@ -16,6 +16,9 @@ Parity status per function (what pins each one, see tests/test_oracle_pins.py):
 * ``verify``       pinned: Kirchhoff spanning-tree counts (n <= 6), mutations.
 * ``prrst``        parity unpinned for its edge set (the paper fixes no unique
                    tree); its output is pinned only through ``verify``.
+* ``bcc``          pinned: brute-force blocks from every simple cycle and cut
+                   vertices by deletion (n <= 8), closed forms (cycle, path,
+                   star, bowtie, grid), networkx where installed.
 * ``tree_depths``  pinned: closed forms (path, star, grid comb), BFS-tree
                    depth equals the BFS level, cycle and range rejection.
 """
@@ -47,6 +50,7 @@ def _L():
         lib.or_verify.argtypes = [I64, P, P, I32, P, I]
         if hasattr(lib, "or_prrst"):
             lib.or_prrst.argtypes = [I64, P, P, I32, P, P]
+        lib.or_bcc.argtypes = [I64, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -169,3 +173,19 @@ def tree_depths(n, parent):
             d += 1
             depth[y] = d
     return depth
+
+
+def bcc(n, offsets, cols):
+    """Blocks (biconnected components) and cut vertices by Hopcroft-Tarjan
+    depth-first search: (label uint32[A], cut uint8[n], number of blocks).
+    label[a] is the smallest CSR position among the arcs of arc a's block
+    (0xFFFFFFFF for a self-loop)."""
+    off, col = _csr(offsets, cols)
+    A = int(off[n]) if n > 0 else 0
+    label = np.empty(max(A, 1), dtype=np.uint32)
+    cut = np.zeros(max(n, 1), dtype=np.uint8)
+    nb = ctypes.c_int64(0)
+    rc = _L().or_bcc(n, _p(off), _p(col), _p(label), _p(cut), ctypes.byref(nb))
+    if rc != 0:
+        raise ValueError(f"or_bcc failed: {rc}")
+    return label[:A].copy(), cut[:n].copy(), int(nb.value)

@@ -28,6 +28,10 @@
  *   or_verify       exact RST verdict with a reason code.
  *   or_prrst        the PR-RST rounds of Section III-C simulated one step at a
  *                   time (alternating min/max hooking, path reversal).
+ *   or_bcc          biconnected components (blocks) and cut vertices by the
+ *                   textbook depth-first search with an edge stack (Hopcroft
+ *                   and Tarjan): the consumer of rooted trees that motivates
+ *                   the paper (Section I).  Independent of any spanning tree.
  *
  * All CSR inputs use int64 offsets (the Python wrapper widens int32 ones),
  * int32 column ids and rows sorted ascending.
@@ -478,4 +482,123 @@ int or_prrst(int64_t n, const int64_t *off, const int32_t *col, int32_t root,
     *rounds_out = t + 1;
     free(Q); free(rep); free(best); free(stk);
     return 0;
+}
+
+/* ------------------------------------------------------------ biconnected components */
+
+/* First position of w in the sorted row v (every copy of a parallel edge is
+ * named by its first copy), or -1. */
+static int64_t first_pos(const int64_t *off, const int32_t *col, int32_t v, int32_t w) {
+    int64_t lo = off[v], hi = off[v + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (col[mid] < w) lo = mid + 1; else hi = mid;
+    }
+    return (lo < off[v + 1] && col[lo] == w) ? lo : -1;
+}
+
+/*
+ * Blocks of an undirected graph (maximal edge sets in which every two edges
+ * lie on a common simple cycle; an edge on no cycle is a block by itself;
+ * self-loops belong to no block).
+ *   label[a]  (length A) for arc a = x->y: the smallest CSR position among
+ *             the arcs of its block (the arc min->max of the block's
+ *             lexicographically smallest edge); 0xFFFFFFFF for self-loops.
+ *   cut[v]    1 iff v has edges in two or more blocks (a cut vertex).
+ *   *nblocks  number of blocks.
+ * Depth-first search from every unvisited vertex with discovery numbers and
+ * low values; tree edges and back edges are pushed on an edge stack when
+ * first met, and a block is popped when a child's low value does not reach
+ * above its parent.  Parallel edges: only one copy of the edge to the parent
+ * is skipped, the other copies are back edges.  Returns 0, or -1 on
+ * allocation failure or asymmetric input.
+ */
+int or_bcc(int64_t n, const int64_t *off, const int32_t *col, uint32_t *label, uint8_t *cut,
+           int64_t *nblocks) {
+    const int64_t A = off[n];
+    const size_t nn = (size_t)(n > 0 ? n : 1), aa = (size_t)(A > 0 ? A : 1);
+    int64_t *disc = malloc(nn * sizeof(int64_t));
+    int64_t *low = malloc(nn * sizeof(int64_t));
+    int64_t *next = malloc(nn * sizeof(int64_t));     /* next arc of v to scan */
+    int32_t *par = malloc(nn * sizeof(int32_t));      /* DFS parent (-1 at a start) */
+    int64_t *in_arc = malloc(nn * sizeof(int64_t));   /* tree arc par->v */
+    uint8_t *skipped = calloc(nn, 1);                 /* one copy of v->par skipped */
+    int32_t *vst = malloc(nn * sizeof(int32_t));      /* vertex stack */
+    int64_t *est = malloc(aa * sizeof(int64_t));      /* edge stack: arc positions */
+    int32_t *esrc = malloc(aa * sizeof(int32_t));     /* and their sources */
+    int64_t *blk = malloc(aa * sizeof(int64_t));      /* block of the edge named by first-copy min->max arc */
+    int64_t *bmin = malloc(aa * sizeof(int64_t));     /* smallest position per block */
+    int rc = 0;
+    if (!disc || !low || !next || !par || !in_arc || !skipped || !vst || !est || !esrc || !blk || !bmin)
+        rc = -1;
+    for (int64_t v = 0; v < n && rc == 0; ++v) { disc[v] = -1; cut[v] = 0; }
+    for (int64_t a = 0; a < A && rc == 0; ++a) blk[a] = -1;
+    int64_t timer = 0, ne = 0, nb = 0;
+    for (int64_t s = 0; s < n && rc == 0; ++s) {
+        if (disc[s] >= 0) continue;
+        int64_t top = 0;
+        vst[top++] = (int32_t)s;
+        disc[s] = low[s] = timer++;
+        next[s] = off[s];
+        par[s] = -1;
+        in_arc[s] = -1;
+        while (top > 0 && rc == 0) {
+            const int32_t v = vst[top - 1];
+            if (next[v] < off[v + 1]) {
+                const int64_t a = next[v]++;
+                const int32_t w = col[a];
+                if (w == v) continue;                                   /* self-loop */
+                if (w == par[v] && !skipped[v]) { skipped[v] = 1; continue; }  /* the entering edge */
+                if (disc[w] < 0) {                                      /* tree edge */
+                    est[ne] = a; esrc[ne] = v; ++ne;
+                    disc[w] = low[w] = timer++;
+                    next[w] = off[w];
+                    par[w] = v;
+                    in_arc[w] = a;
+                    vst[top++] = w;
+                } else if (disc[w] < disc[v]) {                         /* back edge to an ancestor */
+                    est[ne] = a; esrc[ne] = v; ++ne;
+                    if (disc[w] < low[v]) low[v] = disc[w];
+                }                                                       /* else: met from w's side */
+            } else {
+                --top;
+                const int32_t u = par[v];
+                if (u < 0) continue;
+                if (low[v] < low[u]) low[u] = low[v];
+                if (low[v] >= disc[u]) {                                /* u separates v's subtree */
+                    const int64_t id = nb++;
+                    int64_t mn = INT64_MAX;
+                    for (;;) {
+                        if (ne <= 0) { rc = -1; break; }
+                        --ne;
+                        const int64_t e = est[ne];
+                        const int32_t x = esrc[ne], y = col[e];
+                        const int64_t p0 = first_pos(off, col, x < y ? x : y, x < y ? y : x);
+                        if (p0 < 0) { rc = -1; break; }
+                        blk[p0] = id;
+                        if (p0 < mn) mn = p0;
+                        if (e == in_arc[v]) break;
+                    }
+                    bmin[id] = mn;
+                }
+            }
+        }
+    }
+    for (int64_t v = 0; v < n && rc == 0; ++v) {
+        int64_t first = -1;
+        for (int64_t a = off[v]; a < off[v + 1]; ++a) {
+            const int32_t w = col[a];
+            if (w == (int32_t)v) { label[a] = 0xFFFFFFFFu; continue; }
+            const int64_t p0 = first_pos(off, col, (int32_t)v < w ? (int32_t)v : w, (int32_t)v < w ? w : (int32_t)v);
+            if (p0 < 0 || blk[p0] < 0) { rc = -1; break; }
+            const int64_t b = bmin[blk[p0]];
+            label[a] = (uint32_t)b;
+            if (first < 0) first = b;
+            else if (b != first) cut[v] = 1;
+        }
+    }
+    *nblocks = nb;
+    free(disc); free(low); free(next); free(par); free(in_arc); free(skipped); free(vst);
+    free(est); free(esrc); free(blk); free(bmin);
+    return rc;
 }
