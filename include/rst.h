@@ -180,6 +180,27 @@ rst_status rst_verify(const void *csr_offsets, int offsets_bits, const int32_t *
                       int64_t n, int64_t m, int32_t root, const int32_t *parent,
                       int32_t *verdict_out, rst_stream_t stream);
 
+/* rst_bcc -- blocks (biconnected components) and cut vertices, computed from
+ * the CC+Euler rooted spanning forest the way Tarjan and Vishkin do: subtree
+ * intervals from the Euler-tour ranks, low/high values by range queries, and
+ * connectivity of the auxiliary graph on tree edges (the downstream use of
+ * rooted spanning trees named in Section I).
+ *   csr_offsets, offsets_bits, csr_cols, n, m: the graph (see conventions).
+ *   block_out       device uint32[m]: for arc a = x->y, the smallest CSR
+ *                   position among the arcs of the block holding edge {x, y}
+ *                   (so two arcs share a block iff their values are equal;
+ *                   the value does not depend on any spanning tree);
+ *                   0xFFFFFFFF for a self-loop, which lies in no block.
+ *   cut_out         device uint8[n] or NULL: 1 iff the vertex has edges in two
+ *                   or more blocks.
+ *   num_blocks_out  host int64 or NULL: number of blocks.
+ * A block is a maximal set of edges any two of which lie on a common simple
+ * cycle; an edge on no cycle (a bridge) is a block by itself; parallel edges
+ * form a cycle.  Workspace: about 130 bytes per vertex beyond rst_build's
+ * (the range tables over the tour take 80). */
+rst_status rst_bcc(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols, int64_t n, int64_t m,
+                   uint32_t *block_out, uint8_t *cut_out, int64_t *num_blocks_out, rst_stream_t stream);
+
 /* rst_tree_depth -- depth of every vertex of a rooted forest, and its height
  * (Section IV-B, Fig. 2: the trees of connectivity-based strategies are
  * deeper than BFS trees; this measures that trade-off on any parent array).

@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["build", "build_batch", "cc", "euler_root", "verify", "tree_depth", "set_option", "get_option", "lib",
+__all__ = ["build", "build_batch", "cc", "euler_root", "verify", "tree_depth", "bcc", "set_option", "get_option", "lib",
            "RstError", "STRATEGIES"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,12 +44,13 @@ def lib():
         L.rst_verify.argtypes = [P, I, P, I64, I64, I32, P, P, P]
         L.rst_build_batch.argtypes = [P, I, P, P, P, I32, P, I, P, P]
         L.rst_tree_depth.argtypes = [P, I64, P, P, P]
+        L.rst_bcc.argtypes = [P, I, P, I64, I64, P, P, P, P]
         L.rst_set_option.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
         L.rst_get_option.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong)]
         L.rst_status_string.argtypes = [I]
         L.rst_status_string.restype = ctypes.c_char_p
         L.rst_version.restype = I
-        for fn in ("rst_build", "rst_cc", "rst_euler_root", "rst_verify", "rst_shutdown", "rst_set_option", "rst_tree_depth",
+        for fn in ("rst_build", "rst_cc", "rst_euler_root", "rst_verify", "rst_shutdown", "rst_set_option", "rst_tree_depth", "rst_bcc",
                    "rst_get_option"):
             getattr(L, fn).restype = I
         for fn in ("rst_build_batch", "rst_select", "rst_build_batch_graph"):
@@ -180,3 +181,20 @@ def tree_depth(parent, want_depths: bool = True, stream=None):
                                 ctypes.byref(mx), _stream(stream))
     _check("rst_tree_depth", code)
     return depth, int(mx.value)
+
+
+def bcc(offsets, cols, want_cut: bool = True, stream=None):
+    """Blocks and cut vertices: (block label per arc as an int32 tensor holding
+    the uint32 values, -1 for self-loops; cut flags uint8 tensor or None;
+    number of blocks)."""
+    import torch
+    bits, n, m = _graph_args(offsets, cols)
+    label = torch.empty(m, dtype=torch.int32, device=cols.device)
+    cut = torch.empty(n, dtype=torch.uint8, device=cols.device) if want_cut else None
+    nb = ctypes.c_int64(0)
+    code = lib().rst_bcc(ctypes.c_void_p(offsets.data_ptr()), bits, ctypes.c_void_p(cols.data_ptr()), n, m,
+                         ctypes.c_void_p(label.data_ptr()) if m else None,
+                         ctypes.c_void_p(cut.data_ptr()) if cut is not None else None,
+                         ctypes.byref(nb), _stream(stream))
+    _check("rst_bcc", code)
+    return label, cut, int(nb.value)

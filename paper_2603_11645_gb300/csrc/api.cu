@@ -187,6 +187,29 @@ rst_status rst_verify(const void* csr_offsets, int offsets_bits, const int32_t* 
   return run_verify(csr_offsets, offsets_bits, csr_cols, n, m, root, parent, verdict_out, s);
 }
 
+rst_status rst_bcc(const void* csr_offsets, int offsets_bits, const int32_t* csr_cols, int64_t n, int64_t m,
+                   uint32_t* block_out, uint8_t* cut_out, int64_t* num_blocks_out, rst_stream_t stream) {
+  RST_TRY(check_graph(csr_offsets, offsets_bits, csr_cols, n, m));
+  if (m > 0 && !block_out) return RST_ERR_INVALID_ARG;
+  if (n == 0) {
+    if (num_blocks_out) *num_blocks_out = 0;
+    return RST_OK;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CallGuard g;
+  Arena ar;
+  if (offsets_bits == 32) {
+    RST_TRY(begin(bcc_workspace_bytes<int32_t>(n, m), s, &ar));
+    RST_TRY(bcc_run<int32_t>(ar, (const int32_t*)csr_offsets, csr_cols, n, m, block_out, cut_out,
+                             num_blocks_out, s));
+  } else {
+    RST_TRY(begin(bcc_workspace_bytes<int64_t>(n, m), s, &ar));
+    RST_TRY(bcc_run<int64_t>(ar, (const int64_t*)csr_offsets, csr_cols, n, m, block_out, cut_out,
+                             num_blocks_out, s));
+  }
+  return read_device_error(s);
+}
+
 rst_status rst_tree_depth(const int32_t* parent, int64_t n, int32_t* depth_out, int64_t* max_out,
                           rst_stream_t stream) {
   if (n < 0 || n >= ((int64_t)1 << 30)) return RST_ERR_INVALID_ARG;

@@ -23,6 +23,7 @@
 #include "csr_walk.cuh"
 #include "pipeline.cuh"
 #include "strategies.cuh"
+#include "unionfind.cuh"
 
 namespace rst {
 
@@ -30,32 +31,6 @@ constexpr int kSampleRounds = 2;
 constexpr int kGiantSample = 1024;
 
 enum { FC_TREE = 0, FC_ROOTS = 1, FC_GIANT_ROOT = 2, FC_ROOT_LABEL = 3 };
-
-// Root of x; halves the path on the way (each write replaces a pointer by an
-// ancestor, so concurrent finds and hooks stay correct).
-__device__ __forceinline__ int32_t uf_find(int32_t* uf, int32_t x, int64_t n, uint32_t* status) {
-  for (int64_t it = 0; it <= n; ++it) {
-    const int32_t p = __ldcg(&uf[x]);
-    if (p == x) return x;
-    const int32_t g = __ldcg(&uf[p]);
-    if (g != p) uf[x] = g;
-    x = g;
-  }
-  raise_error(status, DERR_WALK_LIMIT);
-  return x;
-}
-
-// Merges the trees of u and v; true iff this call's CAS did the merge.
-__device__ __forceinline__ bool uf_link(int32_t* uf, int32_t u, int32_t v, int64_t n, uint32_t* status) {
-  for (int64_t it = 0; it <= n; ++it) {
-    const int32_t ru = uf_find(uf, u, n, status), rv = uf_find(uf, v, n, status);
-    if (ru == rv) return false;
-    const int32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
-    if (atomicCAS(&uf[hi], hi, lo) == hi) return true;
-  }
-  raise_error(status, DERR_ROUND_LIMIT);
-  return false;
-}
 
 __global__ void k_fast_init(int64_t n, int32_t* __restrict__ uf) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -95,10 +70,10 @@ __global__ void k_fast_sample(const OffT* __restrict__ off, const int32_t* __res
   }
 }
 
-__global__ void k_fast_compress(int64_t n, int32_t* uf, uint32_t* status) {
+__global__ void k_uf_compress(int64_t n, int32_t* uf, uint32_t* status) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
-    uf[v] = uf_find(uf, (int32_t)v, n, status);
+    uf[v] = uf_root(uf, (int32_t)v, n, status);
 }
 
 // The giant component: the most frequent root among kGiantSample vertices
@@ -211,12 +186,12 @@ rst_status ccfast_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n,
   for (int r = 0; r < kSampleRounds; ++r)
     RST_LAUNCH(k_fast_sample<OffT>, gN, kBlock, 0, s)(off, col, n, r, uf, tl, cnt, n, status);
   prof_mark(s, "k_fast_sample");
-  RST_LAUNCH(k_fast_compress, gN, kBlock, 0, s)(n, uf, status);
+  RST_LAUNCH(k_uf_compress, gN, kBlock, 0, s)(n, uf, status);
   RST_LAUNCH(k_fast_giant, 1, kBlock, 0, s)(n, uf, cnt);
   prof_mark(s, "k_fast_compress");
   RST_LAUNCH(k_fast_rest<OffT>, gN, kBlock, 0, s)(off, col, n, uf, tl, cnt, n, status);
   prof_mark(s, "k_fast_rest");
-  RST_LAUNCH(k_fast_compress, gN, kBlock, 0, s)(n, uf, status);
+  RST_LAUNCH(k_uf_compress, gN, kBlock, 0, s)(n, uf, status);
   RST_LAUNCH(k_fast_roots<OffT>, gN, kBlock, 0, s)(off, n, uf, root, roots, cnt);
   RST_LAUNCH(k_fast_pairs<OffT>, gN, kBlock, 0, s)(off, col, tl, cnt, pairs, bits, status);
   prof_mark(s, "k_fast_pairs");

@@ -143,7 +143,7 @@ size_t euler_cc_workspace_bytes(int64_t n, int64_t A, int64_t T, int64_t nroots)
 
 template <class OffT>
 rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32_t root, CcOut* cc,
-                         int32_t* parent_out, uint32_t* rank_out, cudaStream_t s) {
+                         int32_t* parent_out, uint32_t* rank_out, cudaStream_t s, const int32_t** succ_view) {
   const int64_t W = A / 32 + 1;
   uint32_t* wpre = ar.take<uint32_t>(W + 1);
   unsigned long long* tmp = ar.take<unsigned long long>(scan_tmp_words(W));
@@ -195,6 +195,7 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   RST_LAUNCH(k_pairs_succ, gT, kBlock, 0, s)(T, cc->pairs, cc->bits, wpre, toff, is_root, succ);
   prof_mark(s, "k_pairs_succ");
   RST_CUDA(cudaGetLastError());
+  if (succ_view) *succ_view = succ;  // stays valid while the arena is not reset
   RST_TRY(list_rank(ar, N, succ, nullptr, heads, cc->nroots, R, s));
   RST_LAUNCH(k_parent_from_rank, gT, kBlock, 0, s)(T, cc->pairs, R, parent_out);
   prof_mark(s, "k_parent_from_rank");
@@ -203,9 +204,9 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
 }
 
 template rst_status euler_root_cc<int32_t>(Arena&, const int32_t*, int64_t, int64_t, int32_t, CcOut*,
-                                           int32_t*, uint32_t*, cudaStream_t);
+                                           int32_t*, uint32_t*, cudaStream_t, const int32_t**);
 template rst_status euler_root_cc<int64_t>(Arena&, const int64_t*, int64_t, int64_t, int32_t, CcOut*,
-                                           int32_t*, uint32_t*, cudaStream_t);
+                                           int32_t*, uint32_t*, cudaStream_t, const int32_t**);
 
 // ----------------------------------------------------------------- edge-list front end
 

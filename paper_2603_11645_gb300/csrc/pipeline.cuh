@@ -70,7 +70,8 @@ struct EulerIn {
 // tours and sets every other parent from the ranks.
 template <class OffT>
 rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32_t root,
-                         CcOut* cc, int32_t* parent_out, uint32_t* rank_out, cudaStream_t s);
+                         CcOut* cc, int32_t* parent_out, uint32_t* rank_out, cudaStream_t s,
+                         const int32_t** succ_view = nullptr);
 size_t euler_cc_workspace_bytes(int64_t n, int64_t A, int64_t T, int64_t nroots);
 
 // Edge-list front end (rst_euler_root): radix-sorts the 2T arcs by (src, dst).

@@ -37,6 +37,12 @@ rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int
                      int32_t root, int32_t* parent, cudaStream_t s);
 
 // Exact verdict of a parent array.
+// Blocks and cut vertices (bcc.cu).
+template <class OffT>
+size_t bcc_workspace_bytes(int64_t n, int64_t A);
+template <class OffT>
+rst_status bcc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A, uint32_t* label,
+                   uint8_t* cut, int64_t* nblocks, cudaStream_t s);
 // Depth of every vertex of a rooted forest (depth.cu); the workspace must
 // hold depth_workspace_bytes(n).
 size_t depth_workspace_bytes(int64_t n);
