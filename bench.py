@@ -330,6 +330,12 @@ def run_ours(args, rank, world, local_rank):
     # sampled union-find connectivity + the same Euler rooting (non-deterministic tree)
     fast_ms = _time(lambda: step("cc_fast"), max(3, args.bfs_steps), torch, dev, stream, flush)
 
+    # blocks and cut vertices on top of the Euler tour (Tarjan-Vishkin)
+    bcc_ms = _time(lambda: rst.bcc(off, col), max(3, args.bfs_steps), torch, dev, stream, flush)
+    _, bcc_cut, bcc_blocks = rst.bcc(off, col)
+    bcc_rep = {"value": g.m / (bcc_ms / 1e3), "unit": "edges/s", "ms_per_step": bcc_ms,
+               "blocks": bcc_blocks, "cut_vertices": int(bcc_cut.sum().item())}
+
     # tree shape (Fig. 2): heights of the trees each strategy returns
     heights = {}
     for strat in ("cc_euler", "bfs", "pr_rst", "cc_fast"):
@@ -371,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
             "cc_fast": {"value": g.m / (fast_ms / 1e3), "unit": "edges/s", "ms_per_step": fast_ms,
                         "note": "sampled union-find CC + the same Euler rooting; valid RST, tree not unique"},
             "tree_height": heights,
+            "bcc": bcc_rep,
             "batch": batch,
             "families": families,
             "selector": selector,
@@ -458,6 +465,10 @@ def run_families(args, dev, stream, rst, graphs, torch):
         ms = _time(lambda: rst.build(off, col, g.root, strat, out=par), 3, torch, dev, stream)
         out[strat] = {"ms": ms, "value": g.m / (ms / 1e3), "unit": "edges/s"}
     out["cc_euler_speedup_over_bfs"] = out["bfs"]["ms"] / out["cc_euler"]["ms"]
+    ms = _time(lambda: rst.bcc(off, col), 3, torch, dev, stream)
+    _, cut, nb = rst.bcc(off, col)
+    out["bcc"] = {"ms": ms, "value": g.m / (ms / 1e3), "unit": "edges/s", "blocks": nb,
+                  "cut_vertices": int(cut.sum().item())}
     return {"rmat22": out}
 
 

@@ -9,10 +9,12 @@
 //    up arc, and y lies in x's subtree iff key(x) <= key(y) <= end(x).  A tree
 //    root gets key = base_j - 1 and end = base_j + len_j - 1.
 //  2 local values: lo(x) = min(key(x), key(y) over non-tree edges {x, y}),
-//    hi(x) the max; placed at position key(x) of two arrays (other positions
-//    neutral), so low(x) / high(x) over x's subtree are range-min/max queries
-//    over [key(x), end(x)]: a sparse table inside every 32-position block
-//    (built with warp shuffles) plus a sparse table over block minima.
+//    hi(x) the max.  Numbering the non-root vertices by the order of their
+//    down arcs (the preorder; a popcount rank over a bitmap of down-arc
+//    positions) makes x's subtree the index range [idx(x), idx(x) + nd(x) - 1],
+//    nd(x) = (end(x) - key(x) + 1) / 2, so low(x) / high(x) are range-min/max
+//    queries over {lo, hi} pairs stored at idx: a sparse table inside every
+//    32-index block (built with warp shuffles) plus one over block extremes.
 //  3 the auxiliary graph on tree edges (tree edge p(w)-w named by w):
 //      a non-tree edge {x, y} between unrelated vertices joins x and y;
 //      a tree edge u-w with u not a root joins w and u when
@@ -34,36 +36,38 @@ namespace rst {
 constexpr uint32_t kNoBlock = 0xFFFFFFFFu;
 constexpr int kStLevels = 5;  // in-block sparse table: windows of 1..16 positions
 
+// {min of the lo values, max of the hi values} over an index range
 struct RmqView {
-  const int32_t* st[kStLevels];  // st[k][i]: extreme of positions i .. i+2^k-1 (clipped at the block end)
-  const int32_t* bst;            // level k of the block table at bst + k * nb
+  const int2* st[kStLevels];  // st[k][i]: indices i .. i+2^k-1 (clipped at the block end)
+  const int2* bst;            // level k of the block table at bst + k * nb
   int64_t nb;
 };
 
-template <bool kMin>
-__device__ __forceinline__ int32_t pick(int32_t a, int32_t b) {
-  return kMin ? (a < b ? a : b) : (a > b ? a : b);
+__device__ __forceinline__ int2 ext(int2 a, int2 b) {
+  return make_int2(a.x < b.x ? a.x : b.x, a.y > b.y ? a.y : b.y);
 }
 
-// Extreme over positions [l, r] of one 32-position block.
-template <bool kMin>
-__device__ __forceinline__ int32_t rmq_block(const RmqView& v, int64_t l, int64_t r) {
+// Extremes over indices [l, r] of one 32-index block.
+__device__ __forceinline__ int2 rmq_block(const RmqView& v, int64_t l, int64_t r) {
   const int len = (int)(r - l + 1);
   const int k = 31 - __clz(len);
   if (k >= kStLevels)  // the whole block: two windows of 16
-    return pick<kMin>(v.st[kStLevels - 1][l], v.st[kStLevels - 1][l + 16]);
-  return pick<kMin>(v.st[k][l], v.st[k][r - (1 << k) + 1]);
+    return ext(v.st[kStLevels - 1][l], v.st[kStLevels - 1][l + 16]);
+  const int2* t = v.st[0];
+#pragma unroll
+  for (int j = 1; j < kStLevels; ++j)
+    if (k == j) t = v.st[j];  // a select, not a local-memory index
+  return ext(t[l], t[r - (1 << k) + 1]);
 }
 
-template <bool kMin>
-__device__ __forceinline__ int32_t rmq(const RmqView& v, int64_t l, int64_t r) {
+__device__ __forceinline__ int2 rmq(const RmqView& v, int64_t l, int64_t r) {
   const int64_t bl = l >> 5, br = r >> 5;
-  if (bl == br) return rmq_block<kMin>(v, l, r);
-  int32_t x = pick<kMin>(rmq_block<kMin>(v, l, (bl << 5) + 31), rmq_block<kMin>(v, br << 5, r));
+  if (bl == br) return rmq_block(v, l, r);
+  int2 x = ext(rmq_block(v, l, (bl << 5) + 31), rmq_block(v, br << 5, r));
   if (br - bl >= 2) {
     const int64_t b1 = bl + 1, b2 = br - 1;
     const int k = 63 - __clzll(b2 - b1 + 1);
-    x = pick<kMin>(x, pick<kMin>(v.bst[k * v.nb + b1], v.bst[k * v.nb + b2 - (1LL << k) + 1]));
+    x = ext(x, ext(v.bst[k * v.nb + b1], v.bst[k * v.nb + b2 - (1LL << k) + 1]));
   }
   return x;
 }
@@ -202,78 +206,89 @@ __global__ void k_fill_i32_pair(int64_t P, int32_t* __restrict__ a, int32_t va, 
   }
 }
 
-// Local values to the position of each non-root vertex's down arc.
-__global__ void k_bcc_place(int64_t n, const int32_t* __restrict__ parent, const int32_t* __restrict__ key,
-                            const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                            int32_t* __restrict__ mlo, int32_t* __restrict__ mhi) {
+// Bitmap of down-arc positions (the keys of non-root vertices).
+__global__ void k_bcc_mark(int64_t n, const int32_t* __restrict__ parent, const int32_t* __restrict__ key,
+                           uint32_t* __restrict__ dbits) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     if (parent[v] == (int32_t)v) continue;  // roots and isolated vertices
-    mlo[key[v]] = lo[v];
-    mhi[key[v]] = hi[v];
+    const uint32_t k = (uint32_t)key[v];
+    atomicOr(&dbits[k >> 5], 1u << (k & 31));
+  }
+}
+
+// Preorder index of every non-root vertex and its {lo, hi} at that index.
+__global__ void k_bcc_place(int64_t n, const int32_t* __restrict__ parent, const int32_t* __restrict__ key,
+                            const uint32_t* __restrict__ dbits, const uint32_t* __restrict__ dpre,
+                            const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                            int32_t* __restrict__ idx, int2* __restrict__ m) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (parent[v] == (int32_t)v) continue;
+    const uint32_t i = bit_rank(dbits, dpre, (uint64_t)key[v]);
+    idx[v] = (int32_t)i;
+    m[i] = make_int2(lo[v], hi[v]);
   }
 }
 
 struct StPtrs {
-  int32_t* lo[kStLevels];
-  int32_t* hi[kStLevels];
+  int2* st[kStLevels];
 };
 
 // In-block sparse tables (levels 1..4) and the block extremes, one warp per
-// 32-position block.
-__global__ void k_bcc_st(int64_t P, StPtrs sp, int32_t* __restrict__ bmlo, int32_t* __restrict__ bmhi) {
+// 32-index block.
+__global__ void k_bcc_st(int64_t P, StPtrs sp, int2* __restrict__ bm) {
   const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < P; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    int32_t a = i < P ? sp.lo[0][i] : INT_MAX;
-    int32_t b = i < P ? sp.hi[0][i] : INT_MIN;
+    int2 a = i < P ? sp.st[0][i] : make_int2(INT_MAX, INT_MIN);
 #pragma unroll
     for (int k = 1; k <= kStLevels; ++k) {
       const int d = 1 << (k - 1);
-      const int32_t a2 = __shfl_down_sync(0xffffffffu, a, d);
-      const int32_t b2 = __shfl_down_sync(0xffffffffu, b, d);
-      if (lane + d < 32) {
-        a = a2 < a ? a2 : a;
-        b = b2 > b ? b2 : b;
-      }
-      if (k < kStLevels && i < P) {
-        sp.lo[k][i] = a;
-        sp.hi[k][i] = b;
-      }
+      const int2 o = make_int2(__shfl_down_sync(0xffffffffu, a.x, d), __shfl_down_sync(0xffffffffu, a.y, d));
+      if (lane + d < 32) a = ext(a, o);
+      if (k < kStLevels && i < P) sp.st[k][i] = a;
     }
-    if (lane == 0 && i < P) {
-      bmlo[i >> 5] = a;
-      bmhi[i >> 5] = b;
-    }
+    if (lane == 0 && i < P) bm[i >> 5] = a;
   }
 }
 
 // Level k of the block table from level k-1 (windows of 2^k blocks, clipped).
-__global__ void k_bcc_bst(int64_t nb, int k, int32_t* __restrict__ blo, int32_t* __restrict__ bhi) {
+__global__ void k_bcc_bst(int64_t nb, int k, int2* __restrict__ b) {
   const int64_t h = 1LL << (k - 1);
-  const int32_t* plo = blo + (int64_t)(k - 1) * nb;
-  const int32_t* phi = bhi + (int64_t)(k - 1) * nb;
+  const int2* prev = b + (int64_t)(k - 1) * nb;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nb;
        j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j2 = j + h < nb ? j + h : nb - 1;
-    blo[(int64_t)k * nb + j] = plo[j] < plo[j2] ? plo[j] : plo[j2];
-    bhi[(int64_t)k * nb + j] = phi[j] > phi[j2] ? phi[j] : phi[j2];
+    b[(int64_t)k * nb + j] = ext(prev[j], prev[j2]);
   }
+}
+
+__global__ void k_fill_int2(int64_t P, int2* __restrict__ a, int2 v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
 }
 
 // Tree edge u-w (u = parent of w, u not a root) joins w and u when w's
 // subtree reaches outside u's subtree.
 __global__ void k_bcc_rule2(int64_t n, const int32_t* __restrict__ parent, const int32_t* __restrict__ key,
-                            const int32_t* __restrict__ end, RmqView vlo, RmqView vhi, int32_t* uf,
-                            uint32_t* status) {
+                            const int32_t* __restrict__ end, const int32_t* __restrict__ idx,
+                            const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, RmqView v,
+                            int32_t* uf, uint32_t* status) {
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n;
        w += (int64_t)gridDim.x * blockDim.x) {
     const int32_t u = parent[w];
     if (u == (int32_t)w || parent[u] == u) continue;
-    const int64_t l = key[w], r = end[w];
-    const int32_t low = rmq<true>(vlo, l, r);
-    const int32_t high = rmq<false>(vhi, l, r);
-    if (low < key[u] || high > end[u]) uf_link(uf, (int32_t)w, u, n, status);
+    const int32_t kw = key[w], ew = end[w];
+    int2 lh;
+    if (ew == kw + 1) {
+      lh = make_int2(lo[w], hi[w]);  // a leaf: its subtree is itself
+    } else {
+      const int64_t l = idx[w], nd = ((int64_t)ew - kw + 1) / 2;
+      lh = rmq(v, l, l + nd - 1);
+    }
+    if (lh.x < key[u] || lh.y > end[u]) uf_link(uf, (int32_t)w, u, n, status);
   }
 }
 
@@ -397,7 +412,7 @@ __global__ void k_bcc_count(int64_t n, const uint32_t* __restrict__ bmin, unsign
 template <class OffT>
 size_t bcc_workspace_bytes(int64_t n, int64_t A) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256 + 256; };
-  const int64_t T = n, P = 2 * T, nb = (P + 31) / 32 + 1;
+  const int64_t T = n, P = 2 * T, nb = (T + 31) / 32 + 1;
   int levels = 1;
   while ((1LL << levels) <= nb) ++levels;
   size_t b = cc_workspace_bytes<OffT>(n, A) + euler_cc_workspace_bytes(n, A, n, n / 2 + 1);
@@ -405,8 +420,9 @@ size_t bcc_workspace_bytes(int64_t n, int64_t A) {
   b += al((size_t)P * 4);                              // ranks
   b += al((size_t)(n / 2 + 2) * 8) * 2 + al(scan_tmp_words(n / 2 + 2) * 8);
   b += al((size_t)n * 4);                              // bmin
-  b += 2 * kStLevels * al((size_t)P * 4);              // in-block tables
-  b += 2 * al((size_t)levels * nb * 4);                // block tables
+  b += kStLevels * al((size_t)T * 8);                  // in-block tables of {lo, hi}
+  b += al((size_t)levels * nb * 8);                    // block table
+  b += 2 * al((size_t)(P / 32 + 2) * 4) + al(scan_tmp_words(P / 32 + 1) * 8) + al((size_t)n * 4);
   b += al((size_t)(A / kArcTile + 2) * 4) + al(64);
   return b;
 }
@@ -463,33 +479,35 @@ rst_status bcc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, in
   }
   prof_mark(s, "k_bcc_local");
   if (T > 0) {
-    // range tables over the P tour positions
-    const int64_t nb = (P + 31) / 32;
+    // preorder indices of the T non-root vertices and range tables over them
+    const int64_t W = P / 32 + 1;
+    uint32_t* dbits = ar.take<uint32_t>(W + 1);
+    uint32_t* dpre = ar.take<uint32_t>(W + 1);
+    unsigned long long* wtmp = ar.take<unsigned long long>(scan_tmp_words(W));
+    int32_t* idx = ar.take<int32_t>(n);
+    const int64_t nb = (T + 31) / 32;
     int levels = 1;
     while ((1LL << levels) <= nb) ++levels;
     StPtrs sp;
     for (int k = 0; k < kStLevels; ++k) {
-      sp.lo[k] = ar.take<int32_t>(P);
-      sp.hi[k] = ar.take<int32_t>(P);
-      if (!sp.lo[k] || !sp.hi[k]) return RST_ERR_OOM;
+      sp.st[k] = ar.take<int2>(T);
+      if (!sp.st[k]) return RST_ERR_OOM;
     }
-    int32_t* blo = ar.take<int32_t>((int64_t)levels * nb);
-    int32_t* bhi = ar.take<int32_t>((int64_t)levels * nb);
-    if (!blo || !bhi) return RST_ERR_OOM;
-    RST_LAUNCH(k_fill_i32_pair, grid_for(P), kBlock, 0, s)(P, sp.lo[0], INT_MAX, sp.hi[0], INT_MIN);
-    RST_LAUNCH(k_bcc_place, gN, kBlock, 0, s)(n, parent, key, lo, hi, sp.lo[0], sp.hi[0]);
-    RST_LAUNCH(k_bcc_st, grid_for(P), kBlock, 0, s)(P, sp, blo, bhi);
-    for (int k = 1; k < levels; ++k) RST_LAUNCH(k_bcc_bst, grid_for(nb), kBlock, 0, s)(nb, k, blo, bhi);
+    int2* bst = ar.take<int2>((int64_t)levels * nb);
+    if (!dbits || !dpre || !wtmp || !idx || !bst) return RST_ERR_OOM;
+    RST_CUDA(cudaMemsetAsync(dbits, 0, (W + 1) * sizeof(uint32_t), s));
+    RST_LAUNCH(k_bcc_mark, gN, kBlock, 0, s)(n, parent, key, dbits);
+    RST_TRY(scan_popcount_words(dbits, dpre, W, wtmp, s));
+    RST_LAUNCH(k_fill_int2, grid_for(T), kBlock, 0, s)(T, sp.st[0], make_int2(INT_MAX, INT_MIN));
+    RST_LAUNCH(k_bcc_place, gN, kBlock, 0, s)(n, parent, key, dbits, dpre, lo, hi, idx, sp.st[0]);
+    RST_LAUNCH(k_bcc_st, grid_for(T), kBlock, 0, s)(T, sp, bst);
+    for (int k = 1; k < levels; ++k) RST_LAUNCH(k_bcc_bst, grid_for(nb), kBlock, 0, s)(nb, k, bst);
     prof_mark(s, "bcc_tables");
-    RmqView vlo, vhi;
-    for (int k = 0; k < kStLevels; ++k) {
-      vlo.st[k] = sp.lo[k];
-      vhi.st[k] = sp.hi[k];
-    }
-    vlo.bst = blo;
-    vhi.bst = bhi;
-    vlo.nb = vhi.nb = nb;
-    RST_LAUNCH(k_bcc_rule2, gN, kBlock, 0, s)(n, parent, key, end, vlo, vhi, uf, status);
+    RmqView v;
+    for (int k = 0; k < kStLevels; ++k) v.st[k] = sp.st[k];
+    v.bst = bst;
+    v.nb = nb;
+    RST_LAUNCH(k_bcc_rule2, gN, kBlock, 0, s)(n, parent, key, end, idx, lo, hi, v, uf, status);
     prof_mark(s, "k_bcc_rule2");
   }
   RST_LAUNCH(k_uf_compress, gN, kBlock, 0, s)(n, uf, status);
