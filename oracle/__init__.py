@@ -15,7 +15,10 @@ Parity status per function (what pins each one, see tests/test_oracle_pins.py):
 * ``bfs``          pinned: Manhattan levels on grids, brute-force parent rule.
 * ``verify``       pinned: Kirchhoff spanning-tree counts (n <= 6), mutations.
 * ``prrst``        parity unpinned for its edge set (the paper fixes no unique
-                   tree); its output is pinned only through ``verify``.
+                   tree); its output is pinned only through ``verify``.  From
+                   a given forest (edge insertions): hand-derived graft and
+                   reversal cases, and the invariants (valid RST of the new
+                   graph, every old tree edge kept, only inserted edges added).
 * ``bcc``          pinned: brute-force blocks from every simple cycle and cut
                    vertices by deletion (n <= 8), closed forms (cycle, path,
                    star, bowtie, grid), networkx where installed.
@@ -50,6 +53,7 @@ def _L():
         lib.or_verify.argtypes = [I64, P, P, I32, P, I]
         if hasattr(lib, "or_prrst"):
             lib.or_prrst.argtypes = [I64, P, P, I32, P, P]
+            lib.or_prrst_from.argtypes = [I64, P, P, I32, P, P, P]
         lib.or_bcc.argtypes = [I64, P, P, P, P, P]
         _lib = lib
     return _lib
@@ -134,11 +138,17 @@ def rst(n, offsets, cols, root):
     return root_forest(n, tu, tv, root)
 
 
-def prrst(n, offsets, cols, root):
+def prrst(n, offsets, cols, root, init=None):
+    """PR-RST rounds from singletons, or from the rooted forest `init` (the
+    incremental case: cols then hold the old edges plus the inserted ones)."""
     off, col = _csr(offsets, cols)
     par = np.empty(max(n, 1), np.int32)
     rounds = ctypes.c_int64(0)
-    rc = _L().or_prrst(n, _p(off), _p(col), int(root), _p(par), ctypes.byref(rounds))
+    if init is None:
+        rc = _L().or_prrst(n, _p(off), _p(col), int(root), _p(par), ctypes.byref(rounds))
+    else:
+        ini = np.ascontiguousarray(np.asarray(init, dtype=np.int32))
+        rc = _L().or_prrst_from(n, _p(off), _p(col), int(root), _p(ini), _p(par), ctypes.byref(rounds))
     if rc != 0:
         raise ValueError(f"or_prrst failed: {rc}")
     return par[:n].copy(), rounds.value

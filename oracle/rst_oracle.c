@@ -27,7 +27,9 @@
  *                   neighbour on the previous level.
  *   or_verify       exact RST verdict with a reason code.
  *   or_prrst        the PR-RST rounds of Section III-C simulated one step at a
- *                   time (alternating min/max hooking, path reversal).
+ *                   time (alternating min/max hooking, path reversal);
+ *                   or_prrst_from starts them from a given rooted forest
+ *                   (edge insertions into an existing tree).
  *   or_bcc          biconnected components (blocks) and cut vertices by the
  *                   textbook depth-first search with an edge stack (Hopcroft
  *                   and Tarjan): the consumer of rooted trees that motivates
@@ -430,8 +432,25 @@ static void reverse_and_graft(const int32_t *P, int32_t *Q, int32_t u, int32_t v
  *   rounds_out: number of rounds executed (the final hook-free one included)
  * Returns 0, -1 for a bad root or id.
  */
+int or_prrst_from(int64_t n, const int64_t *off, const int32_t *col, int32_t root,
+                  const int32_t *init, int32_t *parent_out, int64_t *rounds_out);
+
 int or_prrst(int64_t n, const int64_t *off, const int32_t *col, int32_t root,
              int32_t *parent_out, int64_t *rounds_out) {
+    return or_prrst_from(n, off, col, root, NULL, parent_out, rounds_out);
+}
+
+/*
+ * The same rounds started from a given rooted forest instead of singletons:
+ * the incremental use of PR-RST's graft and path reversal (Section III-C;
+ * the paper's conclusion points to PR-RST for incremental graphs).  With
+ * init a rooted spanning forest of G and (off, col) the arcs of G plus a
+ * batch of new edges, only new edges can join two trees, so the result keeps
+ * every tree edge of init (some reversed) and adds new edges only.
+ *   init: n parents (roots P[r] = r), or NULL for singletons.
+ */
+int or_prrst_from(int64_t n, const int64_t *off, const int32_t *col, int32_t root,
+                  const int32_t *init, int32_t *parent_out, int64_t *rounds_out) {
     if (n <= 0) { *rounds_out = 0; return 0; }
     if (root < 0 || root >= n) return -1;
     int32_t *P = parent_out;
@@ -440,7 +459,21 @@ int or_prrst(int64_t n, const int64_t *off, const int32_t *col, int32_t root,
     int32_t *stk = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     uint64_t *best = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
     if (!Q || !rep || !best || !stk) { free(Q); free(rep); free(best); free(stk); return -3; }
-    for (int64_t v = 0; v < n; ++v) P[v] = (int32_t)v;
+    for (int64_t v = 0; v < n; ++v) {
+        P[v] = init ? init[v] : (int32_t)v;
+        if (P[v] < 0 || P[v] >= n) { free(Q); free(rep); free(best); free(stk); return -1; }
+    }
+    if (init) {  /* every parent chain must end at a root: rep[] = 0 unknown, 1 on the walk, 2 done */
+        for (int64_t v = 0; v < n; ++v) rep[v] = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t sp = 0;
+            int32_t x = (int32_t)v;
+            while (rep[x] == 0 && P[x] != x) { rep[x] = 1; stk[sp++] = x; x = P[x]; }
+            if (rep[x] == 1) { free(Q); free(rep); free(best); free(stk); return -2; }  /* a cycle */
+            rep[x] = 2;
+            while (sp) rep[stk[--sp]] = 2;
+        }
+    }
     int64_t t = 0;
     for (;; ++t) {
         tree_roots(n, P, rep, stk);
