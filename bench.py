@@ -336,6 +336,10 @@ def run_ours(args, rank, world, local_rank):
     bcc_rep = {"value": g.m / (bcc_ms / 1e3), "unit": "edges/s", "ms_per_step": bcc_ms,
                "blocks": bcc_blocks, "cut_vertices": int(bcc_cut.sum().item())}
 
+    # edge insertions: the forest of the graph with 45% of its edges held back,
+    # then those edges inserted with PR-RST graft and reversal
+    ins_rep = run_insert(g, dev, stream, rst, graphs, torch, max(3, args.bfs_steps))
+
     # tree shape (Fig. 2): heights of the trees each strategy returns
     heights = {}
     for strat in ("cc_euler", "bfs", "pr_rst", "cc_fast"):
@@ -378,6 +382,7 @@ def run_ours(args, rank, world, local_rank):
                         "note": "sampled union-find CC + the same Euler rooting; valid RST, tree not unique"},
             "tree_height": heights,
             "bcc": bcc_rep,
+            "insert": ins_rep,
             "batch": batch,
             "families": families,
             "selector": selector,
@@ -432,6 +437,41 @@ def run_batch(args, dev, stream, rst, graphs, torch):
             "graphs": b.G, "m": b.m, "batched_ms": batched, "per_graph_ms": per_graph,
             "batched_value": b.m / (batched / 1e3), "per_graph_value": b.m / (per_graph / 1e3),
             "unit": "edges/s", "speedup": per_graph / batched}
+
+
+def run_insert(g, dev, stream, rst, graphs, torch, reps):
+    """Rooted spanning forest of g minus a seeded 45% of its edges (CC+Euler;
+    below the square lattice's bond threshold, so a forest of many trees),
+    then the held-back edges inserted in one batch (rst_insert_edges)."""
+    import numpy as np
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets))
+    col = g.cols.astype(np.int64)
+    fwd = src < col
+    lo, hi = src[fwd], col[fwd]
+    drop = ((lo * 0x9E3779B1 + hi * 0x85EBCA77 + 11) % 1000003) < 450000
+    g0 = graphs.from_edges(g.n, lo[~drop], hi[~drop], root=g.root)
+    uv = torch.from_numpy(np.stack([lo[drop], hi[drop]], 1).astype(np.int32)).to(dev)
+    off0 = torch.from_numpy(g0.offsets).to(dev)
+    col0 = torch.from_numpy(g0.cols).to(dev)
+    base = rst.build(off0, col0, g.root, "cc_euler")
+    work = torch.empty_like(base)
+    ts = []
+    for i in range(reps + 1):
+        work.copy_(base)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rst.insert_edges(work, uv, g.root)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if i:
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    return {"workload": f"4096x4096 grid forest with {int(drop.sum())} edges (45%) held back, "
+                        f"then inserted in one batch", "inserted": int(drop.sum()), "ms": ms,
+            "trees_before": int((base.cpu() == torch.arange(g.n, dtype=torch.int32)).sum()),
+            "note": "PR-RST rounds from the existing forest over the inserted edges only"}
 
 
 def _time(fn, reps, torch, dev, stream, flush=None):

@@ -201,6 +201,28 @@ rst_status rst_verify(const void *csr_offsets, int offsets_bits, const int32_t *
 rst_status rst_bcc(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols, int64_t n, int64_t m,
                    uint32_t *block_out, uint8_t *cut_out, int64_t *num_blocks_out, rst_stream_t stream);
 
+/* rst_insert_edges -- update a rooted spanning forest after inserting edges,
+ * with PR-RST's graft and path reversal (Section III-C; the paper's
+ * conclusion names PR-RST as the path for incremental graphs).
+ *   n       number of vertices (unchanged by the insertion).
+ *   parent  device int32[n], in and out.  In: a rooted spanning forest of
+ *           the current graph G (parent[r] == r exactly at roots).  Out: a
+ *           rooted spanning forest of G plus the new edges: every old tree
+ *           edge is kept (some reoriented), only new edges are added; the tree
+ *           holding `root` is rooted at root, every other tree at its minimum
+ *           vertex.
+ *   new_uv  device int32[2k]: the inserted undirected edges {new_uv[2i],
+ *           new_uv[2i+1]} (self-loops and edges inside one tree change
+ *           nothing).
+ * The PR-RST rounds run from the given forest over the new edges only
+ * (minimum rule, then maximum, alternating; each tree takes its eligible
+ * edge with the smallest (u, v) key), which gives the same result as PR-RST
+ * rounds over all edges of the new graph started from that forest.
+ * Returns RST_ERR_DEVICE for an id outside [0, n) and RST_ERR_NOT_CONVERGED
+ * when `parent` holds a cycle. */
+rst_status rst_insert_edges(int64_t n, int32_t *parent, const int32_t *new_uv, int64_t k, int32_t root,
+                            rst_stream_t stream);
+
 /* rst_tree_depth -- depth of every vertex of a rooted forest, and its height
  * (Section IV-B, Fig. 2: the trees of connectivity-based strategies are
  * deeper than BFS trees; this measures that trade-off on any parent array).

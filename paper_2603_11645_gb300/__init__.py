@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["build", "build_batch", "cc", "euler_root", "verify", "tree_depth", "bcc", "set_option", "get_option", "lib",
+__all__ = ["build", "build_batch", "cc", "euler_root", "verify", "tree_depth", "bcc", "insert_edges", "set_option", "get_option", "lib",
            "RstError", "STRATEGIES"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,12 +45,13 @@ def lib():
         L.rst_build_batch.argtypes = [P, I, P, P, P, I32, P, I, P, P]
         L.rst_tree_depth.argtypes = [P, I64, P, P, P]
         L.rst_bcc.argtypes = [P, I, P, I64, I64, P, P, P, P]
+        L.rst_insert_edges.argtypes = [I64, P, P, I64, I32, P]
         L.rst_set_option.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
         L.rst_get_option.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong)]
         L.rst_status_string.argtypes = [I]
         L.rst_status_string.restype = ctypes.c_char_p
         L.rst_version.restype = I
-        for fn in ("rst_build", "rst_cc", "rst_euler_root", "rst_verify", "rst_shutdown", "rst_set_option", "rst_tree_depth", "rst_bcc",
+        for fn in ("rst_build", "rst_cc", "rst_euler_root", "rst_verify", "rst_shutdown", "rst_set_option", "rst_tree_depth", "rst_bcc", "rst_insert_edges",
                    "rst_get_option"):
             getattr(L, fn).restype = I
         for fn in ("rst_build_batch", "rst_select", "rst_build_batch_graph"):
@@ -198,3 +199,18 @@ def bcc(offsets, cols, want_cut: bool = True, stream=None):
                          ctypes.byref(nb), _stream(stream))
     _check("rst_bcc", code)
     return label, cut, int(nb.value)
+
+
+def insert_edges(parent, new_uv, root: int, stream=None):
+    """Updates the rooted spanning forest `parent` (int32 CUDA tensor, in
+    place) after inserting the undirected edges of `new_uv` (int32 CUDA
+    tensor of shape (k, 2)); returns `parent`."""
+    import torch
+    assert parent.is_cuda and parent.dtype == torch.int32 and parent.is_contiguous()
+    uv = new_uv.contiguous()
+    assert uv.is_cuda and uv.dtype == torch.int32 and (uv.numel() == 0 or uv.shape[-1] == 2)
+    k = uv.numel() // 2
+    code = lib().rst_insert_edges(parent.numel(), ctypes.c_void_p(parent.data_ptr()),
+                                  ctypes.c_void_p(uv.data_ptr()) if k else None, k, int(root), _stream(stream))
+    _check("rst_insert_edges", code)
+    return parent

@@ -77,6 +77,38 @@ __global__ void __launch_bounds__(kArcThreads) k_pr_hook(const OffT* __restrict_
   }
 }
 
+// The same proposals from a list of undirected edges (both orientations):
+// the arcs of an insertion batch.
+__global__ void k_pr_hook_edges(int64_t k, const int32_t* __restrict__ uv, int64_t n,
+                                const int32_t* __restrict__ rep, int max_rule,
+                                unsigned long long* __restrict__ best, uint32_t* status) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = uv[2 * j], b = uv[2 * j + 1];
+    if (a < 0 || b < 0 || (int64_t)a >= n || (int64_t)b >= n) {
+      raise_error(status, DERR_INDEX);
+      continue;
+    }
+    const int32_t ra = rep[a], rb = rep[b];
+    if (ra == rb) continue;
+    if (max_rule ? rb > ra : rb < ra)
+      atomicMin(&best[ra], ((unsigned long long)(uint32_t)a << 32) | (uint32_t)b);
+    else
+      atomicMin(&best[rb], ((unsigned long long)(uint32_t)b << 32) | (uint32_t)a);
+  }
+}
+
+// A given starting forest: copied in, parents checked against [0, n).
+__global__ void k_pr_load(int64_t n, const int32_t* __restrict__ init, int32_t* __restrict__ P, uint32_t* status) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t p = init[v];
+    if (p < 0 || (int64_t)p >= n) {
+      raise_error(status, DERR_INDEX);
+      p = (int32_t)v;
+    }
+    P[v] = p;
+  }
+}
+
 // Hooking roots start their paths: the bottom vertex u is marked and
 // remembers its graft target.
 __global__ void k_pr_start(int64_t n, const int32_t* __restrict__ P, const unsigned long long* __restrict__ best,
@@ -188,9 +220,12 @@ static rst_status pr_reverse(PrBufs& b, int64_t n, int K, cudaStream_t s) {
   return RST_OK;
 }
 
+// PR-RST rounds over the arcs of a CSR (off/col, A arcs) or, when uv is set,
+// over the k undirected edges of uv; from singletons, or from the rooted
+// forest `init` when it is set.
 template <class OffT>
 rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root, int32_t* parent,
-                      cudaStream_t s) {
+                      cudaStream_t s, const int32_t* init = nullptr, const int32_t* uv = nullptr, int64_t k = 0) {
   int levels = 2;
   while (((int64_t)1 << (levels - 2)) < n + 1 && levels < kPrMaxLevels) ++levels;
   const int64_t tiles = (A + kArcTile - 1) / kArcTile;
@@ -213,10 +248,14 @@ rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A,
   if (!b.flag) return RST_ERR_OOM;
   unsigned long long* hooks = dev_counter(0);
   const int g = grid_for(n);
-  RST_LAUNCH(k_pr_iota, g, kBlock, 0, s)(n, b.anc[0]);
+  uint32_t* status = st.status;
+  if (init)
+    RST_LAUNCH(k_pr_load, g, kBlock, 0, s)(n, init, b.anc[0], status);
+  else
+    RST_LAUNCH(k_pr_iota, g, kBlock, 0, s)(n, b.anc[0]);
   RST_CUDA(cudaMemsetAsync(b.mark, 0, n, s));
   RST_LAUNCH(k_pr_fill_i32, g, kBlock, 0, s)(n, b.graft, -1);
-  if (A > 0)
+  if (!uv && A > 0)
     RST_LAUNCH(k_arc_tile_rows<OffT>, grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
   int round = 0;
   for (;; ++round) {
@@ -225,9 +264,13 @@ rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A,
     RST_TRY(pr_history(b, n, s, &K));
     const int32_t* rep = b.anc[K];
     RST_LAUNCH(k_pr_fill_u64, g, kBlock, 0, s)(n, b.best);
-    if (A > 0)
+    if (uv) {
+      if (k > 0)
+        RST_LAUNCH(k_pr_hook_edges, grid_for(k), kBlock, 0, s)(k, uv, n, rep, round & 1, b.best, status);
+    } else if (A > 0) {
       RST_LAUNCH(k_pr_hook<OffT>, (unsigned)tiles, kArcThreads, 0, s)(off, col, n, A, b.tile_row, rep, round & 1,
                                                                     b.best);
+    }
     RST_CUDA(cudaMemsetAsync(hooks, 0, sizeof(unsigned long long), s));
     RST_LAUNCH(k_pr_start, g, kBlock, 0, s)(n, b.anc[0], b.best, b.mark, b.graft, hooks);
     unsigned long long h = 0;
@@ -257,6 +300,13 @@ rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int
                      int32_t* parent, cudaStream_t s) {
   if (offsets_bits == 32) return prrst_impl<int32_t>((const int32_t*)off, cols, n, m, root, parent, s);
   return prrst_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, s);
+}
+
+rst_status run_prrst_insert(int64_t n, int32_t* parent, const int32_t* uv, int64_t k, int32_t root,
+                            cudaStream_t s) {
+  // the rounds read the starting forest from `parent` and write the result
+  // back to it at the end (the copy into the history buffers comes first)
+  return prrst_impl<int32_t>(nullptr, nullptr, n, 0, root, parent, s, parent, uv, k);
 }
 
 }  // namespace rst

@@ -48,6 +48,10 @@ rst_status bcc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, in
 size_t depth_workspace_bytes(int64_t n);
 rst_status tree_depth(const int32_t* parent, int64_t n, int32_t* depth_out, int64_t* max_out,
                       cudaStream_t s);
+// PR-RST rounds started from the rooted forest in `parent` over k inserted
+// edges (uv pairs); the result replaces `parent` (prrst.cu).
+rst_status run_prrst_insert(int64_t n, int32_t* parent, const int32_t* uv, int64_t k, int32_t root,
+                            cudaStream_t s);
 rst_status run_verify(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                       int32_t root, const int32_t* parent, int32_t* verdict_out, cudaStream_t s);
 

@@ -1,0 +1,94 @@
+"""rst_insert_edges (PR-RST rounds from an existing forest) against the
+oracle's rounds from the same forest: bit-exact parent arrays."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_11645_gb300 import graphs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _graph(n, edges):
+    return graphs.from_edges(n, [e[0] for e in edges], [e[1] for e in edges], root=0)
+
+
+def _gpu_insert(init, new, root):
+    import paper_2603_11645_gb300 as rst
+    par = torch.from_numpy(np.asarray(init, dtype=np.int32)).cuda()
+    uv = torch.from_numpy(np.asarray(new, dtype=np.int32).reshape(-1, 2)).cuda()
+    rst.insert_edges(par, uv, root)
+    return par.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,old,init,new,root", [
+    (4, [(0, 1), (1, 2)], [0, 0, 1, 3], [(2, 3)], 0),
+    (5, [(0, 1), (1, 2), (3, 4)], [0, 0, 1, 3, 3], [(4, 1)], 0),
+    (5, [(0, 1), (1, 2), (3, 4)], [0, 0, 1, 3, 3], [(4, 1)], 4),
+    (7, [(0, 5), (1, 6)], [0, 0, 2, 3, 4, 0, 1], [(5, 6), (0, 1)], 0),
+    (3, [(0, 1)], [0, 0, 2], [], 2),                 # no insertion: re-rooting only
+    (3, [(0, 1)], [0, 0, 2], [(2, 2), (0, 1)], 0),   # self-loop and an edge inside a tree
+])
+def test_insert_small(n, old, init, new, root):
+    g = _graph(n, old + new)
+    want, _ = oracle.prrst(n, g.offsets, g.cols, root, init=init)
+    assert np.array_equal(_gpu_insert(init, new, root), want)
+
+
+def _dropped(g, frac, seed):
+    """g minus a random fraction of its edges, and the dropped edges."""
+    rng = np.random.default_rng(seed)
+    src = np.repeat(np.arange(g.n), np.diff(g.offsets)).astype(np.int64)
+    col = g.cols.astype(np.int64)
+    lo, hi = np.minimum(src, col), np.maximum(src, col)
+    h = (lo * 0x9E3779B1 + hi * 0x85EBCA77 + seed) % 1000003
+    drop = h < frac * 1000003
+    keep = ~drop
+    g0 = graphs.from_edges(g.n, src[keep & (src < col)], col[keep & (src < col)], root=g.root)
+    new = np.stack([src[drop & (src < col)], col[drop & (src < col)]], 1)
+    return g0, new[rng.permutation(len(new))]
+
+
+@pytest.mark.parametrize("which,frac", [("er", 0.3), ("grid", 0.25), ("rmat", 0.5), ("chain", 0.2)])
+def test_insert_random_batches(which, frac):
+    g = {"er": lambda: graphs.erdos_renyi(20000, 25000, seed=51),
+         "grid": lambda: graphs.grid(300, 200, seed=52, permute=True, root="random"),
+         "rmat": lambda: graphs.rmat(14, 8, seed=53, connect=False, offsets_bits=32),
+         "chain": lambda: graphs.chain_chords(30000, 0.001, seed=54)}[which]()
+    g0, new = _dropped(g, frac, seed=5)
+    init = oracle.rst(g0.n, g0.offsets, g0.cols, g0.root)
+    root = int(g.root)
+    want, _ = oracle.prrst(g.n, g.offsets, g.cols, root, init=init)
+    got = _gpu_insert(init, new, root)
+    assert np.array_equal(got, want)
+    assert oracle.verify(g.n, g.offsets, g.cols, root, got) == oracle.VALID
+
+
+def test_insert_after_a_gpu_build():
+    import paper_2603_11645_gb300 as rst
+    g = graphs.grid(1024, 1024, seed=55, permute=True, root="random")
+    g0, new = _dropped(g, 0.3, seed=6)
+    off0 = torch.from_numpy(g0.offsets).cuda()
+    col0 = torch.from_numpy(g0.cols).cuda()
+    par = rst.build(off0, col0, g.root, "cc_euler")
+    init = par.cpu().numpy()
+    rst.insert_edges(par, torch.from_numpy(new.astype(np.int32)).cuda(), g.root)
+    want, _ = oracle.prrst(g.n, g.offsets, g.cols, g.root, init=init)
+    assert np.array_equal(par.cpu().numpy(), want)
+
+
+def test_insert_rejects_bad_ids_and_cycles():
+    import paper_2603_11645_gb300 as rst
+    par = torch.tensor([0, 0, 1], dtype=torch.int32, device="cuda")
+    with pytest.raises(rst.RstError) as e:
+        rst.insert_edges(par, torch.tensor([[0, 9]], dtype=torch.int32, device="cuda"), 0)
+    assert e.value.code == 7
+    cyc = torch.tensor([1, 2, 0], dtype=torch.int32, device="cuda")
+    with pytest.raises(rst.RstError) as e:
+        rst.insert_edges(cyc, torch.zeros((0, 2), dtype=torch.int32, device="cuda"), 0)
+    assert e.value.code == 4
+    # the library stays usable
+    ok = torch.tensor([0, 0, 2], dtype=torch.int32, device="cuda")
+    rst.insert_edges(ok, torch.tensor([[1, 2]], dtype=torch.int32, device="cuda"), 0)
+    assert ok.cpu().tolist() == [0, 0, 1]
