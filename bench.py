@@ -186,7 +186,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
 
     import paper_2603_11645_gb300 as rst
-    from paper_2603_11645_gb300 import graphs
+    from paper_2603_11645_gb300 import graphs, multi
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -235,12 +235,8 @@ def run_ours(args, rank, world, local_rank):
     L.rst_profile_enable(0)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * g.m * args.steps / (total_ms / 1e3)
+    total_ms = multi.max_over_ranks(sum(step_ms), dev)  # the slowest replica
+    value = multi.whole_job_rate(g.m * args.steps, world, total_ms / 1e3)
 
     # stage times: the dominant kernel of the timed region
     stages = {}
@@ -289,12 +285,8 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * g.m * e2e_steps / (e2e_total / 1e3)
+    e2e_total = multi.max_over_ranks(sum(e2e_ms), dev)
+    e2e_value = multi.whole_job_rate(g.m * e2e_steps, world, e2e_total / 1e3)
 
     # the library's own GPU BFS on the same graph (the step-bound baseline)
     bfs_ms = []
@@ -346,7 +338,7 @@ def run_ours(args, rank, world, local_rank):
         step(strat)
         heights[strat] = rst.tree_depth(par, want_depths=False)[1]
 
-    batch = None if args.no_batch else run_batch(args, dev, stream, rst, graphs, torch)
+    batch = None if args.no_batch else run_batch(args, dev, stream, rst, graphs, torch, rank, world)
     families = None if args.no_families else run_families(args, dev, stream, rst, graphs, torch)
     selector = run_selector_report(off, col, g.root, torch)
 
@@ -392,9 +384,16 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def run_batch(args, dev, stream, rst, graphs, torch):
-    """4096 mixed graphs: one rst_build_batch call vs one rst_build call per graph."""
-    b = graphs.workload_batch()
+def run_batch(args, dev, stream, rst, graphs, torch, rank=0, world=1):
+    """4096 mixed graphs: one rst_build_batch call vs one rst_build call per
+    graph.  With several ranks the graphs are split by arc count (LPT) and
+    each rank builds its share; times are the slowest rank's."""
+    from paper_2603_11645_gb300 import multi
+    full = graphs.workload_batch()
+    b = full
+    if world > 1:
+        shard = multi.lpt_shards([g.A for g in full.graphs], world)[rank]
+        b = graphs.pack_batch([full.graphs[i] for i in shard])
     from paper_2603_11645_gb300 import autotune
     autotune.apply(b.N, b.A)
     off = torch.from_numpy(b.offsets).to(dev)
@@ -414,7 +413,7 @@ def run_batch(args, dev, stream, rst, graphs, torch):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         times.append(e0.elapsed_time(e1))
-    batched = statistics.median(times)
+    batched = multi.max_over_ranks(statistics.median(times), dev)
     # per-graph launches over the same resident data (zero-copy views)
     views = []
     for g_i, g in enumerate(b.graphs):
@@ -431,11 +430,13 @@ def run_batch(args, dev, stream, rst, graphs, torch):
         rst.build(o, c, r, out=p)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    per_graph = e0.elapsed_time(e1)
-    return {"workload": f"{b.G} graphs (grid / chain+chords / R-MAT in turn), n log-uniform 1K-4K, "
-                        f"{b.N} vertices, {b.A} arcs, int32 packed CSR",
-            "graphs": b.G, "m": b.m, "batched_ms": batched, "per_graph_ms": per_graph,
-            "batched_value": b.m / (batched / 1e3), "per_graph_value": b.m / (per_graph / 1e3),
+    per_graph = multi.max_over_ranks(e0.elapsed_time(e1), dev)
+    return {"ranks": world,
+            "workload": f"{full.G} graphs (grid / chain+chords / R-MAT in turn), n log-uniform 1K-4K, "
+                        f"{full.N} vertices, {full.A} arcs, int32 packed CSR"
+                        + (f", split over {world} ranks by arc count" if world > 1 else ""),
+            "graphs": full.G, "m": full.m, "batched_ms": batched, "per_graph_ms": per_graph,
+            "batched_value": full.m / (batched / 1e3), "per_graph_value": full.m / (per_graph / 1e3),
             "unit": "edges/s", "speedup": per_graph / batched}
 
 
