@@ -33,10 +33,12 @@ def _entry():
 def _cases():
     return [graphs.workload_grid256(),
             graphs.rmat(12, 8, seed=21, connect=False, offsets_bits=64),
-            graphs.erdos_renyi(5000, 9000, seed=3)]
+            graphs.erdos_renyi(5000, 9000, seed=3),
+            # at the documented limits: 65,536 vertices, just under 524,288 arcs
+            graphs.erdos_renyi(65536, 262000, seed=5)]
 
 
-@pytest.mark.parametrize("gi", range(3))
+@pytest.mark.parametrize("gi", range(4))
 def test_noalloc_equals_rst_build_on_two_calls(gi):
     import paper_2603_11645_gb300 as rst
     g = _cases()[gi]
