@@ -829,6 +829,24 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   return RST_OK;
 }
 
+// Round 1 alone (the sampled connectivity strategy starts from it): P ends
+// as every vertex's round-1 root, pairs[0, counters[0]) holds the tree-edge
+// records and bits marks both of their arcs (bits must start zeroed).
+template <class OffT>
+rst_status round1_forest(const OffT* off, const int32_t* col, int64_t n, int32_t* P, uint32_t* J,
+                         uint4* pairs, uint32_t* bits, unsigned long long* counters, cudaStream_t s) {
+  uint32_t* status = state().status;
+  const int gN = grid_for(n);
+  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, status);
+  RST_LAUNCH(k_r1_resolve<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, pairs, bits, counters, status);
+  RST_CUDA(cudaGetLastError());
+  return RST_OK;
+}
+template rst_status round1_forest<int32_t>(const int32_t*, const int32_t*, int64_t, int32_t*, uint32_t*, uint4*,
+                                           uint32_t*, unsigned long long*, cudaStream_t);
+template rst_status round1_forest<int64_t>(const int64_t*, const int32_t*, int64_t, int32_t*, uint32_t*, uint4*,
+                                           uint32_t*, unsigned long long*, cudaStream_t);
+
 template rst_status cc_run<int32_t>(Arena&, const int32_t*, const int32_t*, int64_t, int64_t,
                                     int32_t, int32_t*, CcOut*, cudaStream_t);
 template rst_status cc_run<int64_t>(Arena&, const int64_t*, const int32_t*, int64_t, int64_t,

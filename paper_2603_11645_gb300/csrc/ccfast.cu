@@ -2,11 +2,15 @@
 // (the hooking freedom Section III-B leaves: any rule that merges components
 // works; this one trades the deterministic minimum-key forest for less work).
 //
-//  1 sampling: for r < kSampleRounds every vertex links with the r-th
-//    neighbour of its row (link = find both roots, CAS the larger root's
-//    pointer to the smaller one); one successful CAS merges two trees, so the
-//    arc that made it is a spanning-forest edge and is recorded;
-//  2 compress every pointer to its root;
+//  1 first neighbours: the atomic-free round 1 of the deterministic path
+//    (every vertex hooks to the first entry of its sorted row; mutual pairs
+//    are the roots) gives a forest whose roots are its trees' minimum
+//    vertices, the tree-edge records with their twin arcs, and P pointing at
+//    the roots, which is a ready union-find state;
+//  2 sampling: every vertex links with the second entry of its row (link =
+//    find both roots, CAS the larger root's pointer to the smaller one); one
+//    successful CAS merges two trees, so the arc that made it is a
+//    spanning-forest edge and is recorded; then every pointer is compressed;
 //  3 the most frequent root among a fixed sample of vertices is the giant
 //    component; vertices outside it link with the rest of their rows (an edge
 //    from the giant to another component is met from the other side);
@@ -27,16 +31,12 @@
 
 namespace rst {
 
-constexpr int kSampleRounds = 2;
+constexpr int kSampleRounds = 2;  // row entries 0 and 1 are linked for every vertex
 constexpr int kGiantSample = 1024;
 
-enum { FC_TREE = 0, FC_ROOTS = 1, FC_GIANT_ROOT = 2, FC_ROOT_LABEL = 3 };
-
-__global__ void k_fast_init(int64_t n, int32_t* __restrict__ uf) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x)
-    uf[v] = (int32_t)v;
-}
+// counters: round-1 records (the index round 1 counts in), roots, the giant
+// root, the requested root's label, union-find tree edges
+enum { FC_R1 = 0, FC_ROOTS = 1, FC_GIANT_ROOT = 2, FC_ROOT_LABEL = 3, FC_TREE = 4 };
 
 // Round r of the sampling: vertex u links with the r-th entry of its row.
 template <class OffT>
@@ -123,12 +123,14 @@ __global__ void k_fast_rest(const OffT* __restrict__ off, const int32_t* __restr
   }
 }
 
-// Tree-edge records and bitmap marks; roots of components with edges.
+// Tree-edge records (after round 1's) and bitmap marks of the union-find
+// edges; roots of components with edges.
 template <class OffT>
 __global__ void k_fast_pairs(const OffT* __restrict__ off, const int32_t* __restrict__ col,
                              const int3* __restrict__ tl, const unsigned long long* cnt,
-                             uint4* __restrict__ pairs, uint32_t* __restrict__ bits, uint32_t* status) {
+                             uint4* __restrict__ pairs0, uint32_t* __restrict__ bits, uint32_t* status) {
   const int64_t T = (int64_t)cnt[FC_TREE];
+  uint4* __restrict__ pairs = pairs0 + cnt[FC_R1];
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int3 e = tl[t];
@@ -163,7 +165,7 @@ __global__ void k_fast_roots(const OffT* __restrict__ off, int64_t n, const int3
 template <class OffT>
 size_t ccfast_workspace_bytes(int64_t n, int64_t A) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256 + 256; };
-  return al((size_t)n * 4) + al((size_t)n * 12) + al((size_t)n * 16) + al(((size_t)A / 32 + 2) * 4) +
+  return 2 * al((size_t)n * 4) + al((size_t)n * 12) + al((size_t)n * 16) + al(((size_t)A / 32 + 2) * 4) +
          al((size_t)(n / 2 + 1) * 4) + al(8 * 8);
 }
 
@@ -171,20 +173,21 @@ template <class OffT>
 rst_status ccfast_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
                       int32_t* labels_out, CcOut* out, cudaStream_t s) {
   int32_t* uf = ar.take<int32_t>(n);
+  uint32_t* J = ar.take<uint32_t>(n);
   int3* tl = ar.take<int3>(n);
   uint4* pairs = ar.take<uint4>(n);
   uint32_t* bits = ar.take<uint32_t>(A / 32 + 2);
   int32_t* roots = ar.take<int32_t>(n / 2 + 1);
   unsigned long long* cnt = ar.take<unsigned long long>(8);
-  if (!uf || !tl || !pairs || !bits || !roots || !cnt) return RST_ERR_OOM;
+  if (!uf || !J || !tl || !pairs || !bits || !roots || !cnt) return RST_ERR_OOM;
   uint32_t* status = state().status;
   const int gN = grid_for(n);
   RST_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
   RST_CUDA(cudaMemsetAsync(bits, 0, (A / 32 + 2) * sizeof(uint32_t), s));
-  RST_LAUNCH(k_fast_init, gN, kBlock, 0, s)(n, uf);
   prof_mark(s, "fast_setup");
-  for (int r = 0; r < kSampleRounds; ++r)
-    RST_LAUNCH(k_fast_sample<OffT>, gN, kBlock, 0, s)(off, col, n, r, uf, tl, cnt, n, status);
+  RST_TRY(round1_forest<OffT>(off, col, n, uf, J, pairs, bits, cnt, s));
+  prof_mark(s, "fast_round1");
+  RST_LAUNCH(k_fast_sample<OffT>, gN, kBlock, 0, s)(off, col, n, 1, uf, tl, cnt, n, status);
   prof_mark(s, "k_fast_sample");
   RST_LAUNCH(k_uf_compress, gN, kBlock, 0, s)(n, uf, status);
   RST_LAUNCH(k_fast_giant, 1, kBlock, 0, s)(n, uf, cnt);
@@ -200,7 +203,7 @@ rst_status ccfast_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n,
     RST_CUDA(cudaMemcpyAsync(labels_out, uf, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   unsigned long long h[8];
   RST_TRY(fetch_u64(cnt, 8, h, s));
-  out->T = (int64_t)h[FC_TREE];
+  out->T = (int64_t)(h[FC_R1] + h[FC_TREE]);
   out->pairs = pairs;
   out->bits = bits;
   out->nroots = (int64_t)h[FC_ROOTS];

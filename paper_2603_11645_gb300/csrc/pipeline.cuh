@@ -45,6 +45,11 @@ template <class OffT>
 size_t cc_workspace_bytes(int64_t n, int64_t A);
 // Release cached round graphs (rst_shutdown).
 void destroy_round_graphs();
+// Round 1 of the hooking alone (cc.cu): P = round-1 roots, tree-edge records
+// counted in counters[0], their arcs marked in bits.
+template <class OffT>
+rst_status round1_forest(const OffT* off, const int32_t* col, int64_t n, int32_t* P, uint32_t* J,
+                         uint4* pairs, uint32_t* bits, unsigned long long* counters, cudaStream_t s);
 // The same outputs from sampled union-find hooking (ccfast.cu): a valid
 // spanning forest with the same components, chosen by races (not unique).
 template <class OffT>
