@@ -20,9 +20,10 @@ def declared_functions():
     return sorted(names)
 
 
-def test_header_declares_the_survey_calls():
+def test_header_declares_the_core_calls():
     names = declared_functions()
-    for want in ["rst_build", "rst_cc", "rst_euler_root", "rst_verify", "rst_status_string"]:
+    for want in ["rst_build", "rst_cc", "rst_euler_root", "rst_build_batch", "rst_select", "rst_verify",
+                 "rst_status_string", "rst_bcc", "rst_insert_edges", "rst_tree_depth", "rst_set_option"]:
         assert want in names
 
 
