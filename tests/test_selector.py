@@ -167,3 +167,33 @@ def test_selector_regret_beats_always_cc_euler():
     r_cc = S.regret(Tt, np.ones(len(Tt), dtype=int))
     assert r_sel <= r_cc
     assert r_sel <= 0.10
+
+
+@pytest.mark.gpu
+def test_auto_strategy_builds_what_the_selector_chooses():
+    """RST_AUTO runs the strategy rst_select picks, with that strategy's exact result."""
+    import oracle
+    import paper_2603_11645_gb300 as rst
+    from paper_2603_11645_gb300 import selector as S
+    if S.load_default() is None:
+        pytest.skip("no trained selector weights in the repository")
+    cases = [graphs.grid(300, 200, seed=61, permute=True, root="random"),
+             graphs.rmat(14, 16, seed=62, connect=True, offsets_bits=32),
+             graphs.chain_chords(20000, 0.01, seed=63),
+             graphs.random_4regular(5000, seed=64)]
+    seen = set()
+    for g in cases:
+        off = torch.from_numpy(g.offsets).cuda()
+        col = torch.from_numpy(g.cols).cuda()
+        choice, pred = S.select(off, col, g.root)
+        assert np.all(np.isfinite(pred))
+        par = rst.build(off, col, g.root, "auto").cpu().numpy()
+        if choice == "cc_euler":
+            want = oracle.rst(g.n, g.offsets, g.cols, g.root)
+        elif choice == "bfs":
+            want = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
+        else:
+            want = oracle.prrst(g.n, g.offsets, g.cols, g.root)[0]
+        assert np.array_equal(par, want), (g.name, choice)
+        seen.add(choice)
+    assert seen  # at least one strategy exercised through RST_AUTO
