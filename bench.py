@@ -389,7 +389,7 @@ def run_batch(args, dev, stream, rst, graphs, torch, rank=0, world=1):
     graph.  With several ranks the graphs are split by arc count (LPT) and
     each rank builds its share; times are the slowest rank's."""
     from paper_2603_11645_gb300 import multi
-    full = graphs.workload_batch()
+    full = graphs.workload_batch(hi=args.batch_hi)
     b = full
     if world > 1:
         shard = multi.lpt_shards([g.A for g in full.graphs], world)[rank]
@@ -432,7 +432,8 @@ def run_batch(args, dev, stream, rst, graphs, torch, rank=0, world=1):
     torch.cuda.synchronize(dev)
     per_graph = multi.max_over_ranks(e0.elapsed_time(e1), dev)
     return {"ranks": world,
-            "workload": f"{full.G} graphs (grid / chain+chords / R-MAT in turn), n log-uniform 1K-4K, "
+            "workload": f"{full.G} graphs (grid / chain+chords / R-MAT in turn), n log-uniform "
+                        f"1K-{args.batch_hi // 1024}K, "
                         f"{full.N} vertices, {full.A} arcs, int32 packed CSR"
                         + (f", split over {world} ranks by arc count" if world > 1 else ""),
             "graphs": full.G, "m": full.m, "batched_ms": batched, "per_graph_ms": per_graph,
@@ -593,6 +594,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-families", action="store_true")
+    ap.add_argument("--batch-hi", type=int, default=4096,
+                    help="largest vertex count of the batch's graphs (262144: the literal 1K-256K size law)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="SIDE",
                     help="only run the CC+Euler step (W warm-up + K steps, no timing) on a SIDE x SIDE "
                          "grid of the headline family; the command the ncu captures use")

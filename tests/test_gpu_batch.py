@@ -75,3 +75,25 @@ def test_batch_workload_4096_graphs():
     for g_i, g in enumerate(b.graphs):
         want = oracle.rst(g.n, g.offsets, g.cols, g.root)
         assert np.array_equal(par[b.vtx_off[g_i]:b.vtx_off[g_i + 1]], want), (g_i, g.name)
+
+
+@pytest.mark.skipif(__import__("os").environ.get("RST_MAX_SIZE") != "1", reason="opt-in: RST_MAX_SIZE=1")
+def test_batch_literal_size_law():
+    """4,096 graphs with n log-uniform in [1K, 256K] (about 2.5e9 arcs, int64
+    packed offsets): every graph's slice checked by the verifier on the GPU,
+    64 of them against the oracle bit for bit."""
+    import paper_2603_11645_gb300 as rst
+    b = graphs.workload_batch(hi=262144)
+    dev = to_dev(b)
+    par = rst.build_batch(*dev)
+    assert b.A > 2 ** 31
+    parn = par.cpu().numpy()
+    rng = np.random.default_rng(7)
+    sample = set(rng.choice(b.G, 64, replace=False).tolist())
+    for g_i, g in enumerate(b.graphs):
+        sl = parn[b.vtx_off[g_i]:b.vtx_off[g_i + 1]]
+        off = torch.from_numpy(g.offsets).cuda()
+        col = torch.from_numpy(g.cols).cuda()
+        assert rst.verify(off, col, g.root, torch.from_numpy(sl.copy()).cuda()) == 0, g_i
+        if g_i in sample:
+            assert np.array_equal(sl, oracle.rst(g.n, g.offsets, g.cols, g.root)), (g_i, g.name)
