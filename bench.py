@@ -111,8 +111,12 @@ def kernel_bytes(name, n, A, st, o):
     K = N // 2  # tree edges that are toured
     c1, E2 = st["c1"], st["E2"]
     models = {
-        "k_r1_choose": (n + 1) * o + 4 * n + 8 * n,
-        "k_r1_resolve": 16 * n + (n - c1) * (2 * o + 4 + 16) + 4 * n,
+        # offsets, the first entries of every row, P and J, a 32-byte row record
+        "k_r1_choose": (n + 1) * o + 4 * n + 8 * n + 32 * n,
+        # P, J, P written per vertex; per non-root the used part of the chosen
+        # neighbour's row record (start, degree and its row's entries, at most
+        # six) and a 16-byte tree-edge record
+        "k_r1_resolve": 16 * n + (n - c1) * (8 + 4 * min(A / max(n, 1), 6) + 16) + 4 * n,
         "k_r1_number": 8 * n + 8 * c1,
         "k_r1_label": 16 * n,
         "k_build_list": (n + 1) * o + 4 * A + 4 * n + 2 * A + 12 * E2,

@@ -50,7 +50,18 @@ struct CcCtl {
   unsigned int done;   // blocks of the round's last kernel that have finished
 };
 
+// Row record of a vertex, one aligned 32-byte sector: where its row starts,
+// its degree and the first kRecCols entries.  Round 1 reads the chosen
+// neighbour's record once instead of its pointer, its row bounds and its row.
+constexpr int kRecCols = 6;
+struct __align__(32) RowRec {
+  uint32_t start;
+  uint32_t deg;
+  int32_t c[kRecCols];
+};
+
 struct CcBuffers {
+  RowRec* rec;       // per-vertex row records (may be null)
   int32_t* P;        // n: round-1 hook target, then root
   uint32_t* J;       // n: CSR position of the arc to the first neighbour (kNone: isolated)
   int32_t* CID;      // n: dense component id of round-1 roots
@@ -75,6 +86,9 @@ struct CcBuffers {
 static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
   CcBuffers b{};
   int64_t half = n / 2 + 1;
+  // row records only where the workspace may grow (not in the fixed-scratch
+  // variant, whose size limits were set without them)
+  b.rec = state_overridden() ? nullptr : ar.take<RowRec>(n + 1);
   b.P = ar.take<int32_t>(n + 1);
   b.J = ar.take<uint32_t>(n + 1);
   b.CID = ar.take<int32_t>(n + 1);
@@ -119,10 +133,18 @@ enum { CNT_PAIRS = 0, CNT_COMPS = 1, CNT_LIST = 2, CNT_ROOTS = 3, CNT_NEXT = 4, 
 template <class OffT>
 __global__ void k_r1_choose(const OffT* __restrict__ off, const int32_t* __restrict__ col,
                             int64_t n, int32_t* __restrict__ P, uint32_t* __restrict__ J,
-                            uint32_t* status) {
+                            RowRec* __restrict__ rec, uint32_t* status) {
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
     int64_t j = (int64_t)off[u], hi = (int64_t)off[u + 1];
+    if (rec) {
+      RowRec r;
+      r.start = (uint32_t)j;
+      r.deg = (uint32_t)(hi - j);
+#pragma unroll
+      for (int i = 0; i < kRecCols; ++i) r.c[i] = j + i < hi ? col[j + i] : -1;
+      rec[u] = r;
+    }
     while (j < hi && col[j] == (int32_t)u) ++j;
     int32_t v0 = (int32_t)u;
     uint32_t jj = kNone;
@@ -148,8 +170,8 @@ __global__ void k_r1_choose(const OffT* __restrict__ off, const int32_t* __restr
 template <class OffT>
 __global__ void k_r1_resolve(const OffT* __restrict__ off, const int32_t* __restrict__ col,
                              int64_t n, int32_t* P, const uint32_t* __restrict__ J,
-                             uint4* __restrict__ pairs, uint32_t* __restrict__ bits,
-                             unsigned long long* counters, uint32_t* status) {
+                             const RowRec* __restrict__ rows, uint4* __restrict__ pairs,
+                             uint32_t* __restrict__ bits, unsigned long long* counters, uint32_t* status) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t u = base + threadIdx.x;
@@ -158,12 +180,46 @@ __global__ void k_r1_resolve(const OffT* __restrict__ off, const int32_t* __rest
     if (u < n) {
       const int32_t v0 = P[u];  // only this thread writes P[u]
       if (v0 != (int32_t)u) {
-        const bool mutual = (P[v0] == (int32_t)u);
+        // v0's first choice y0 (its first non-self entry), its row start and
+        // u's position q in its row: from v0's record when it holds the
+        // whole row, else from P and the CSR
+        int32_t y0 = -1;
+        int64_t q = -1;
+        bool have_q = false;
+        int64_t lo = 0, end = 0;
+        if (rows) {
+          const RowRec R = rows[v0];
+          lo = (int64_t)R.start;
+          end = lo + (int64_t)R.deg;
+#pragma unroll
+          for (int i = kRecCols - 1; i >= 0; --i)
+            if (i < (int)R.deg && R.c[i] != v0) y0 = R.c[i];
+#pragma unroll
+          for (int i = kRecCols - 1; i >= 0; --i)
+            if (i < (int)R.deg && R.c[i] == (int32_t)u) q = lo + i;
+          have_q = R.deg <= (uint32_t)kRecCols;
+          if (y0 < 0 || (int64_t)y0 >= n) y0 = P[v0];  // long row of self-loops, or a bad id
+        } else {
+          y0 = P[v0];
+          lo = (int64_t)off[v0];
+          end = (int64_t)off[v0 + 1];
+        }
+        const bool mutual = (y0 == (int32_t)u);
         const bool is_root = mutual && (int32_t)u < v0;
         if (is_root) {
           P[u] = (int32_t)u;
         } else {
-          int64_t q = row_find(off, col, v0, (int32_t)u);
+          if (!have_q) {
+            int64_t L = lo, H = end;
+            while (L < H) {
+              const int64_t mid = (L + H) >> 1;
+              if (col[mid] < (int32_t)u)
+                L = mid + 1;
+              else
+                H = mid;
+            }
+            q = (L < end && col[L] == (int32_t)u) ? L : -1;
+          }
           if (q < 0) {
             raise_error(status, DERR_INDEX);  // the CSR is not symmetric
           } else {
@@ -172,14 +228,19 @@ __global__ void k_r1_resolve(const OffT* __restrict__ off, const int32_t* __rest
             atomicOr(&bits[rec.x >> 5], 1u << (rec.x & 31));
             atomicOr(&bits[rec.y >> 5], 1u << (rec.y & 31));
           }
-          // chase to the root
-          int32_t x = v0, r = -1;
-          for (int64_t it = 0; it <= n; ++it) {
-            const int32_t y = P[x];
-            if (y == x) { r = x; break; }
-            const int32_t z = P[y];
-            if (z == x) { r = x < y ? x : y; break; }
-            x = y;
+          // chase to the root: x -> y = P[x] -> z = P[y]; the first y is y0
+          int32_t r = -1;
+          if (mutual) {
+            r = v0;  // the pair's smaller end (u > v0 here)
+          } else {
+            int32_t x = v0, y = y0;
+            for (int64_t it = 0; it <= n; ++it) {
+              if (y == x) { r = x; break; }
+              const int32_t z = P[y];
+              if (z == x) { r = x < y ? x : y; break; }
+              x = y;
+              y = z;
+            }
           }
           if (r < 0) {
             raise_error(status, DERR_ROUND_LIMIT);
@@ -730,9 +791,9 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
 
   const int gN = grid_for(n);
   prof_mark(s, "cc_setup");
-  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, status);
+  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, status);
   prof_mark(s, "k_r1_choose");
-  RST_LAUNCH(k_r1_resolve<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.pairs, b.bits, cnt, status);
+  RST_LAUNCH(k_r1_resolve<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, cnt, status);
   prof_mark(s, "k_r1_resolve");
   RST_LAUNCH(k_r1_number, gN, kBlock, 0, s)(n, b.P, b.J, b.CID, b.minvpool, cnt);
   prof_mark(s, "k_r1_number");
@@ -837,8 +898,8 @@ rst_status round1_forest(const OffT* off, const int32_t* col, int64_t n, int32_t
                          uint4* pairs, uint32_t* bits, unsigned long long* counters, cudaStream_t s) {
   uint32_t* status = state().status;
   const int gN = grid_for(n);
-  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, status);
-  RST_LAUNCH(k_r1_resolve<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, pairs, bits, counters, status);
+  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, nullptr, status);
+  RST_LAUNCH(k_r1_resolve<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, nullptr, pairs, bits, counters, status);
   RST_CUDA(cudaGetLastError());
   return RST_OK;
 }
