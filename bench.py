@@ -123,8 +123,10 @@ def kernel_bytes(name, n, A, st, o):
         "k_toff": (n + 1) * (o + 8 + 4) + 2 * n,
         "k_prune_leaves": 16 * T + 2 * T + 4 * (T - K),
         "k_pairs_succ": 16 * T + K * (16 + 16 + 16 + 8),
-        "k_lr_walk1": 16 * N + 12 * ((N + 15) // 16),
-        "k_lr_final1": 8 * N + 4 * N + 4 * ((N + 15) // 16),
+        # successor read and packed 4-byte record written per element; per
+        # splitter its start, next splitter and weight
+        "k_lr_walk1": 8 * N + 12 * ((N + 15) // 16),
+        "k_lr_final1": 4 * N + 4 * N + 4 * ((N + 15) // 16),
         "k_parent_from_rank": 16 * T + K * (8 + 4),
     }
     return models.get(name)

@@ -8,6 +8,10 @@
 // 8-byte {owner splitter, offset} record per element to a separate array.
 // (Overwriting the successor record in place is several times slower on
 // GB300: the store to the address just loaded stalls the dependent chain.)
+// On the first level the record is packed into 32 bits (owner in the high
+// bits, offset in the low ones; an offset that does not fit goes to a full
+// 8-byte record): the scattered writes then land in an array half the size,
+// which L2 holds far better, and the walk runs about a quarter faster.
 // The splitters form a shorter weighted list, ranked the same way until it fits
 // one block's shared memory, where Wyllie pointer jumping finishes it.  A
 // final coalesced pass adds each owner's position to the element's offset.
@@ -30,6 +34,7 @@ constexpr int kLrMaxLevels = 24;  // N < 2^32 shrinks by ~K per level
 
 struct LevelBufs {
   int2* ol;         // N {owner, offset} records of this level
+  uint32_t* ol32;   // level 0: the same packed into 32 bits (null: unpacked)
   int32_t* snext;   // S successors of the next level
   uint32_t* w_next; // S weights of the next level
   int32_t* sstart;  // S (only the head slots are used)
@@ -52,10 +57,13 @@ struct LevelList {
 
 static void lr_layout(Arena& ar, int64_t N, int64_t h, int sh, LevelList* levels,
                       int32_t** wyl_pj, uint32_t** wyl_val, int32_t** wyl_flag) {
+  bool first = true;
   while (N > kLrBase && h <= N / 4) {
     const int64_t S = lr_splitters(N, h, sh);
     LevelBufs b;
     b.ol = ar.take<int2>(N);
+    b.ol32 = first ? ar.take<uint32_t>(N) : nullptr;
+    first = false;
     b.snext = ar.take<int32_t>(S);
     b.w_next = ar.take<uint32_t>(S);
     b.sstart = ar.take<int32_t>(S);
@@ -124,6 +132,7 @@ __global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S
                                                             const uint32_t* __restrict__ w,
                                                             const int32_t* __restrict__ sstart,
                                                             int2* __restrict__ ol,
+                                                            uint32_t* __restrict__ ol32, int fbits,
                                                             int32_t* __restrict__ snext,
                                                             uint32_t* __restrict__ w_next,
                                                             unsigned long long* visited,
@@ -138,12 +147,29 @@ __global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S
       w_next[s] = 0;
       continue;
     }
-    ol[start] = make_int2((int32_t)s, 0);
+    // packed records (first level, unit weights): owner in the high bits,
+    // offset in the low fbits; an offset that does not fit is written to ol
+    // and marked by the all-ones word
+    const uint32_t omax = ol32 ? (1u << fbits) - 1u : 0u;
+    const uint32_t ohi = ol32 ? (uint32_t)s << fbits : 0u;
+    if (ol32)
+      ol32[start] = ohi;
+    else
+      ol[start] = make_int2((int32_t)s, 0);
     uint32_t acc = wget(w, start);
     int32_t x = nxt[start];
     int64_t steps = 1;
     while (x >= 0 && (x & mask) != 0) {
-      ol[x] = make_int2((int32_t)s, (int32_t)acc);
+      if (ol32) {
+        if (acc < omax) {
+          ol32[x] = ohi | acc;
+        } else {
+          ol32[x] = 0xffffffffu;
+          ol[x] = make_int2((int32_t)s, (int32_t)acc);
+        }
+      } else {
+        ol[x] = make_int2((int32_t)s, (int32_t)acc);
+      }
       acc += wget(w, x);
       x = nxt[x];
       if (++steps > N) {
@@ -168,13 +194,20 @@ __global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S
 // An unvisited element's record holds whatever the workspace held before, so
 // the owner index is bounds-checked (S = number of splitters) before use.
 __global__ void k_lr_final(int64_t N, int64_t S, const int2* __restrict__ ol,
+                           const uint32_t* __restrict__ ol32, int fbits,
                            const uint32_t* __restrict__ spos, uint32_t* __restrict__ pos,
                            const unsigned long long* visited, uint32_t* status) {
   if (visited && blockIdx.x == 0 && threadIdx.x == 0 && *visited != (unsigned long long)N)
     raise_error(status, DERR_NOT_FOREST);
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
        x += (int64_t)gridDim.x * blockDim.x) {
-    const int2 r = ol[x];
+    int2 r;
+    if (ol32) {
+      const uint32_t v = ol32[x];
+      r = v != 0xffffffffu ? make_int2((int32_t)(v >> fbits), (int32_t)(v & ((1u << fbits) - 1u))) : ol[x];
+    } else {
+      r = ol[x];
+    }
     pos[x] = (r.x >= 0 && (int64_t)r.x < S) ? spos[r.x] + (uint32_t)r.y : kNone;
   }
 }
@@ -279,6 +312,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     uint32_t* pos;
   };
   Frame frames[kLrMaxLevels];
+  int lfbits[kLrMaxLevels] = {};
   Frame f{N, nxt, w, heads, pos};
   for (int l = 0; l < levels.count; ++l) {
     LevelBufs& b = levels.b[l];
@@ -287,8 +321,14 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     if (l == 0) RST_CUDA(cudaMemsetAsync(visited, 0, sizeof(unsigned long long), s));
     RST_LAUNCH(k_lr_heads, grid_for(nheads), kBlock, 0, s)(f.N, S0, sh, f.heads, nheads, b.sstart, b.shead);
     prof_mark(s, l == 0 ? "lr_prep1" : "lr_prep");
+    int obits = 1;
+    while (((int64_t)1 << obits) < S) ++obits;
+    const int fbits = 32 - obits;
+    if (fbits < 8) b.ol32 = nullptr;  // too many splitters to pack: full records
+    lfbits[l] = fbits;
     RST_LAUNCH(k_lr_walk, (unsigned)((S + kLrWalkThreads - 1) / kLrWalkThreads), kLrWalkThreads, 0, s)(
-        f.N, S0, S, sh, f.nxt, f.w, b.sstart, b.ol, b.snext, b.w_next, l == 0 ? visited : nullptr, status);
+        f.N, S0, S, sh, f.nxt, f.w, b.sstart, b.ol, b.ol32, fbits, b.snext, b.w_next,
+        l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_walk1" : "k_lr_walk");
     RST_CUDA(cudaGetLastError());
     frames[l] = f;
@@ -325,7 +365,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     LevelBufs& b = levels.b[l];
     const int64_t S = ((fr.N + (1LL << sh) - 1) >> sh) + nheads;
 
-    RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.spos, fr.pos,
+    RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.ol32, lfbits[l], b.spos, fr.pos,
                                                          l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_final1" : "k_lr_final");
   }
