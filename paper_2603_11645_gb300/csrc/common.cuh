@@ -204,6 +204,21 @@ __device__ __forceinline__ unsigned long long block_reserve(unsigned long long* 
   return r;
 }
 
+// Streams read or written once, marked evict-first in L2 (createpolicy +
+// .L2::cache_hint), so that they do not push out the arrays the same kernel
+// gathers from or scatters into.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4* p, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
 // ------------------------------------------------------------------ scan
 // Exclusive prefix sums over 64-bit values: out[i] = sum(in[0..i)), and
 // out[count] = total.  `in` may alias `out`.  tmp needs scan_tmp_words(count).

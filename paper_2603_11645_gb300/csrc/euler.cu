@@ -20,9 +20,10 @@ namespace rst {
 
 __global__ void k_parent_from_rank(int64_t T, const uint4* __restrict__ pairs,
                                    const uint32_t* __restrict__ R, int32_t* __restrict__ parent) {
+  const uint64_t once = l2_evict_first();  // the records: read once, keep L2 for R and parent
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 r = pairs[t];  // {i, k, a, b}: i = a->b, k = b->a
+    const uint4 r = ld_stream(&pairs[t], once);  // {i, k, a, b}: i = a->b, k = b->a
     if (r.x == kNone) continue;  // a pruned leaf edge: parent already set
     const uint32_t ri = R[r.x], rk = R[r.y];
     if (ri < rk)
