@@ -173,6 +173,7 @@ __global__ void k_r1_resolve(const OffT* __restrict__ off, const int32_t* __rest
                              const RowRec* __restrict__ rows, uint4* __restrict__ pairs,
                              uint32_t* __restrict__ bits, unsigned long long* counters, uint32_t* status) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const uint64_t once = l2_evict_first();  // J and the records stream; L2 keeps P and the row records
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t u = base + threadIdx.x;
     bool emit = false;
@@ -224,7 +225,7 @@ __global__ void k_r1_resolve(const OffT* __restrict__ off, const int32_t* __rest
             raise_error(status, DERR_INDEX);  // the CSR is not symmetric
           } else {
             emit = true;
-            rec = make_uint4(J[u], (uint32_t)q, (uint32_t)u, (uint32_t)v0);
+            rec = make_uint4(ld_stream(&J[u], once), (uint32_t)q, (uint32_t)u, (uint32_t)v0);
             atomicOr(&bits[rec.x >> 5], 1u << (rec.x & 31));
             atomicOr(&bits[rec.y >> 5], 1u << (rec.y & 31));
           }
@@ -251,7 +252,7 @@ __global__ void k_r1_resolve(const OffT* __restrict__ off, const int32_t* __rest
       }
     }
     const unsigned long long slot = block_reserve<kBlock>(&counters[CNT_PAIRS], emit ? 1u : 0u);
-    if (emit) pairs[slot] = rec;
+    if (emit) st_stream(&pairs[slot], rec, once);
   }
 }
 
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
                                                             unsigned long long* __restrict__ best,
                                                             uint32_t* status) {
   __shared__ __align__(16) int32_t s_row[kArcTile];
+  const uint64_t once = l2_evict_first();  // the columns stream past; L2 keeps C1 and the hook slots
   for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
     const int cnt = (int)(A - a0 < kArcTile ? A - a0 : kArcTile);
     const int64_t t = a0 / kArcTile;
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
       bu[k] = 0;
       bv[k] = 0;
       if (i < cnt) {
-        const int32_t v = col[a0 + i];
+        const int32_t v = ld_stream(&col[a0 + i], once);
         const int32_t u = s_row[i];
         if (v < 0 || (int64_t)v >= n) {
           raise_error(status, DERR_INDEX);

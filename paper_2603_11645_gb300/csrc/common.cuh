@@ -219,6 +219,22 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p, uint64_t pol) {
                : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_stream(uint4* p, uint4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
+  int32_t v;
+  asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 // ------------------------------------------------------------------ scan
 // Exclusive prefix sums over 64-bit values: out[i] = sum(in[0..i)), and
 // out[count] = total.  `in` may alias `out`.  tmp needs scan_tmp_words(count).
