@@ -309,33 +309,45 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
     arc_tile_rows(off, n, a0, cnt, s_row, tile_row[t], tile_row[t + 1]);
     // Survivors are written warp-contiguously per unrolled step (order in
     // the list does not matter), so every store instruction is coalesced.
+    // All label gathers of the tile are issued before the first hook atomic
+    // (the atomics would otherwise order the next arc's gathers behind them).
     int32_t bu[kArcPer], bv[kArcPer];
     uint32_t mask = 0;
 #pragma unroll
     for (int k = 0; k < kArcPer; ++k) {
       const int i = k * kArcThreads + threadIdx.x;
+      bv[k] = i < cnt ? ld_stream(&col[a0 + i], once) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kArcPer; ++k) {
+      const int i = k * kArcThreads + threadIdx.x;
+      const int32_t v = bv[k];
       bu[k] = 0;
       bv[k] = 0;
       if (i < cnt) {
-        const int32_t v = ld_stream(&col[a0 + i], once);
         const int32_t u = s_row[i];
         if (v < 0 || (int64_t)v >= n) {
           raise_error(status, DERR_INDEX);
         } else if (v > u) {
-          const int32_t cu = C1[u];
-          const int32_t cv = C1[v];
-          bu[k] = cu;
-          bv[k] = cv;
-          if (cu != cv) {
-            mask |= 1u << k;
-            // the first contraction round's hook, fused into the scan (a slot
-            // already below the key needs no atomic; slots only decrease)
-            const unsigned long long key = (unsigned long long)(uint32_t)(a0 + i) << 32;
-            const unsigned long long ku = key | (uint32_t)cv, kv = key | (uint32_t)cu;
-            if (__ldcg(&best[cu]) > ku) atomicMin(&best[cu], ku);
-            if (__ldcg(&best[cv]) > kv) atomicMin(&best[cv], kv);
-          }
+          bu[k] = C1[u];
+          bv[k] = C1[v];
+          mask |= 1u << k;
         }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kArcPer; ++k) {
+      const int32_t cu = bu[k], cv = bv[k];
+      if (((mask >> k) & 1u) && cu != cv) {
+        // the first contraction round's hook, fused into the scan (a slot
+        // already below the key needs no atomic; slots only decrease)
+        const int i = k * kArcThreads + threadIdx.x;
+        const unsigned long long key = (unsigned long long)(uint32_t)(a0 + i) << 32;
+        const unsigned long long ku = key | (uint32_t)cv, kv = key | (uint32_t)cu;
+        if (__ldcg(&best[cu]) > ku) atomicMin(&best[cu], ku);
+        if (__ldcg(&best[cv]) > kv) atomicMin(&best[cv], kv);
+      } else {
+        mask &= ~(1u << k);
       }
     }
     const int lane = threadIdx.x & 31;
@@ -388,6 +400,7 @@ __device__ __forceinline__ int64_t next_round_stride(int64_t C, int64_t cap) {
 
 struct CcPtrs {
   const int32_t* col;
+  const RowRec* rec;  // row records (null: the twin is found by binary search)
   int32_t* Ecu[2];
   int32_t* Ecv[2];
   uint32_t* Ep[2];
@@ -428,7 +441,9 @@ __global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__
 // copy of the hook slots (shared memory) and each block then offers one key
 // per touched slot, instead of every entry contending on a few global slots.
 constexpr int kHookLocal = 1024;
-__global__ void k_round_hook(CcPtrs b) {
+constexpr int kHookPer = 4;  // list entries per thread and step
+constexpr int kHookBlocksPerSm = 6;  // resident at the register budget below
+__global__ void __launch_bounds__(kBlock, kHookBlocksPerSm) k_round_hook(CcPtrs b) {
   __shared__ unsigned long long s_best[kHookLocal];
   CcCtl* t = b.ctl;
   const int r = t->cur;
@@ -446,47 +461,93 @@ __global__ void k_round_hook(CcPtrs b) {
   const int32_t* __restrict__ Icu = b.Ecu[src];
   const int32_t* __restrict__ Icv = b.Ecv[src];
   const uint32_t* __restrict__ Ip = b.Ep[src];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride) {
-    const int64_t e = base + threadIdx.x;
-    bool keep = false;
-    int32_t cu = 0, cv = 0;
-    uint32_t p = 0;
-    if (e < E) {
-      cu = Icu[e];
-      cv = Icv[e];
-      p = Ip[e];
-      if (mp) {
-        cu = mp[cu];
-        cv = mp[cv];
-      }
-      keep = cu != cv;
-      if (keep) {
-        // read before the atomic: a value already below the key (possibly
-        // stale, values only decrease) makes the atomic unnecessary, which
-        // removes most of the contention once few components remain
-        const unsigned long long key = (unsigned long long)p << 32;
-        const unsigned long long ku = key | (uint32_t)cv, kv = key | (uint32_t)cu;
-        if (local) {
-          atomicMin(&s_best[cu], ku);
-          atomicMin(&s_best[cv], kv);
-        } else {
-          unsigned long long* su = &best[cu * bs];
-          unsigned long long* sv = &best[cv * bs];
-          if (__ldcg(su) > ku) atomicMin(su, ku);
-          if (__ldcg(sv) > kv) atomicMin(sv, kv);
-        }
+  const int64_t tile = (int64_t)blockDim.x * kHookPer;
+  const int64_t stride = (int64_t)gridDim.x * tile;
+  const uint64_t once = l2_evict_first();  // this round's list is read once
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t base = (int64_t)blockIdx.x * tile; base < E; base += stride) {
+    // A thread takes kHookPer entries; all their reads and component-map
+    // gathers are issued before the first hook atomic, so several chains of
+    // dependent loads are in flight at once.
+    int32_t cu[kHookPer], cv[kHookPer];
+    uint32_t p[kHookPer];
+    uint32_t mask = 0;
+#pragma unroll
+    for (int k = 0; k < kHookPer; ++k) {
+      const int64_t e = base + (int64_t)k * blockDim.x + threadIdx.x;
+      cu[k] = 0;
+      cv[k] = 0;
+      p[k] = 0;
+      if (e < E) {
+        cu[k] = ld_stream(&Icu[e], once);
+        cv[k] = ld_stream(&Icv[e], once);
+        p[k] = ld_stream(&Ip[e], once);
+        mask |= 1u << k;
       }
     }
-    const unsigned long long slot = block_reserve<kBlock>(&t->st[r + 1].E, keep ? 1u : 0u);
-    if (keep) {
-      if ((int64_t)slot < b.ecap) {
-        b.Ecu[dst][slot] = cu;
-        b.Ecv[dst][slot] = cv;
-        b.Ep[dst][slot] = p;
-      } else {
-        raise_error(b.status, DERR_CAPACITY);
+    if (mp) {
+#pragma unroll
+      for (int k = 0; k < kHookPer; ++k)
+        if ((mask >> k) & 1u) {
+          cu[k] = mp[cu[k]];
+          cv[k] = mp[cv[k]];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kHookPer; ++k)
+      if (cu[k] == cv[k]) mask &= ~(1u << k);
+    if (local) {
+#pragma unroll
+      for (int k = 0; k < kHookPer; ++k)
+        if ((mask >> k) & 1u) {
+          const unsigned long long key = (unsigned long long)p[k] << 32;
+          atomicMin(&s_best[cu[k]], key | (uint32_t)cv[k]);
+          atomicMin(&s_best[cv[k]], key | (uint32_t)cu[k]);
+        }
+    } else {
+      // read before the atomic: a value already below the key (possibly
+      // stale, values only decrease) makes the atomic unnecessary, which
+      // removes most of the contention once few components remain
+      unsigned long long ou[kHookPer], ov[kHookPer];
+#pragma unroll
+      for (int k = 0; k < kHookPer; ++k) {
+        ou[k] = 0;
+        ov[k] = 0;
+        if ((mask >> k) & 1u) {
+          ou[k] = __ldcg(&best[cu[k] * bs]);
+          ov[k] = __ldcg(&best[cv[k] * bs]);
+        }
       }
+#pragma unroll
+      for (int k = 0; k < kHookPer; ++k)
+        if ((mask >> k) & 1u) {
+          const unsigned long long key = (unsigned long long)p[k] << 32;
+          const unsigned long long ku = key | (uint32_t)cv[k], kv = key | (uint32_t)cu[k];
+          if (ou[k] > ku) atomicMin(&best[cu[k] * bs], ku);
+          if (ov[k] > kv) atomicMin(&best[cv[k] * bs], kv);
+        }
+    }
+    // survivors: one reservation per warp, written warp-contiguously per step
+    unsigned wtot = 0;
+#pragma unroll
+    for (int k = 0; k < kHookPer; ++k) wtot += __popc(__ballot_sync(0xffffffffu, (mask >> k) & 1u));
+    const unsigned long long mine = block_reserve<kBlock>(&t->st[r + 1].E, lane == 0 ? wtot : 0u);
+    unsigned long long run = __shfl_sync(0xffffffffu, mine, 0);
+#pragma unroll
+    for (int k = 0; k < kHookPer; ++k) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (mask >> k) & 1u);
+      if ((mask >> k) & 1u) {
+        const unsigned long long slot = run + __popc(bal & lt);
+        if ((int64_t)slot < b.ecap) {
+          b.Ecu[dst][slot] = cu[k];
+          b.Ecv[dst][slot] = cv[k];
+          b.Ep[dst][slot] = p[k];
+        } else {
+          raise_error(b.status, DERR_CAPACITY);
+        }
+      }
+      run += __popc(bal);
     }
   }
   if (local) {
@@ -523,49 +584,124 @@ __device__ __forceinline__ bool twin_of_position(const OffT* __restrict__ off,
   return true;
 }
 
+// The same from b's row record when it holds the whole row: the entries below b
+// (a < b: keys name arcs min -> max) are the candidates, and their row starts
+// are read together instead of one binary-search step after another.
+template <class OffT>
+__device__ __forceinline__ bool twin_from_record(const OffT* __restrict__ off, const RowRec& R,
+                                                 int32_t b, uint64_t p, int32_t* a_out, int64_t* q_out) {
+  uint64_t lo[kRecCols], hi[kRecCols];
+#pragma unroll
+  for (int i = 0; i < kRecCols; ++i) {
+    const bool cand = i < (int)R.deg && R.c[i] >= 0 && R.c[i] < b;
+    lo[i] = cand ? (uint64_t)off[R.c[i]] : ~0ull;
+    hi[i] = cand ? (uint64_t)off[R.c[i] + 1] : 0ull;
+  }
+  bool found = false;
+#pragma unroll
+  for (int i = 0; i < kRecCols; ++i)
+    if (lo[i] <= p && p < hi[i]) {
+      found = true;
+      *a_out = R.c[i];
+      *q_out = (int64_t)R.start + i;
+    }
+  return found;
+}
+
 // A component with no incident edge is final; otherwise it hooks onto the
 // component its minimum-key edge reaches, except the smaller id of a mutual
 // pair, which stays a root.  Each hook records its tree edge.
+constexpr int kResolvePer = 2;  // components per thread and step
+constexpr int kResolveBlocksPerSm = 5;
 template <class OffT>
-__global__ void k_round_resolve(CcPtrs b, const OffT* __restrict__ off) {
+__global__ void __launch_bounds__(kBlock, kResolveBlocksPerSm) k_round_resolve(CcPtrs b, const OffT* __restrict__ off) {
   CcCtl* t = b.ctl;
   const int r = t->cur;
   const int64_t C = (int64_t)t->st[r].C;
   const unsigned long long* __restrict__ best = b.best[r & 1];
   const int64_t bs = t->st[r].bs;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < C; base += stride) {
-    const int64_t c = base + threadIdx.x;
-    bool emit = false;
-    uint4 rec = make_uint4(0, 0, 0, 0);
-    if (c < C) {
-      const unsigned long long bc = best[c * bs];
-      if (bc == ~0ull) {
-        b.P2[c] = (int32_t)c;
-      } else {
-        const int32_t c2 = (int32_t)(uint32_t)(bc & 0xffffffffull);
-        const uint32_t p = (uint32_t)(bc >> 32);
-        const int32_t bb = b.col[p];  // issued with the partner's slot read
-        const bool mutual = (uint32_t)(best[(int64_t)c2 * bs] >> 32) == p;
-        if (mutual && (int32_t)c < c2) {
-          b.P2[c] = (int32_t)c;
+  const int64_t tile = (int64_t)blockDim.x * kResolvePer;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t base = (int64_t)blockIdx.x * tile; base < C; base += (int64_t)gridDim.x * tile) {
+    // the slot, arc and partner reads of both components are in flight together
+    unsigned long long bc[kResolvePer];
+    int32_t bb[kResolvePer];
+    uint32_t pk[kResolvePer];
+#pragma unroll
+    for (int j = 0; j < kResolvePer; ++j) {
+      const int64_t c = base + (int64_t)j * blockDim.x + threadIdx.x;
+      bc[j] = c < C ? best[c * bs] : ~0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kResolvePer; ++j) {
+      bb[j] = 0;
+      pk[j] = 0;
+      if (bc[j] != ~0ull) {
+        bb[j] = b.col[(uint32_t)(bc[j] >> 32)];
+        pk[j] = (uint32_t)(best[(int64_t)(uint32_t)(bc[j] & 0xffffffffull) * bs] >> 32);
+      }
+    }
+    uint32_t hook = 0;
+#pragma unroll
+    for (int j = 0; j < kResolvePer; ++j) {
+      const int64_t c = base + (int64_t)j * blockDim.x + threadIdx.x;
+      if (c < C) {
+        const int32_t c2 = (int32_t)(uint32_t)(bc[j] & 0xffffffffull);
+        const uint32_t p = (uint32_t)(bc[j] >> 32);
+        if (bc[j] == ~0ull || (pk[j] == p && (int32_t)c < c2)) {
+          b.P2[c] = (int32_t)c;  // final, or the smaller end of a mutual pair
         } else {
           b.P2[c] = c2;
-          int32_t a = 0;
-          int64_t q = 0;
-          if (twin_of_position(off, b.col, bb, (uint64_t)p, &a, &q)) {
-            emit = true;
-            rec = make_uint4(p, (uint32_t)q, (uint32_t)a, (uint32_t)bb);
-            atomicOr(&b.bits[p >> 5], 1u << (p & 31));
-            atomicOr(&b.bits[rec.y >> 5], 1u << (rec.y & 31));
-          } else {
-            raise_error(b.status, DERR_INDEX);
-          }
+          hook |= 1u << j;
         }
       }
     }
-    const unsigned long long slot = block_reserve<kBlock>(&b.counters[CNT_PAIRS], emit ? 1u : 0u);
-    if (emit) b.pairs[slot] = rec;
+    RowRec R[kResolvePer];
+    if (b.rec) {
+#pragma unroll
+      for (int j = 0; j < kResolvePer; ++j)
+        if ((hook >> j) & 1u) R[j] = b.rec[bb[j]];
+    }
+    uint4 out[kResolvePer];
+    uint32_t emit = 0;
+#pragma unroll
+    for (int j = 0; j < kResolvePer; ++j) {
+      out[j] = make_uint4(0, 0, 0, 0);
+      if ((hook >> j) & 1u) {
+        const uint32_t p = (uint32_t)(bc[j] >> 32);
+        int32_t a = 0;
+        int64_t q = 0;
+        bool found;
+        if (b.rec && R[j].deg <= (uint32_t)kRecCols)
+          found = twin_from_record(off, R[j], bb[j], (uint64_t)p, &a, &q);
+        else
+          found = twin_of_position(off, b.col, bb[j], (uint64_t)p, &a, &q);
+        if (found) {
+          emit |= 1u << j;
+          out[j] = make_uint4(p, (uint32_t)q, (uint32_t)a, (uint32_t)bb[j]);
+        } else {
+          raise_error(b.status, DERR_INDEX);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kResolvePer; ++j)
+      if ((emit >> j) & 1u) {
+        atomicOr(&b.bits[out[j].x >> 5], 1u << (out[j].x & 31));
+        atomicOr(&b.bits[out[j].y >> 5], 1u << (out[j].y & 31));
+      }
+    unsigned wtot = 0;
+#pragma unroll
+    for (int j = 0; j < kResolvePer; ++j) wtot += __popc(__ballot_sync(0xffffffffu, (emit >> j) & 1u));
+    const unsigned long long mine = block_reserve<kBlock>(&b.counters[CNT_PAIRS], lane == 0 ? wtot : 0u);
+    unsigned long long run = __shfl_sync(0xffffffffu, mine, 0);
+#pragma unroll
+    for (int j = 0; j < kResolvePer; ++j) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (emit >> j) & 1u);
+      if ((emit >> j) & 1u) b.pairs[run + __popc(bal & lt)] = out[j];
+      run += __popc(bal);
+    }
   }
 }
 
@@ -721,8 +857,10 @@ template <class OffT>
 static void launch_round_body(const CcPtrs& p, const OffT* off, cudaGraphConditionalHandle h,
                               int use_handle, cudaStream_t s) {
   const int g = device_info().sms * tuning().round_bps;
-  RST_LAUNCH(k_round_hook, g, kBlock, 0, s)(p);
-  RST_LAUNCH(k_round_resolve<OffT>, g, kBlock, 0, s)(p, off);
+  const int gh = device_info().sms * std::min(tuning().round_bps, kHookBlocksPerSm);
+  RST_LAUNCH(k_round_hook, gh, kBlock, 0, s)(p);
+  const int gr = device_info().sms * std::min(tuning().round_bps, kResolveBlocksPerSm);
+  RST_LAUNCH(k_round_resolve<OffT>, gr, kBlock, 0, s)(p, off);
   RST_LAUNCH(k_round_settle, g, kBlock, 0, s)(p);
   RST_LAUNCH(k_round_map, g, kBlock, 0, s)(p, h, use_handle);
 }
@@ -803,6 +941,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   prof_mark(s, "k_r1_label");
   CcPtrs p;
   p.col = col;
+  p.rec = b.rec;
   for (int k = 0; k < 2; ++k) {
     p.Ecu[k] = b.Ecu[k];
     p.Ecv[k] = b.Ecv[k];

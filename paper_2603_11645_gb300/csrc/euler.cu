@@ -18,6 +18,12 @@ namespace rst {
 
 // ----------------------------------------------------------------- core
 
+// Tree records per thread and step in leaf pruning, whose byte gathers are
+// issued together so several dependent chains are in flight (the other record
+// kernels are bound by DRAM sectors and gain nothing from it).
+constexpr int kEuPer = 4;
+constexpr int kEuBlocksPerSm = 6;  // resident blocks at its 40 registers
+
 __global__ void k_parent_from_rank(int64_t T, const uint4* __restrict__ pairs,
                                    const uint32_t* __restrict__ R, int32_t* __restrict__ parent) {
   const uint64_t once = l2_evict_first();  // the records: read once, keep L2 for R and parent
@@ -83,20 +89,35 @@ __global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint32_t* 
 // has its single tree neighbour as parent.  Its edge leaves the tree that is
 // toured (both arcs' bits are cleared) and the pair is marked done.  Removing
 // leaves changes no ancestor relation among the remaining vertices.
-__global__ void k_prune_leaves(int64_t T, uint4* __restrict__ pairs, const uint8_t* __restrict__ leaf,
+__global__ void __launch_bounds__(kBlock, kEuBlocksPerSm) k_prune_leaves(int64_t T, uint4* __restrict__ pairs, const uint8_t* __restrict__ leaf,
                                uint32_t* __restrict__ bits, int32_t* __restrict__ parent) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    uint4 r = pairs[t];
-    const int32_t a = (int32_t)r.z, b = (int32_t)r.w;
-    const bool la = leaf[a], lb = leaf[b];
-    if (!la && !lb) continue;
-    if (lb) parent[b] = a;
-    if (la) parent[a] = b;
-    atomicAnd(&bits[r.x >> 5], ~(1u << (r.x & 31)));
-    atomicAnd(&bits[r.y >> 5], ~(1u << (r.y & 31)));
-    r.x = kNone;
-    pairs[t] = r;
+  const int64_t tile = (int64_t)blockDim.x * kEuPer;
+  for (int64_t base = (int64_t)blockIdx.x * tile; base < T; base += (int64_t)gridDim.x * tile) {
+    uint4 r[kEuPer];
+#pragma unroll
+    for (int j = 0; j < kEuPer; ++j) {
+      const int64_t t = base + (int64_t)j * blockDim.x + threadIdx.x;
+      r[j] = t < T ? pairs[t] : make_uint4(0, 0, 0, 0);
+    }
+    bool la[kEuPer], lb[kEuPer];
+#pragma unroll
+    for (int j = 0; j < kEuPer; ++j) {
+      const int64_t t = base + (int64_t)j * blockDim.x + threadIdx.x;
+      la[j] = t < T && leaf[r[j].z];
+      lb[j] = t < T && leaf[r[j].w];
+    }
+#pragma unroll
+    for (int j = 0; j < kEuPer; ++j) {
+      if (!la[j] && !lb[j]) continue;
+      const int64_t t = base + (int64_t)j * blockDim.x + threadIdx.x;
+      const int32_t a = (int32_t)r[j].z, b = (int32_t)r[j].w;
+      if (lb[j]) parent[b] = a;
+      if (la[j]) parent[a] = b;
+      atomicAnd(&bits[r[j].x >> 5], ~(1u << (r[j].x & 31)));
+      atomicAnd(&bits[r[j].y >> 5], ~(1u << (r[j].y & 31)));
+      r[j].x = kNone;
+      pairs[t] = r[j];
+    }
   }
 }
 
@@ -170,7 +191,7 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   prof_mark(s, "k_toff");
   int64_t N = 2 * T;
   if (prune) {
-    RST_LAUNCH(k_prune_leaves, grid_for(T), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
+    RST_LAUNCH(k_prune_leaves, grid_for((T + kEuPer - 1) / kEuPer, kBlock, kEuBlocksPerSm), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
     prof_mark(s, "k_prune_leaves");
     RST_TRY(scan_popcount_words(cc->bits, wpre, W, tmp, s));
     RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, cc->bits, wpre, is_root, toff, nullptr,
