@@ -167,92 +167,154 @@ __global__ void k_r1_choose(const OffT* __restrict__ off, const int32_t* __restr
 // the tree edge and shortcut u to its root (in place; any value a concurrent
 // reader sees is an ancestor, and a 2-cycle is a mutual pair whose smaller id
 // is the root).
+constexpr int kR1Per = 2;  // vertices per thread and step in round-1 resolve
+constexpr int kR1BlocksPerSm = 5;
 template <class OffT>
-__global__ void k_r1_resolve(const OffT* __restrict__ off, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const OffT* __restrict__ off, const int32_t* __restrict__ col,
                              int64_t n, int32_t* P, const uint32_t* __restrict__ J,
                              const RowRec* __restrict__ rows, uint4* __restrict__ pairs,
                              uint32_t* __restrict__ bits, unsigned long long* counters, uint32_t* status) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const uint64_t once = l2_evict_first();  // J and the records stream; L2 keeps P and the row records
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int64_t u = base + threadIdx.x;
-    bool emit = false;
-    uint4 rec = make_uint4(0, 0, 0, 0);
-    if (u < n) {
-      const int32_t v0 = P[u];  // only this thread writes P[u]
-      if (v0 != (int32_t)u) {
-        // v0's first choice y0 (its first non-self entry), its row start and
-        // u's position q in its row: from v0's record when it holds the
-        // whole row, else from P and the CSR
-        int32_t y0 = -1;
-        int64_t q = -1;
-        bool have_q = false;
-        int64_t lo = 0, end = 0;
-        if (rows) {
-          const RowRec R = rows[v0];
-          lo = (int64_t)R.start;
-          end = lo + (int64_t)R.deg;
+  const int64_t tile = (int64_t)blockDim.x * kR1Per;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+    // Every load of a step is issued for both vertices before either is used:
+    // own pointers, then the chosen neighbours' records, then the chases in
+    // lockstep.  Positions fit 32 bits (fewer than 2^32 arcs).
+    int32_t v0[kR1Per], y[kR1Per];
+    uint32_t act = 0;
 #pragma unroll
-          for (int i = kRecCols - 1; i >= 0; --i)
-            if (i < (int)R.deg && R.c[i] != v0) y0 = R.c[i];
+    for (int j = 0; j < kR1Per; ++j) {
+      const int64_t u = base + (int64_t)j * blockDim.x + threadIdx.x;
+      v0[j] = u < n ? P[u] : (int32_t)u;  // only this thread writes P[u]
+      if (u < n && v0[j] != (int32_t)u) act |= 1u << j;
+    }
+    // v0's first choice y0 (its first non-self entry) and u's position q in
+    // v0's row: from v0's record when it holds the whole row, else from P and
+    // a binary search of the row
+    uint32_t q[kR1Per];
+    uint32_t haveq = 0;
+    if (rows) {
+      RowRec R[kR1Per];
 #pragma unroll
-          for (int i = kRecCols - 1; i >= 0; --i)
-            if (i < (int)R.deg && R.c[i] == (int32_t)u) q = lo + i;
-          have_q = R.deg <= (uint32_t)kRecCols;
-          if (y0 < 0 || (int64_t)y0 >= n) y0 = P[v0];  // long row of self-loops, or a bad id
-        } else {
-          y0 = P[v0];
-          lo = (int64_t)off[v0];
-          end = (int64_t)off[v0 + 1];
+      for (int j = 0; j < kR1Per; ++j)
+        if ((act >> j) & 1u) R[j] = rows[v0[j]];
+#pragma unroll
+      for (int j = 0; j < kR1Per; ++j) {
+        y[j] = -1;
+        q[j] = kNone;
+        if (!((act >> j) & 1u)) continue;
+        const int32_t u = (int32_t)(base + (int64_t)j * blockDim.x + threadIdx.x);
+#pragma unroll
+        for (int i = kRecCols - 1; i >= 0; --i)
+          if (i < (int)R[j].deg && R[j].c[i] != v0[j]) y[j] = R[j].c[i];
+#pragma unroll
+        for (int i = kRecCols - 1; i >= 0; --i)
+          if (i < (int)R[j].deg && R[j].c[i] == u) q[j] = R[j].start + (uint32_t)i;
+        if (R[j].deg <= (uint32_t)kRecCols) haveq |= 1u << j;
+      }
+#pragma unroll
+      for (int j = 0; j < kR1Per; ++j)  // long row of self-loops, or a bad id
+        if (((act >> j) & 1u) && (y[j] < 0 || (int64_t)y[j] >= n)) y[j] = P[v0[j]];
+    } else {
+#pragma unroll
+      for (int j = 0; j < kR1Per; ++j) {
+        y[j] = -1;
+        q[j] = kNone;
+        if ((act >> j) & 1u) y[j] = P[v0[j]];
+      }
+    }
+    uint32_t emit = 0, chase = 0;
+    int32_t x[kR1Per], root[kR1Per];
+#pragma unroll
+    for (int j = 0; j < kR1Per; ++j) {
+      x[j] = 0;
+      root[j] = -1;
+      if (!((act >> j) & 1u)) continue;
+      const int64_t u = base + (int64_t)j * blockDim.x + threadIdx.x;
+      const bool mutual = (y[j] == (int32_t)u);
+      if (mutual && (int32_t)u < v0[j]) {
+        root[j] = (int32_t)u;  // the smaller end of a mutual pair
+        continue;
+      }
+      if (!((haveq >> j) & 1u)) {
+        const int64_t lo = (int64_t)off[v0[j]], end = (int64_t)off[v0[j] + 1];
+        int64_t L = lo, H = end;
+        while (L < H) {
+          const int64_t mid = (L + H) >> 1;
+          if (col[mid] < (int32_t)u)
+            L = mid + 1;
+          else
+            H = mid;
         }
-        const bool mutual = (y0 == (int32_t)u);
-        const bool is_root = mutual && (int32_t)u < v0;
-        if (is_root) {
-          P[u] = (int32_t)u;
+        q[j] = (L < end && col[L] == (int32_t)u) ? (uint32_t)L : kNone;
+      }
+      if (q[j] == kNone)
+        raise_error(status, DERR_INDEX);  // the CSR is not symmetric
+      else
+        emit |= 1u << j;
+      // chase to the root: x -> y = P[x] -> z = P[y]; the first y is y0
+      if (mutual) {
+        root[j] = v0[j];  // the pair's smaller end (u > v0 here)
+      } else {
+        x[j] = v0[j];
+        chase |= 1u << j;
+      }
+    }
+    for (int64_t it = 0; chase && it <= n; ++it) {
+      int32_t z[kR1Per];
+#pragma unroll
+      for (int j = 0; j < kR1Per; ++j) {
+        z[j] = 0;
+        if ((chase >> j) & 1u) {
+          if (y[j] == x[j]) {
+            root[j] = x[j];
+            chase &= ~(1u << j);
+          } else {
+            z[j] = P[y[j]];
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kR1Per; ++j) {
+        if (!((chase >> j) & 1u)) continue;
+        if (z[j] == x[j]) {
+          root[j] = x[j] < y[j] ? x[j] : y[j];
+          chase &= ~(1u << j);
         } else {
-          if (!have_q) {
-            int64_t L = lo, H = end;
-            while (L < H) {
-              const int64_t mid = (L + H) >> 1;
-              if (col[mid] < (int32_t)u)
-                L = mid + 1;
-              else
-                H = mid;
-            }
-            q = (L < end && col[L] == (int32_t)u) ? L : -1;
-          }
-          if (q < 0) {
-            raise_error(status, DERR_INDEX);  // the CSR is not symmetric
-          } else {
-            emit = true;
-            rec = make_uint4(ld_stream(&J[u], once), (uint32_t)q, (uint32_t)u, (uint32_t)v0);
-            atomicOr(&bits[rec.x >> 5], 1u << (rec.x & 31));
-            atomicOr(&bits[rec.y >> 5], 1u << (rec.y & 31));
-          }
-          // chase to the root: x -> y = P[x] -> z = P[y]; the first y is y0
-          int32_t r = -1;
-          if (mutual) {
-            r = v0;  // the pair's smaller end (u > v0 here)
-          } else {
-            int32_t x = v0, y = y0;
-            for (int64_t it = 0; it <= n; ++it) {
-              if (y == x) { r = x; break; }
-              const int32_t z = P[y];
-              if (z == x) { r = x < y ? x : y; break; }
-              x = y;
-              y = z;
-            }
-          }
-          if (r < 0) {
-            raise_error(status, DERR_ROUND_LIMIT);
-            r = (int32_t)u;
-          }
-          P[u] = r;
+          x[j] = y[j];
+          y[j] = z[j];
         }
       }
     }
-    const unsigned long long slot = block_reserve<kBlock>(&counters[CNT_PAIRS], emit ? 1u : 0u);
-    if (emit) st_stream(&pairs[slot], rec, once);
+#pragma unroll
+    for (int j = 0; j < kR1Per; ++j) {
+      if (!((act >> j) & 1u)) continue;
+      const int64_t u = base + (int64_t)j * blockDim.x + threadIdx.x;
+      if (root[j] < 0) {
+        raise_error(status, DERR_ROUND_LIMIT);
+        root[j] = (int32_t)u;
+      }
+      P[u] = root[j];
+    }
+    unsigned wtot = 0;
+#pragma unroll
+    for (int j = 0; j < kR1Per; ++j) wtot += __popc(__ballot_sync(0xffffffffu, (emit >> j) & 1u));
+    const unsigned long long mine = block_reserve<kBlock>(&counters[CNT_PAIRS], lane == 0 ? wtot : 0u);
+    unsigned long long run = __shfl_sync(0xffffffffu, mine, 0);
+#pragma unroll
+    for (int j = 0; j < kR1Per; ++j) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (emit >> j) & 1u);
+      if ((emit >> j) & 1u) {
+        const int64_t u = base + (int64_t)j * blockDim.x + threadIdx.x;
+        const uint4 rec = make_uint4(ld_stream(&J[u], once), q[j], (uint32_t)u, (uint32_t)v0[j]);
+        atomicOr(&bits[rec.x >> 5], 1u << (rec.x & 31));
+        atomicOr(&bits[rec.y >> 5], 1u << (rec.y & 31));
+        st_stream(&pairs[run + __popc(bal & lt)], rec, once);
+      }
+      run += __popc(bal);
+    }
   }
 }
 
@@ -339,13 +401,14 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
     for (int k = 0; k < kArcPer; ++k) {
       const int32_t cu = bu[k], cv = bv[k];
       if (((mask >> k) & 1u) && cu != cv) {
-        // the first contraction round's hook, fused into the scan (a slot
-        // already below the key needs no atomic; slots only decrease)
+        // the first contraction round's hook, fused into the scan.  With
+        // millions of slots contention is low, and reading a slot before its
+        // atomic (as later rounds do) would only add a round trip here.
         const int i = k * kArcThreads + threadIdx.x;
         const unsigned long long key = (unsigned long long)(uint32_t)(a0 + i) << 32;
         const unsigned long long ku = key | (uint32_t)cv, kv = key | (uint32_t)cu;
-        if (__ldcg(&best[cu]) > ku) atomicMin(&best[cu], ku);
-        if (__ldcg(&best[cv]) > kv) atomicMin(&best[cv], kv);
+        atomicMin(&best[cu], ku);
+        atomicMin(&best[cv], kv);
       } else {
         mask &= ~(1u << k);
       }
@@ -933,7 +996,8 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   prof_mark(s, "cc_setup");
   RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, status);
   prof_mark(s, "k_r1_choose");
-  RST_LAUNCH(k_r1_resolve<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, cnt, status);
+  RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
+      off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, cnt, status);
   prof_mark(s, "k_r1_resolve");
   RST_LAUNCH(k_r1_number, gN, kBlock, 0, s)(n, b.P, b.J, b.CID, b.minvpool, cnt);
   prof_mark(s, "k_r1_number");
@@ -1040,7 +1104,8 @@ rst_status round1_forest(const OffT* off, const int32_t* col, int64_t n, int32_t
   uint32_t* status = state().status;
   const int gN = grid_for(n);
   RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, nullptr, status);
-  RST_LAUNCH(k_r1_resolve<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, nullptr, pairs, bits, counters, status);
+  RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
+      off, col, n, P, J, nullptr, pairs, bits, counters, status);
   RST_CUDA(cudaGetLastError());
   return RST_OK;
 }
