@@ -117,8 +117,9 @@ def kernel_bytes(name, n, A, st, o):
         # neighbour's row record (start, degree and its row's entries, at most
         # six) and a 16-byte tree-edge record
         "k_r1_resolve": 16 * n + (n - c1) * (8 + 4 * min(A / max(n, 1), 6) + 16) + 4 * n,
-        "k_r1_number": 8 * n + 8 * c1,
-        "k_r1_label": 16 * n,
+        # J and P per vertex, its label written, the root bitmap and prefix
+        # read once, the minimum vertex of every round-1 component written
+        "k_r1_label": 12 * n + n // 4 + 4 * c1,
         "k_build_list": (n + 1) * o + 4 * A + 4 * n + 2 * A + 12 * E2,
         "k_toff": (n + 1) * (o + 8 + 4) + 2 * n,
         "k_prune_leaves": 16 * T + 2 * T + 4 * (T - K),

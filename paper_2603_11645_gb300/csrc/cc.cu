@@ -64,7 +64,9 @@ struct CcBuffers {
   RowRec* rec;       // per-vertex row records (may be null)
   int32_t* P;        // n: round-1 hook target, then root
   uint32_t* J;       // n: CSR position of the arc to the first neighbour (kNone: isolated)
-  int32_t* CID;      // n: dense component id of round-1 roots
+  uint32_t* rbits;   // n/32 + 2 words: round-1 roots that have edges
+  uint32_t* rpre;    // n/32 + 1: exclusive popcount prefix of rbits (dense root ids)
+  unsigned long long* rtmp;  // scan scratch
   int32_t* C1;       // n: round-1 component of each vertex (-1: isolated)
   int32_t* Ecu[2];   // list entries (ping-pong)
   int32_t* Ecv[2];
@@ -91,7 +93,9 @@ static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
   b.rec = state_overridden() ? nullptr : ar.take<RowRec>(n + 1);
   b.P = ar.take<int32_t>(n + 1);
   b.J = ar.take<uint32_t>(n + 1);
-  b.CID = ar.take<int32_t>(n + 1);
+  b.rbits = ar.take<uint32_t>(n / 32 + 2);
+  b.rpre = ar.take<uint32_t>(n / 32 + 2);
+  b.rtmp = ar.take<unsigned long long>(scan_tmp_words(n / 32 + 1));
   b.C1 = ar.take<int32_t>(n + 1);
   b.ecap = A / 2 + 1;
   for (int k = 0; k < 2; ++k) {
@@ -173,7 +177,8 @@ template <class OffT>
 __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const OffT* __restrict__ off, const int32_t* __restrict__ col,
                              int64_t n, int32_t* P, const uint32_t* __restrict__ J,
                              const RowRec* __restrict__ rows, uint4* __restrict__ pairs,
-                             uint32_t* __restrict__ bits, unsigned long long* counters, uint32_t* status) {
+                             uint32_t* __restrict__ bits, uint32_t* __restrict__ rbits,
+                             unsigned long long* counters, uint32_t* status) {
   const uint64_t once = l2_evict_first();  // J and the records stream; L2 keeps P and the row records
   const int64_t tile = (int64_t)blockDim.x * kR1Per;
   const int lane = threadIdx.x & 31;
@@ -235,7 +240,8 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
       const int64_t u = base + (int64_t)j * blockDim.x + threadIdx.x;
       const bool mutual = (y[j] == (int32_t)u);
       if (mutual && (int32_t)u < v0[j]) {
-        root[j] = (int32_t)u;  // the smaller end of a mutual pair
+        root[j] = (int32_t)u;  // the smaller end of a mutual pair: a root with edges
+        if (rbits) atomicOr(&rbits[u >> 5], 1u << (u & 31));
         continue;
       }
       if (!((haveq >> j) & 1u)) {
@@ -295,6 +301,7 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
       if (root[j] < 0) {
         raise_error(status, DERR_ROUND_LIMIT);
         root[j] = (int32_t)u;
+        if (rbits) atomicOr(&rbits[u >> 5], 1u << (u & 31));
       }
       P[u] = root[j];
     }
@@ -318,30 +325,25 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
   }
 }
 
-// Dense ids for round-1 roots that have edges.  The root of a round-1
+// Round-1 labels: the dense id of a root with edges is its rank among those
+// roots (a popcount prefix over their bitmap, so ids follow vertex order), and
+// every non-isolated vertex takes the id of its root.  The root of a round-1
 // component is its minimum vertex (the minimum vertex w hooks to its first
 // neighbour x, whose first neighbour is w), so minv starts as the root id.
-__global__ void k_r1_number(int64_t n, const int32_t* __restrict__ P,
-                            const uint32_t* __restrict__ J, int32_t* __restrict__ CID,
-                            int32_t* __restrict__ minv, unsigned long long* counters) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int64_t v = base + threadIdx.x;
-    bool is_root = false;
-    if (v < n) is_root = (P[v] == (int32_t)v) && (J[v] != kNone);
-    const unsigned long long id = block_reserve<kBlock>(&counters[CNT_COMPS], is_root ? 1u : 0u);
-    if (is_root) {
-      CID[v] = (int32_t)id;
-      minv[id] = (int32_t)v;
-    }
-  }
-}
-
 __global__ void k_r1_label(int64_t n, const int32_t* __restrict__ P, const uint32_t* __restrict__ J,
-                           const int32_t* __restrict__ CID, int32_t* __restrict__ C1) {
+                           const uint32_t* __restrict__ rbits, const uint32_t* __restrict__ rpre,
+                           int32_t* __restrict__ C1, int32_t* __restrict__ minv,
+                           unsigned long long* counters) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_COMPS] = rpre[n / 32 + 1];
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
-    C1[v] = (J[v] == kNone) ? -1 : CID[P[v]];
+    int32_t c = -1;
+    if (J[v] != kNone) {
+      const int32_t r = P[v];
+      c = (int32_t)bit_rank(rbits, rpre, (uint64_t)r);
+      if (r == (int32_t)v) minv[c] = (int32_t)v;
+    }
+    C1[v] = c;
   }
 }
 
@@ -991,17 +993,18 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   RST_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
   RST_CUDA(cudaMemsetAsync(b.bits, 0, (A / 32 + 2) * sizeof(uint32_t), s));
   RST_CUDA(cudaMemsetAsync(b.ctl, 0, sizeof(CcCtl), s));
+  RST_CUDA(cudaMemsetAsync(b.rbits, 0, (n / 32 + 2) * sizeof(uint32_t), s));
 
   const int gN = grid_for(n);
   prof_mark(s, "cc_setup");
   RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, status);
   prof_mark(s, "k_r1_choose");
   RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
-      off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, cnt, status);
+      off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, b.rbits, cnt, status);
   prof_mark(s, "k_r1_resolve");
-  RST_LAUNCH(k_r1_number, gN, kBlock, 0, s)(n, b.P, b.J, b.CID, b.minvpool, cnt);
-  prof_mark(s, "k_r1_number");
-  RST_LAUNCH(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.CID, b.C1);
+  RST_TRY(scan_popcount_words(b.rbits, b.rpre, n / 32 + 1, b.rtmp, s));
+  prof_mark(s, "r1_rootscan");
+  RST_LAUNCH(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rbits, b.rpre, b.C1, b.minvpool, cnt);
   prof_mark(s, "k_r1_label");
   CcPtrs p;
   p.col = col;
@@ -1105,7 +1108,7 @@ rst_status round1_forest(const OffT* off, const int32_t* col, int64_t n, int32_t
   const int gN = grid_for(n);
   RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, nullptr, status);
   RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
-      off, col, n, P, J, nullptr, pairs, bits, counters, status);
+      off, col, n, P, J, nullptr, pairs, bits, nullptr, counters, status);
   RST_CUDA(cudaGetLastError());
   return RST_OK;
 }
