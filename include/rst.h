@@ -294,8 +294,9 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *   the launch-granularity choice Section III-C makes for PR-RST (several
  *   pointer jumps per global synchronisation, chosen empirically); the
  *   package's autotune module searches them offline per size bucket:
- *     "lr_spacing"            list-ranking splitter spacing K, a power of two
- *                             in [16, 512] (default 16);
+ *     "lr_spacing"            list-ranking splitter spacing K of the first
+ *                             level, a power of two in [16, 512] (default 16;
+ *                             the deeper, L2-resident levels use 8);
  *     "round_blocks_per_sm"   grid of the contraction-round kernels, in resident
  *                             256-thread blocks per SM, [1, 16] (default 8);
  *     "bfs_bottom_up_divisor" BFS steps bottom-up while the frontier holds more

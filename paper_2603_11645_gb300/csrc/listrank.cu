@@ -2,8 +2,8 @@
 // tree's Euler tour, each tree ranked independently).
 //
 // Sparse ruling set with recursion.  Every K-th element by index (K = 2^sh,
-// 16 unless rst_set_option("lr_spacing") changes it) and every list head is a
-// splitter; one thread per splitter walks its sublist up to the
+// 16 unless rst_set_option("lr_spacing") changes it; 8 on the deeper levels)
+// and every list head is a splitter; one thread per splitter walks its sublist up to the
 // next splitter, reading the successor array (read-only) and writing one
 // 8-byte {owner splitter, offset} record per element to a separate array.
 // (Overwriting the successor record in place is several times slower on
@@ -32,6 +32,12 @@ constexpr int kLrWalkThreads = 128;
 
 constexpr int kLrMaxLevels = 24;  // N < 2^32 shrinks by ~K per level
 
+// Levels after the first use a closer spacing: their lists are short and
+// L2-resident, so a level's time is its longest sublist (about K ln S steps
+// of dependent L2 reads), not its bytes.
+constexpr int kLrDeepShift = 3;
+static int level_shift(int level, int sh) { return level == 0 || sh < kLrDeepShift ? sh : kLrDeepShift; }
+
 struct LevelBufs {
   int2* ol;         // N {owner, offset} records of this level
   uint32_t* ol32;   // level 0: the same packed into 32 bits (null: unpacked)
@@ -58,8 +64,8 @@ struct LevelList {
 static void lr_layout(Arena& ar, int64_t N, int64_t h, int sh, LevelList* levels,
                       int32_t** wyl_pj, uint32_t** wyl_val, int32_t** wyl_flag) {
   bool first = true;
-  while (N > kLrBase && h <= N / 4) {
-    const int64_t S = lr_splitters(N, h, sh);
+  for (int l = 0; N > kLrBase && h <= N / 4; ++l) {
+    const int64_t S = lr_splitters(N, h, level_shift(l, sh));
     LevelBufs b;
     b.ol = ar.take<int2>(N);
     b.ol32 = first ? ar.take<uint32_t>(N) : nullptr;
@@ -316,10 +322,11 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   Frame f{N, nxt, w, heads, pos};
   for (int l = 0; l < levels.count; ++l) {
     LevelBufs& b = levels.b[l];
-    const int64_t S0 = (f.N + (1LL << sh) - 1) >> sh;
+    const int shl = level_shift(l, sh);
+    const int64_t S0 = (f.N + (1LL << shl) - 1) >> shl;
     const int64_t S = S0 + nheads;
     if (l == 0) RST_CUDA(cudaMemsetAsync(visited, 0, sizeof(unsigned long long), s));
-    RST_LAUNCH(k_lr_heads, grid_for(nheads), kBlock, 0, s)(f.N, S0, sh, f.heads, nheads, b.sstart, b.shead);
+    RST_LAUNCH(k_lr_heads, grid_for(nheads), kBlock, 0, s)(f.N, S0, shl, f.heads, nheads, b.sstart, b.shead);
     prof_mark(s, l == 0 ? "lr_prep1" : "lr_prep");
     int obits = 1;
     while (((int64_t)1 << obits) < S) ++obits;
@@ -327,7 +334,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     if (fbits < 8) b.ol32 = nullptr;  // too many splitters to pack: full records
     lfbits[l] = fbits;
     RST_LAUNCH(k_lr_walk, (unsigned)((S + kLrWalkThreads - 1) / kLrWalkThreads), kLrWalkThreads, 0, s)(
-        f.N, S0, S, sh, f.nxt, f.w, b.sstart, b.ol, b.ol32, fbits, b.snext, b.w_next,
+        f.N, S0, S, shl, f.nxt, f.w, b.sstart, b.ol, b.ol32, fbits, b.snext, b.w_next,
         l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_walk1" : "k_lr_walk");
     RST_CUDA(cudaGetLastError());
@@ -363,7 +370,8 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   for (int l = levels.count - 1; l >= 0; --l) {
     const Frame& fr = frames[l];
     LevelBufs& b = levels.b[l];
-    const int64_t S = ((fr.N + (1LL << sh) - 1) >> sh) + nheads;
+    const int shl = level_shift(l, sh);
+    const int64_t S = ((fr.N + (1LL << shl) - 1) >> shl) + nheads;
 
     RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.ol32, lfbits[l], b.spos, fr.pos,
                                                          l == 0 ? visited : nullptr, status);
