@@ -298,7 +298,9 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *                             level, a power of two in [16, 512] (default 16;
  *                             the deeper, L2-resident levels use 8);
  *     "round_blocks_per_sm"   grid of the contraction-round kernels, in resident
- *                             256-thread blocks per SM, [1, 16] (default 8);
+ *                             256-thread blocks per SM, [1, 16] (default 8;
+ *                             the hook and resolve kernels take at most 6 and
+ *                             5, the blocks their registers let reside);
  *     "bfs_bottom_up_divisor" BFS steps bottom-up while the frontier holds more
  *                             than n / divisor vertices, [1, 10^6] (default 20).
  *   Out-of-range values and unknown keys return RST_ERR_INVALID_ARG and change

@@ -3,9 +3,10 @@
 The knobs (include/rst.h, rst_set_option) change how the work is split into
 launches and samples, never a result:
 
-* ``lr_spacing``: list-ranking splitter spacing K (one splitter per K tour
-  arcs; sample rate 1/K);
-* ``round_blocks_per_sm``: grid of the contraction-round kernels;
+* ``lr_spacing``: list-ranking splitter spacing K of the first level (one
+  splitter per K tour arcs; sample rate 1/K; the deeper levels use 8);
+* ``round_blocks_per_sm``: grid of the contraction-round kernels (the hook
+  and resolve kernels cap it at the blocks their registers let reside);
 * ``bfs_bottom_up_divisor``: BFS steps bottom-up while the frontier holds more
   than n / divisor vertices.
 

@@ -1,0 +1,88 @@
+"""GPU parity on multigraphs: duplicate edges, self-loops, rows of only
+self-loops and hub rows longer than a row record (more than six entries).
+
+The input contract tolerates all of these and none may become a tree edge;
+the round-1 row records, the record-based twin lookup and its binary-search
+fallback all meet them here.  Every strategy is compared with the CPU oracle
+bit for bit where the result is unique (CC+Euler, BFS, PR-RST, labels and the
+tree edge set) and checked for validity where races pick the tree (cc_fast).
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def multigraph_csr(n, u, v):
+    """Symmetric CSR with sorted rows; a self-loop (x, x) puts x twice in row x."""
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    src = np.concatenate([u, v])
+    dst = np.concatenate([v, u])
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    off = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(off, src + 1, 1)
+    off = np.cumsum(off).astype(np.int32)
+    return off, np.ascontiguousarray(dst.astype(np.int32))
+
+
+def make_case(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(2, 6000))
+    m = int(rng.integers(0, 4 * n))
+    pool = max(1, m // 2)
+    pu = rng.integers(0, n, size=pool)
+    pv = rng.integers(0, n, size=pool)
+    pick = rng.integers(0, pool, size=m)          # sampling with replacement: duplicates
+    u, v = pu[pick], pv[pick]
+    loops = rng.random(m) < 0.05                  # self-loops
+    v = np.where(loops, u, v)
+    hubs = rng.integers(0, n, size=3)             # hub rows longer than a record
+    hu = np.repeat(hubs, 12)
+    hv = rng.integers(0, n, size=hu.size)
+    u = np.concatenate([u, hu, hu[:6]])           # and some duplicated hub edges
+    v = np.concatenate([v, hv, hv[:6]])
+    if n > 3:                                     # a vertex with only self-loops, then one edge
+        u = np.concatenate([u, [1] * 8, [1]])
+        v = np.concatenate([v, [1] * 8, [2]])
+    root = int(rng.integers(0, n))
+    off, col = multigraph_csr(n, u, v)
+    return n, off, col, root
+
+
+CASES = list(range(10))
+
+
+@pytest.mark.parametrize("seed", CASES)
+def test_multigraph_all_strategies(seed):
+    import paper_2603_11645_gb300 as rst
+    n, off_h, col_h, root = make_case(seed)
+    d = torch.device("cuda:0")
+    off = torch.from_numpy(off_h).to(d)
+    col = torch.from_numpy(col_h).to(d)
+
+    par = rst.build(off, col, root, "cc_euler")
+    assert np.array_equal(par.cpu().numpy(), oracle.rst(n, off_h, col_h, root))
+
+    labels, uv, T = rst.cc(off, col)
+    lab, tu, tv = oracle.cc_kruskal(n, off_h, col_h)
+    assert np.array_equal(labels.cpu().numpy(), lab)
+    assert T == len(tu)
+    got = uv.cpu().numpy()[:T]
+    got = got[np.lexsort((got[:, 1], got[:, 0]))]
+    assert np.array_equal(got[:, 0], tu) and np.array_equal(got[:, 1], tv)
+    assert not np.any(got[:, 0] == got[:, 1])     # no self-loop became a tree edge
+
+    lev, want_bfs = oracle.bfs(n, off_h, col_h, root)
+    assert np.array_equal(rst.build(off, col, root, "bfs").cpu().numpy(), want_bfs)
+
+    want_pr, _ = oracle.prrst(n, off_h, col_h, root)
+    assert np.array_equal(rst.build(off, col, root, "pr_rst").cpu().numpy(), want_pr)
+
+    fast = rst.build(off, col, root, "cc_fast")
+    assert rst.verify(off, col, root, fast) == 0
+    assert oracle.verify(n, off_h, col_h, root, fast.cpu().numpy()) == 0
