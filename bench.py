@@ -129,6 +129,9 @@ def kernel_bytes(name, n, A, st, o):
         "k_lr_walk1": 8 * N + 12 * ((N + 15) // 16),
         "k_lr_final1": 4 * N + 4 * N + 4 * ((N + 15) // 16),
         "k_parent_from_rank": 16 * T + K * (8 + 4),
+        # the same reading two packed first-level records and two splitter
+        # positions per toured edge instead of two positions
+        "k_parent_from_owner": 16 * T + K * (8 + 8 + 4),
     }
     return models.get(name)
 

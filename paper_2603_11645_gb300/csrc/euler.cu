@@ -39,6 +39,30 @@ __global__ void k_parent_from_rank(int64_t T, const uint4* __restrict__ pairs,
   }
 }
 
+// The same with positions read from the first list-ranking level's records
+// (the final pass over all elements left out); it also reports a walk that did
+// not reach every element (the input was not a forest).
+__global__ void k_parent_from_owner(int64_t T, const uint4* __restrict__ pairs, const int2* __restrict__ ol,
+                                    const uint32_t* __restrict__ ol32, int fbits,
+                                    const uint32_t* __restrict__ spos, int64_t S,
+                                    const unsigned long long* visited, int64_t N,
+                                    int32_t* __restrict__ parent, uint32_t* status) {
+  if (visited && blockIdx.x == 0 && threadIdx.x == 0 && *visited != (unsigned long long)N)
+    raise_error(status, DERR_NOT_FOREST);
+  const uint64_t once = l2_evict_first();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = ld_stream(&pairs[t], once);  // {i, k, a, b}: i = a->b, k = b->a
+    if (r.x == kNone) continue;
+    const uint32_t ri = lr_position(ol, ol32, fbits, spos, S, r.x);
+    const uint32_t rk = lr_position(ol, ol32, fbits, spos, S, r.y);
+    if (ri < rk)
+      parent[r.w] = (int32_t)r.z;
+    else
+      parent[r.z] = (int32_t)r.w;
+  }
+}
+
 static size_t euler_core_bytes(int64_t T) {
   const int64_t N = 2 * T;
   return ((size_t)N * 8 + 255) / 256 * 256 + 256 + ((size_t)N * 4 + 255) / 256 * 256 + 256 +
@@ -218,9 +242,18 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   prof_mark(s, "k_pairs_succ");
   RST_CUDA(cudaGetLastError());
   if (succ_view) *succ_view = succ;  // stays valid while the arena is not reset
-  RST_TRY(list_rank(ar, N, succ, nullptr, heads, cc->nroots, R, s));
-  RST_LAUNCH(k_parent_from_rank, gT, kBlock, 0, s)(T, cc->pairs, R, parent_out);
-  prof_mark(s, "k_parent_from_rank");
+  // Without requested ranks the parents read their positions straight from the
+  // first ranking level's records (no pass writing every position).
+  LrFirstLevel lv;
+  RST_TRY(list_rank(ar, N, succ, nullptr, heads, cc->nroots, R, s, rank_out ? nullptr : &lv));
+  if (lv.valid) {
+    RST_LAUNCH(k_parent_from_owner, gT, kBlock, 0, s)(T, cc->pairs, lv.ol, lv.ol32, lv.fbits, lv.spos, lv.S,
+                                                      lv.visited, lv.N, parent_out, state().status);
+    prof_mark(s, "k_parent_from_owner");
+  } else {
+    RST_LAUNCH(k_parent_from_rank, gT, kBlock, 0, s)(T, cc->pairs, R, parent_out);
+    prof_mark(s, "k_parent_from_rank");
+  }
   RST_CUDA(cudaGetLastError());
   return RST_OK;
 }

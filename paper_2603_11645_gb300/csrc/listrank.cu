@@ -206,16 +206,8 @@ __global__ void k_lr_final(int64_t N, int64_t S, const int2* __restrict__ ol,
   if (visited && blockIdx.x == 0 && threadIdx.x == 0 && *visited != (unsigned long long)N)
     raise_error(status, DERR_NOT_FOREST);
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    int2 r;
-    if (ol32) {
-      const uint32_t v = ol32[x];
-      r = v != 0xffffffffu ? make_int2((int32_t)(v >> fbits), (int32_t)(v & ((1u << fbits) - 1u))) : ol[x];
-    } else {
-      r = ol[x];
-    }
-    pos[x] = (r.x >= 0 && (int64_t)r.x < S) ? spos[r.x] + (uint32_t)r.y : kNone;
-  }
+       x += (int64_t)gridDim.x * blockDim.x)
+    pos[x] = lr_position(ol, ol32, fbits, spos, S, (uint32_t)x);
 }
 
 // Base case in one block: predecessor pointers, then Wyllie pointer jumping
@@ -294,7 +286,8 @@ __global__ void k_wyl_round(int64_t N, const int32_t* __restrict__ pj, const uin
 }
 
 rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w, const int32_t* heads,
-                     int64_t nheads, uint32_t* pos, cudaStream_t s) {
+                     int64_t nheads, uint32_t* pos, cudaStream_t s, LrFirstLevel* first) {
+  if (first) first->valid = false;
   if (N <= 0) return RST_OK;
   LevelList levels;
   int32_t* wpj = nullptr;
@@ -372,6 +365,17 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     LevelBufs& b = levels.b[l];
     const int shl = level_shift(l, sh);
     const int64_t S = ((fr.N + (1LL << shl) - 1) >> shl) + nheads;
+    if (l == 0 && first) {  // the caller reads positions from the records
+      first->valid = true;
+      first->ol = b.ol;
+      first->ol32 = b.ol32;
+      first->fbits = lfbits[0];
+      first->spos = b.spos;
+      first->S = S;
+      first->visited = visited;
+      first->N = fr.N;
+      break;
+    }
 
     RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.ol32, lfbits[l], b.spos, fr.pos,
                                                          l == 0 ? visited : nullptr, status);

@@ -87,8 +87,37 @@ size_t euler_edges_workspace_bytes(int64_t n, int64_t T);
 // ----------------------------------------------------------------- list ranking
 // pos[x] = sum of weights of the elements before x in its list (weights 1 when
 // w == nullptr).  nxt[x] = successor or -1.  heads: one entry per list.
+//
+// With `first` set, the first level's final pass may be left out: its records
+// are then described in *first (valid = true) and pos is NOT written; the
+// caller derives any element's position with lr_position().
+struct LrFirstLevel {
+  bool valid = false;
+  const int2* ol = nullptr;        // {owner splitter, offset} (overflow and unpacked records)
+  const uint32_t* ol32 = nullptr;  // packed records (owner << fbits | offset), or null
+  int fbits = 0;
+  const uint32_t* spos = nullptr;  // positions of the splitters
+  int64_t S = 0;                   // number of splitters
+  const unsigned long long* visited = nullptr;  // elements the walks reached (must be N)
+  int64_t N = 0;
+};
 rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w,
-                     const int32_t* heads, int64_t nheads, uint32_t* pos, cudaStream_t s);
+                     const int32_t* heads, int64_t nheads, uint32_t* pos, cudaStream_t s,
+                     LrFirstLevel* first = nullptr);
+// Position of element x from first-level records (kNone for an element no walk
+// reached, whose record holds stale data: its owner is bounds-checked).
+__device__ __forceinline__ uint32_t lr_position(const int2* __restrict__ ol, const uint32_t* __restrict__ ol32,
+                                                int fbits, const uint32_t* __restrict__ spos, int64_t S,
+                                                uint32_t x) {
+  int2 r;
+  if (ol32) {
+    const uint32_t v = ol32[x];
+    r = v != 0xffffffffu ? make_int2((int32_t)(v >> fbits), (int32_t)(v & ((1u << fbits) - 1u))) : ol[x];
+  } else {
+    r = ol[x];
+  }
+  return (r.x >= 0 && (int64_t)r.x < S) ? spos[r.x] + (uint32_t)r.y : kNone;
+}
 size_t list_rank_workspace_bytes(int64_t N, int64_t nheads);
 // Upper bound over any number of heads.
 size_t list_rank_workspace_upper(int64_t N);

@@ -271,3 +271,29 @@ def test_list_ranking_head_on_a_splitter_after_other_calls():
     r = rank.cpu().numpy()
     # sorted arcs: (0,1), then per vertex i >= 1: (i,i-1), (i,i+1)
     assert r[0] == 0 and np.array_equal(p2.cpu().numpy(), par)
+
+
+def test_euler_root_rejects_non_forests_then_recovers():
+    """An edge list with a cycle or a repeated edge is not a forest: the call
+    fails with an error code (its connectivity pass finds fewer tree edges
+    than given), and the next call on a forest is exact again, with and
+    without ranks (the two list-ranking exits)."""
+    import paper_2603_11645_gb300 as rst
+    n = 9
+    bad = [
+        ([0, 1, 2, 3, 5, 6], [1, 2, 3, 0, 6, 7]),   # a 4-cycle next to a path
+        ([0, 1, 1, 4], [1, 2, 2, 5]),               # a repeated edge
+    ]
+    for u, v in bad:
+        uv = torch.tensor(np.stack([u, v], 1), dtype=torch.int32, device="cuda")
+        for with_rank in (False, True):
+            with pytest.raises(rst.RstError):
+                rst.euler_root(n, uv, 0, with_rank=with_rank)
+    g = graphs.grid(300, 200, seed=21, permute=True, root="random")
+    lab, tu, tv = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+    uv = torch.from_numpy(np.stack([tu, tv], 1).astype(np.int32)).cuda()
+    s, d, r, p = oracle.euler_tour(g.n, tu, tv, g.root)
+    par, rank = rst.euler_root(g.n, uv, g.root)
+    assert np.array_equal(par.cpu().numpy(), p) and np.array_equal(rank.cpu().numpy(), r)
+    par2, _ = rst.euler_root(g.n, uv, g.root, with_rank=False)
+    assert np.array_equal(par2.cpu().numpy(), p)
