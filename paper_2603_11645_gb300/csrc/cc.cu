@@ -65,7 +65,7 @@ struct CcBuffers {
   int32_t* P;        // n: round-1 hook target, then root
   uint32_t* J;       // n: CSR position of the arc to the first neighbour (kNone: isolated)
   uint32_t* rbits;   // n/32 + 2 words: round-1 roots that have edges
-  uint32_t* rpre;    // n/32 + 1: exclusive popcount prefix of rbits (dense root ids)
+  uint2* rrank;      // n/32 + 2: {rbits word, popcount before it} (dense root ids)
   unsigned long long* rtmp;  // scan scratch
   int32_t* C1;       // n: round-1 component of each vertex (-1: isolated)
   int32_t* Ecu[2];   // list entries (ping-pong)
@@ -94,7 +94,7 @@ static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
   b.P = ar.take<int32_t>(n + 1);
   b.J = ar.take<uint32_t>(n + 1);
   b.rbits = ar.take<uint32_t>(n / 32 + 2);
-  b.rpre = ar.take<uint32_t>(n / 32 + 2);
+  b.rrank = ar.take<uint2>(n / 32 + 2);
   b.rtmp = ar.take<unsigned long long>(scan_tmp_words(n / 32 + 1));
   b.C1 = ar.take<int32_t>(n + 1);
   b.ecap = A / 2 + 1;
@@ -331,16 +331,15 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
 // component is its minimum vertex (the minimum vertex w hooks to its first
 // neighbour x, whose first neighbour is w), so minv starts as the root id.
 __global__ void k_r1_label(int64_t n, const int32_t* __restrict__ P, const uint32_t* __restrict__ J,
-                           const uint32_t* __restrict__ rbits, const uint32_t* __restrict__ rpre,
-                           int32_t* __restrict__ C1, int32_t* __restrict__ minv,
-                           unsigned long long* counters) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_COMPS] = rpre[n / 32 + 1];
+                           const uint2* __restrict__ rrank, int32_t* __restrict__ C1,
+                           int32_t* __restrict__ minv, unsigned long long* counters) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_COMPS] = rrank[n / 32 + 1].y;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     int32_t c = -1;
     if (J[v] != kNone) {
       const int32_t r = P[v];
-      c = (int32_t)bit_rank(rbits, rpre, (uint64_t)r);
+      c = (int32_t)bit_rank2(rrank, (uint64_t)r);
       if (r == (int32_t)v) minv[c] = (int32_t)v;
     }
     C1[v] = c;
@@ -1002,9 +1001,9 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
       off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, b.rbits, cnt, status);
   prof_mark(s, "k_r1_resolve");
-  RST_TRY(scan_popcount_words(b.rbits, b.rpre, n / 32 + 1, b.rtmp, s));
+  RST_TRY(scan_popcount_ranked(b.rbits, b.rrank, n / 32 + 1, b.rtmp, s));
   prof_mark(s, "r1_rootscan");
-  RST_LAUNCH(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rbits, b.rpre, b.C1, b.minvpool, cnt);
+  RST_LAUNCH(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rrank, b.C1, b.minvpool, cnt);
   prof_mark(s, "k_r1_label");
   CcPtrs p;
   p.col = col;

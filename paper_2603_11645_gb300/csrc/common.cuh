@@ -244,5 +244,9 @@ rst_status scan_exclusive_u64(const unsigned long long* in, unsigned long long* 
 // Same over 32-bit words of a bitmap: out[w] = popcount of words [0, w).
 rst_status scan_popcount_words(const uint32_t* words, uint32_t* out, int64_t count,
                                unsigned long long* tmp, cudaStream_t s);
+// The same interleaved with the words: out[i] = {words[i], popcount of words
+// [0, i)} for i < count, out[count] = {0, total}.
+rst_status scan_popcount_ranked(const uint32_t* words, uint2* out, int64_t count,
+                                unsigned long long* tmp, cudaStream_t s);
 
 }  // namespace rst

@@ -94,15 +94,15 @@ __global__ void k_mark_roots(int64_t nroots, const int32_t* __restrict__ roots, 
 // and singletons also take P[v] = v; with leaf set, leaf[v] marks vertices of
 // tree degree 1 that are not tree roots.
 template <class OffT>
-__global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint32_t* __restrict__ bits,
-                       const uint32_t* __restrict__ wpre, const uint8_t* __restrict__ is_root,
+__global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint2* __restrict__ rk,
+                       const uint8_t* __restrict__ is_root,
                        uint32_t* __restrict__ toff, int32_t* __restrict__ parent, uint8_t* __restrict__ leaf) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
        v += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t0 = bit_rank(bits, wpre, (uint64_t)off[v]);
+    const uint32_t t0 = bit_rank2(rk, (uint64_t)off[v]);
     toff[v] = t0;
     if (v < n && (parent || leaf)) {
-      const uint32_t t1 = bit_rank(bits, wpre, (uint64_t)off[v + 1]);
+      const uint32_t t1 = bit_rank2(rk, (uint64_t)off[v + 1]);
       if (parent && (t0 == t1 || is_root[v])) parent[v] = (int32_t)v;
       if (leaf) leaf[v] = (t1 - t0 == 1u && !is_root[v]) ? 1 : 0;
     }
@@ -159,15 +159,15 @@ __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32
 // and the Euler successors of both arcs: succ(i) follows rev(i) = k in b's
 // run (wrapping to first[b]), succ(k) follows i in a's run; the arc that
 // wraps into a tree root's first arc is cut (succ = -1).
-__global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint32_t* __restrict__ bits,
-                             const uint32_t* __restrict__ wpre, const uint32_t* __restrict__ toff,
+__global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint2* __restrict__ rk,
+                             const uint32_t* __restrict__ toff,
                              const uint8_t* __restrict__ is_root, int32_t* __restrict__ succ) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
     uint4 r = pairs[t];
     if (r.x == kNone) continue;  // pruned leaf edge
-    const uint32_t i = bit_rank(bits, wpre, r.x);
-    const uint32_t k = bit_rank(bits, wpre, r.y);
+    const uint32_t i = bit_rank2(rk, r.x);
+    const uint32_t k = bit_rank2(rk, r.y);
     const int32_t a = (int32_t)r.z, b = (int32_t)r.w;
     r.x = i;
     r.y = k;
@@ -191,13 +191,13 @@ template <class OffT>
 rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32_t root, CcOut* cc,
                          int32_t* parent_out, uint32_t* rank_out, cudaStream_t s, const int32_t** succ_view) {
   const int64_t W = A / 32 + 1;
-  uint32_t* wpre = ar.take<uint32_t>(W + 1);
+  uint2* rk = ar.take<uint2>(W + 1);  // {tree-arc bitmap word, prefix}
   unsigned long long* tmp = ar.take<unsigned long long>(scan_tmp_words(W));
   uint8_t* is_root = ar.take<uint8_t>(n);
   uint32_t* toff = ar.take<uint32_t>(n + 1);
   int32_t* heads = ar.take<int32_t>(cc->nroots + 1);
-  if (!wpre || !tmp || !is_root || !toff || !heads) return RST_ERR_OOM;
-  RST_TRY(scan_popcount_words(cc->bits, wpre, W, tmp, s));
+  if (!rk || !tmp || !is_root || !toff || !heads) return RST_ERR_OOM;
+  RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
   prof_mark(s, "eu_bitscan");
   RST_CUDA(cudaMemsetAsync(is_root, 0, n, s));
   if (cc->nroots > 0)
@@ -210,18 +210,18 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   const bool prune = rank_out == nullptr && T > 0;
   uint8_t* leaf = prune ? ar.take<uint8_t>(n) : nullptr;
   if (prune && !leaf) return RST_ERR_OOM;
-  RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, cc->bits, wpre, is_root, toff, parent_out,
+  RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, rk, is_root, toff, parent_out,
                                                           leaf);
   prof_mark(s, "k_toff");
   int64_t N = 2 * T;
   if (prune) {
     RST_LAUNCH(k_prune_leaves, grid_for((T + kEuPer - 1) / kEuPer, kBlock, kEuBlocksPerSm), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
     prof_mark(s, "k_prune_leaves");
-    RST_TRY(scan_popcount_words(cc->bits, wpre, W, tmp, s));
-    RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, cc->bits, wpre, is_root, toff, nullptr,
+    RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
+    RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, rk, is_root, toff, nullptr,
                                                             nullptr);
     unsigned long long left = 0;
-    RST_CUDA(cudaMemcpyAsync(host_scratch(8), wpre + W, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    RST_CUDA(cudaMemcpyAsync(host_scratch(8), &rk[W].y, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     RST_CUDA(cudaStreamSynchronize(s));
     uint32_t left32 = 0;
     std::memcpy(&left32, host_scratch(8), sizeof(uint32_t));
@@ -238,7 +238,7 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
   if (!succ || !R) return RST_ERR_OOM;
   const int gT = grid_for(T);
-  RST_LAUNCH(k_pairs_succ, gT, kBlock, 0, s)(T, cc->pairs, cc->bits, wpre, toff, is_root, succ);
+  RST_LAUNCH(k_pairs_succ, gT, kBlock, 0, s)(T, cc->pairs, rk, toff, is_root, succ);
   prof_mark(s, "k_pairs_succ");
   RST_CUDA(cudaGetLastError());
   if (succ_view) *succ_view = succ;  // stays valid while the arena is not reset

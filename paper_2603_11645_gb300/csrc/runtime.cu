@@ -235,10 +235,26 @@ __global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* part
   if (threadIdx.x == 0) partial[nparts] = carry;
 }
 
-template <class Load, class OutT>
+template <class OutT>
+struct StorePrefix {
+  OutT* out;
+  __device__ void operator()(int64_t i, unsigned long long run) const { out[i] = (OutT)run; }
+  __device__ void total(int64_t count, unsigned long long t) const { out[count] = (OutT)t; }
+};
+// {word, popcount of the words before it}: one 8-byte read ranks a bit
+struct StoreRanked {
+  const uint32_t* words;
+  uint2* out;
+  __device__ void operator()(int64_t i, unsigned long long run) const {
+    out[i] = make_uint2(words[i], (uint32_t)run);
+  }
+  __device__ void total(int64_t count, unsigned long long t) const { out[count] = make_uint2(0u, (uint32_t)t); }
+};
+
+template <class Load, class Store>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(Load load, int64_t count,
                                                               const unsigned long long* partial,
-                                                              OutT* out) {
+                                                              Store store) {
   __shared__ unsigned long long sw[33];
   int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   unsigned long long v[kScanItems];
@@ -254,32 +270,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(Load load, int64_t c
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     int64_t i = base + k;
-    if (i < count) out[i] = (OutT)run;
+    if (i < count) store(i, run);
     run += v[k];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) out[count] = (OutT)partial[gridDim.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0) store.total(count, partial[gridDim.x]);
 }
 
-template <class Load, class OutT>
-static rst_status scan_impl(Load load, OutT* out, int64_t count, unsigned long long* tmp,
+template <class Load, class Store>
+static rst_status scan_impl(Load load, Store store, int64_t count, unsigned long long* tmp,
                             cudaStream_t s) {
   int64_t blocks = (count + kScanTile - 1) / kScanTile;
   if (blocks < 1) blocks = 1;
   RST_LAUNCH(k_scan_reduce, (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp);
   RST_LAUNCH(k_scan_partials, 1, 1024, 0, s)(tmp, blocks);
-  RST_LAUNCH(k_scan_down, (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp, out);
+  RST_LAUNCH(k_scan_down, (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp, store);
   RST_CUDA(cudaGetLastError());
   return RST_OK;
 }
 
 rst_status scan_exclusive_u64(const unsigned long long* in, unsigned long long* out, int64_t count,
                               unsigned long long* tmp, cudaStream_t s) {
-  return scan_impl(LoadU64{in}, out, count, tmp, s);
+  return scan_impl(LoadU64{in}, StorePrefix<unsigned long long>{out}, count, tmp, s);
 }
 
 rst_status scan_popcount_words(const uint32_t* words, uint32_t* out, int64_t count,
                                unsigned long long* tmp, cudaStream_t s) {
-  return scan_impl(LoadPopc{words}, out, count, tmp, s);
+  return scan_impl(LoadPopc{words}, StorePrefix<uint32_t>{out}, count, tmp, s);
+}
+
+rst_status scan_popcount_ranked(const uint32_t* words, uint2* out, int64_t count,
+                                unsigned long long* tmp, cudaStream_t s) {
+  return scan_impl(LoadPopc{words}, StoreRanked{words, out}, count, tmp, s);
 }
 
 }  // namespace rst
