@@ -251,27 +251,44 @@ struct StoreRanked {
   __device__ void total(int64_t count, unsigned long long t) const { out[count] = make_uint2(0u, (uint32_t)t); }
 };
 
+// Shared-memory slot of tile item i: one pad slot per 16 items, so both the
+// striped accesses and each thread's run of kScanItems hit distinct banks.
+__device__ __forceinline__ int scan_slot(int i) { return i + (i >> 4); }
+
+// Loads and stores are striped across the block (coalesced); a shared-memory
+// transpose hands every thread kScanItems consecutive items to scan.
 template <class Load, class Store>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(Load load, int64_t count,
                                                               const unsigned long long* partial,
                                                               Store store) {
   __shared__ unsigned long long sw[33];
-  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-  unsigned long long v[kScanItems];
-  unsigned long long s = 0;
+  __shared__ unsigned long long sv[kScanTile + kScanTile / 16];
+  const int64_t tile0 = (int64_t)blockIdx.x * kScanTile;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    int64_t i = base + k;
-    v[k] = i < count ? load(i) : 0ull;
-    s += v[k];
+    const int local = k * kScanThreads + threadIdx.x;
+    const int64_t i = tile0 + local;
+    sv[scan_slot(local)] = i < count ? load(i) : 0ull;
   }
+  __syncthreads();
+  unsigned long long s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) s += sv[scan_slot(threadIdx.x * kScanItems + k)];
   unsigned long long ex = block_exclusive_scan(s, sw, (unsigned long long*)nullptr);
   unsigned long long run = ex + partial[blockIdx.x];
 #pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {  // each item becomes its exclusive prefix
+    const int j = scan_slot(threadIdx.x * kScanItems + k);
+    const unsigned long long t = sv[j];
+    sv[j] = run;
+    run += t;
+  }
+  __syncthreads();
+#pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    int64_t i = base + k;
-    if (i < count) store(i, run);
-    run += v[k];
+    const int local = k * kScanThreads + threadIdx.x;
+    const int64_t i = tile0 + local;
+    if (i < count) store(i, sv[scan_slot(local)]);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) store.total(count, partial[gridDim.x]);
 }
