@@ -86,3 +86,47 @@ def test_multigraph_all_strategies(seed):
     fast = rst.build(off, col, root, "cc_fast")
     assert rst.verify(off, col, root, fast) == 0
     assert oracle.verify(n, off_h, col_h, root, fast.cpu().numpy()) == 0
+
+
+def test_multigraph_batch_equals_each_graph():
+    """The disjoint-union batch on multigraph members: every slice equals the
+    oracle's tree of that member (CC+Euler), and BFS slices equal the oracle BFS."""
+    import paper_2603_11645_gb300 as rst
+    from paper_2603_11645_gb300 import graphs
+    members = []
+    for seed in CASES:
+        n, off, col, root = make_case(seed)
+        members.append(graphs.Graph(f"multigraph {seed}", n, off, col, root))
+    b = graphs.pack_batch(members)
+    d = torch.device("cuda:0")
+    args = [torch.from_numpy(x).to(d) for x in (b.offsets, b.cols, b.vtx_off, b.arc_off, b.roots)]
+    for strategy in ("cc_euler", "bfs"):
+        par = rst.build_batch(*args, strategy=strategy).cpu().numpy()
+        for i, g in enumerate(members):
+            got = par[b.vtx_off[i]:b.vtx_off[i + 1]]
+            if strategy == "cc_euler":
+                want = oracle.rst(g.n, g.offsets, g.cols, g.root)
+            else:
+                want = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
+            assert np.array_equal(got, want), (strategy, g.name)
+
+
+@pytest.mark.parametrize("seed", CASES[:5])
+def test_multigraph_blocks_and_depths(seed):
+    """Blocks, cut vertices and tree depths on the same multigraphs."""
+    import paper_2603_11645_gb300 as rst
+    n, off_h, col_h, root = make_case(seed)
+    d = torch.device("cuda:0")
+    off = torch.from_numpy(off_h).to(d)
+    col = torch.from_numpy(col_h).to(d)
+    lab, cut, nb = rst.bcc(off, col)
+    wl, wc, wn = oracle.bcc(n, off_h, col_h)
+    assert nb == wn
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), wl)
+    assert np.array_equal(cut.cpu().numpy(), wc)
+    par = rst.build(off, col, root, "cc_euler")
+    depth, height = rst.tree_depth(par)
+    want = oracle.tree_depths(n, par.cpu().numpy())
+    want_d = want[0] if isinstance(want, tuple) else want
+    assert np.array_equal(depth.cpu().numpy(), want_d)
+    assert height == int(np.max(want_d)) if n else height == 0
