@@ -42,7 +42,7 @@ rst_status build_cc_euler(const OffT* off, const int32_t* cols, int64_t n, int64
   prof_mark(s, "start");
   RST_TRY(begin(ws, s, &ar));
   CcOut cc;
-  RST_TRY(cc_run<OffT>(ar, off, cols, n, m, root, nullptr, &cc, s));
+  RST_TRY(cc_run<OffT>(ar, off, cols, n, m, root, nullptr, &cc, s, /*prefetch_euler=*/true));
   RST_TRY(euler_root_cc<OffT>(ar, off, n, m, root, &cc, parent, rank_out, s));
   rst_status st = read_device_error(s);
   prof_mark(s, "end");
@@ -241,6 +241,7 @@ rst_status rst_shutdown(void) {
   if (st.ws) cudaFree(st.ws);
   if (st.status) cudaFree(st.status);
   if (st.hostbuf) cudaFreeHost(st.hostbuf);
+  if (st.readback) cudaEventDestroy(st.readback);
   st = DeviceState{};
   return RST_OK;
 }

@@ -984,9 +984,21 @@ static rst_status round_graph_for(const CcPtrs& p, const OffT* off, int64_t n, i
 
 template <class OffT>
 rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A,
-                  int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s) {
+                  int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s, bool prefetch_euler) {
   CcBuffers b = cc_layout(ar, n, A);
   if (!b.P || !b.ctl) return RST_ERR_OOM;
+  // Euler-stage buffers taken here when its first steps are queued early
+  // (the Euler stage then takes them no more, so the total is unchanged)
+  const int64_t W = A / 32 + 1;
+  uint2* pre_rk = nullptr;
+  unsigned long long* pre_tmp = nullptr;
+  uint8_t* pre_root = nullptr;
+  if (prefetch_euler && state().readback && !state_overridden()) {
+    pre_rk = ar.take<uint2>(W + 1);
+    pre_tmp = ar.take<unsigned long long>(scan_tmp_words(W));
+    pre_root = ar.take<uint8_t>(n);
+    if (!pre_rk || !pre_tmp || !pre_root) return RST_ERR_OOM;
+  }
   uint32_t* status = state().status;
   unsigned long long* cnt = dev_counter(0);
   RST_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
@@ -1061,12 +1073,24 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   }
   prof_mark(s, "cc_rounds");
 
-  // one read of the round control: counts for the Euler stage and labels
-  CcCtl* hctl = reinterpret_cast<CcCtl*>(host_scratch(sizeof(CcCtl)));
-  if (!hctl) return RST_ERR_OOM;
+  // one read-back of the counters and the round control (pinned), with the
+  // Euler stage's first steps queued behind it when requested
+  static_assert(8 * sizeof(unsigned long long) + sizeof(CcCtl) <= kHostBufWords * sizeof(unsigned long long),
+                "read-back buffer too small");
+  unsigned long long* hb = state().hostbuf;
+  CcCtl* hctl = reinterpret_cast<CcCtl*>(hb + 8);
+  RST_CUDA(cudaMemcpyAsync(hb, cnt, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   RST_CUDA(cudaMemcpyAsync(hctl, b.ctl, sizeof(CcCtl), cudaMemcpyDeviceToHost, s));
+  if (pre_rk) {
+    RST_CUDA(cudaEventRecord(state().readback, s));
+    RST_TRY(scan_popcount_ranked(b.bits, pre_rk, W, pre_tmp, s));
+    RST_CUDA(cudaMemsetAsync(pre_root, 0, n, s));
+    RST_CUDA(cudaEventSynchronize(state().readback));
+  } else {
+    RST_CUDA(cudaStreamSynchronize(s));
+  }
   unsigned long long h[8];
-  RST_TRY(fetch_u64(cnt, 8, h, s));
+  for (int i = 0; i < 8; ++i) h[i] = hb[i];
   const int rounds_done = hctl->cur;
   if (!eager) count_launches(4LL * rounds_done);  // the round kernels the graph ran
   if (labels_out) {
@@ -1091,6 +1115,9 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   out->roots = b.roots;
   out->rounds = rounds_done + 1;
   out->root_label = root >= 0 ? hctl->root_label : -1;
+  out->rk = pre_rk;
+  out->rk_tmp = pre_tmp;
+  out->is_root = pre_root;
   set_stat(STAT_ROUNDS, out->rounds);
   set_stat(STAT_T, out->T);
   set_stat(STAT_NROOTS, out->nroots);
@@ -1117,9 +1144,9 @@ template rst_status round1_forest<int64_t>(const int64_t*, const int32_t*, int64
                                            uint32_t*, unsigned long long*, cudaStream_t);
 
 template rst_status cc_run<int32_t>(Arena&, const int32_t*, const int32_t*, int64_t, int64_t,
-                                    int32_t, int32_t*, CcOut*, cudaStream_t);
+                                    int32_t, int32_t*, CcOut*, cudaStream_t, bool);
 template rst_status cc_run<int64_t>(Arena&, const int64_t*, const int32_t*, int64_t, int64_t,
-                                    int32_t, int32_t*, CcOut*, cudaStream_t);
+                                    int32_t, int32_t*, CcOut*, cudaStream_t, bool);
 template size_t cc_workspace_bytes<int32_t>(int64_t, int64_t);
 template size_t cc_workspace_bytes<int64_t>(int64_t, int64_t);
 

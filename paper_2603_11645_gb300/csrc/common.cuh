@@ -119,8 +119,10 @@ struct DeviceState {
   char* ws = nullptr;          // workspace
   size_t ws_cap = 0;
   uint32_t* status = nullptr;  // device error word + small scalars (64 words)
-  unsigned long long* hostbuf = nullptr;  // pinned host scratch (64 words)
+  unsigned long long* hostbuf = nullptr;  // pinned host scratch (kHostBufWords words)
+  cudaEvent_t readback = nullptr;         // marks a read-back inside a longer stream (may be null)
 };
+constexpr int kHostBufWords = 512;
 
 // Per-device state and the process-wide call lock.  A call that must not
 // allocate installs its own DeviceState (fixed buffers) for the current host

@@ -191,15 +191,20 @@ template <class OffT>
 rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32_t root, CcOut* cc,
                          int32_t* parent_out, uint32_t* rank_out, cudaStream_t s, const int32_t** succ_view) {
   const int64_t W = A / 32 + 1;
-  uint2* rk = ar.take<uint2>(W + 1);  // {tree-arc bitmap word, prefix}
-  unsigned long long* tmp = ar.take<unsigned long long>(scan_tmp_words(W));
-  uint8_t* is_root = ar.take<uint8_t>(n);
+  // the ranked bitmap and the cleared root flags may already be queued by the
+  // connectivity pass (cc->rk, cc->is_root)
+  const bool pre = cc->rk != nullptr && cc->rk_tmp != nullptr && cc->is_root != nullptr;
+  uint2* rk = pre ? cc->rk : ar.take<uint2>(W + 1);  // {tree-arc bitmap word, prefix}
+  unsigned long long* tmp = pre ? cc->rk_tmp : ar.take<unsigned long long>(scan_tmp_words(W));
+  uint8_t* is_root = pre ? cc->is_root : ar.take<uint8_t>(n);
   uint32_t* toff = ar.take<uint32_t>(n + 1);
   int32_t* heads = ar.take<int32_t>(cc->nroots + 1);
   if (!rk || !tmp || !is_root || !toff || !heads) return RST_ERR_OOM;
-  RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
-  prof_mark(s, "eu_bitscan");
-  RST_CUDA(cudaMemsetAsync(is_root, 0, n, s));
+  if (!pre) {
+    RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
+    prof_mark(s, "eu_bitscan");
+    RST_CUDA(cudaMemsetAsync(is_root, 0, n, s));
+  }
   if (cc->nroots > 0)
     RST_LAUNCH(k_mark_roots, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label,
                                                          root, cc->rootof, is_root);

@@ -33,7 +33,7 @@ struct NoAllocSlot {
   DeviceState st;
 };
 NoAllocSlot g_slots[kMaxDev];
-unsigned long long g_host_words[kMaxDev][64];  // static host buffer for readbacks
+unsigned long long g_host_words[kMaxDev][kHostBufWords];  // static host buffer for readbacks
 
 // Per-device set-up, with that device current: resolve the device addresses of
 // the fixed arrays (the host-side names are only stand-ins).

@@ -37,16 +37,25 @@ struct CcOut {
   // requested for the component whose canonical label is L, or -1.  When set
   // it replaces root / root_label.
   const int32_t* rootof = nullptr;
+  // Set when the connectivity pass already started the Euler stage's first
+  // steps while the host read its counts back: the ranked tree-arc bitmap
+  // (A/32 + 2 {word, prefix} pairs, from bits) and a zeroed root-flag array.
+  uint2* rk = nullptr;
+  unsigned long long* rk_tmp = nullptr;  // the scan's scratch (reused by later scans)
+  uint8_t* is_root = nullptr;
 };
 
 struct CcPlan;  // workspace layout, defined in cc.cu
 
 // Connected components + spanning forest.  `labels_out` (nullable) receives the
 // canonical label of every vertex.  `root` (may be -1) selects the vertex whose
-// component label is returned in out->root_label.
+// component label is returned in out->root_label.  With prefetch_euler the
+// Euler stage's bitmap scan and root-flag clear are queued behind the count
+// read-back, so the GPU runs them while the host waits (out->rk, out->is_root).
 template <class OffT>
 rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A,
-                  int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s);
+                  int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s,
+                  bool prefetch_euler = false);
 template <class OffT>
 size_t cc_workspace_bytes(int64_t n, int64_t A);
 // Release cached round graphs (rst_shutdown).

@@ -92,7 +92,10 @@ static rst_status ensure_small(DeviceState& st) {
     RST_CUDA(cudaMemset(st.status, 0, 64 * sizeof(uint32_t)));
   }
   if (!st.hostbuf) {
-    RST_CUDA(cudaMallocHost(&st.hostbuf, 64 * sizeof(unsigned long long)));
+    RST_CUDA(cudaMallocHost(&st.hostbuf, kHostBufWords * sizeof(unsigned long long)));
+  }
+  if (!st.readback) {
+    RST_CUDA(cudaEventCreateWithFlags(&st.readback, cudaEventDisableTiming));
   }
   return RST_OK;
 }
