@@ -14,7 +14,9 @@
 // which L2 holds far better, and the walk runs about a quarter faster.
 // The splitters form a shorter weighted list, ranked the same way until it fits
 // one block's shared memory, where Wyllie pointer jumping finishes it.  A
-// final coalesced pass adds each owner's position to the element's offset.
+// final coalesced pass adds each owner's position to the element's offset;
+// at the first level a caller that only needs some positions can skip it and
+// read them from the records (lr_position).
 //
 // Element indices follow the lexicographic arc order, unrelated to tour
 // order, so index-spaced splitters sample the tour uniformly: gaps average K.
