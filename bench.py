@@ -175,6 +175,31 @@ def traffic_for(kernel, units):
     return int(e["bytes_per_unit"] * units)
 
 
+def roofline_entry(dom, kern, n, A, st, peak, peak_src, total_ms, world):
+    """The `roofline` object for the dominant kernel `dom`: algorithmic bytes
+    per launch over its mean live launch time, against the measured copy
+    bandwidth `peak` (GB/s).  `kern` maps kernel stage names to their live
+    launch times (ms).  `traffic` is the committed per-launch DRAM traffic of
+    that kernel (None when its source changed since the capture), and
+    `traffic_frac` the DRAM bandwidth that traffic amounts to at the live
+    launch time, as a fraction of the same peak."""
+    if not dom:
+        return None
+    per_launch_ms = sum(kern[dom]) / len(kern[dom])
+    byts = kernel_bytes(dom, n, A, st, 4)
+    if not byts:
+        return None
+    achieved = byts / (per_launch_ms / 1e3) / 1e9
+    traffic = traffic_for(dom, st["lr_n"] if dom.startswith("k_lr") else st["T"])
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_frac": (round(traffic / (per_launch_ms / 1e3) / 1e9 / peak, 4)
+                             if traffic else None),
+            "kernel": dom, "algorithmic_bytes": int(byts),
+            "launch_ms": round(per_launch_ms, 4), "peak_source": peak_src,
+            "share_of_step": round(sum(kern[dom]) / total_ms, 3) if world == 1 else None}
+
+
 # ----------------------------------------------------------------- oracle (CPU baseline)
 
 def oracle_edges_per_s(g, reps=1):
@@ -260,18 +285,7 @@ def run_ours(args, rank, world, local_rank):
     st = {"rounds": stats[0], "c1": stats[1], "E2": stats[2], "T": stats[3], "nroots": stats[4],
           "lr_levels": stats[5], "lr_n": stats[6]}
     peak, peak_src = measured_peaks()
-    roofline = None
-    if dom:
-        per_launch_ms = sum(kern[dom]) / len(kern[dom])
-        byts = kernel_bytes(dom, g.n, g.A, st, 4)
-        if byts:
-            achieved = byts / (per_launch_ms / 1e3) / 1e9
-            roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(achieved / peak, 4),
-                        "traffic": traffic_for(dom, st["lr_n"] if dom.startswith("k_lr") else st["T"]),
-                        "kernel": dom, "algorithmic_bytes": int(byts),
-                        "launch_ms": round(per_launch_ms, 4), "peak_source": peak_src,
-                        "share_of_step": round(sum(kern[dom]) / total_ms, 3) if world == 1 else None}
+    roofline = roofline_entry(dom, kern, g.n, g.A, st, peak, peak_src, total_ms, world)
     stage_summary = {nm: round(sum(v) / args.steps, 4) for nm, v in
                      sorted(stages.items(), key=lambda kv: -sum(kv[1]))}
 

@@ -70,3 +70,22 @@ def test_committed_traffic_records_name_existing_kernels():
         src = bench._function_source(os.path.join(bench.ROOT, e["file"]), e["function"])
         assert src is not None, key
         assert e["bytes_per_unit"] > 0 and e["read_bytes"] + e["write_bytes"] > 0
+
+
+def test_roofline_entry_for_the_headline_kernel():
+    """The roofline object as the bench builds it from live stage times:
+    achieved = algorithmic bytes / mean launch time, frac against the peak,
+    and the committed traffic converted to a bandwidth fraction."""
+    kern = {"k_r1_resolve": [0.48, 0.50], "k_pairs_succ": [0.44, 0.44]}
+    r = bench.roofline_entry("k_r1_resolve", kern, N_V, A, STATS, 6786.2, "measured", 3.5 * 2, 1)
+    byts = bench.kernel_bytes("k_r1_resolve", N_V, A, STATS, 4)
+    assert r["kernel"] == "k_r1_resolve" and r["algorithmic_bytes"] == int(byts)
+    assert r["launch_ms"] == 0.49
+    assert abs(r["achieved"] - byts / 0.49e-3 / 1e9) < 0.1
+    assert abs(r["frac"] - r["achieved"] / 6786.2) < 1e-4
+    assert r["traffic"] == bench.traffic_for("k_r1_resolve", STATS["T"])
+    if r["traffic"]:
+        assert abs(r["traffic_frac"] - r["traffic"] / 0.49e-3 / 1e9 / 6786.2) < 1e-4
+    assert r["share_of_step"] == round(0.98 / 7.0, 3)
+    assert bench.roofline_entry(None, kern, N_V, A, STATS, 1.0, "", 1.0, 1) is None
+    assert bench.roofline_entry("k_unknown", {"k_unknown": [1.0]}, N_V, A, STATS, 1.0, "", 1.0, 1) is None
