@@ -461,6 +461,65 @@ def test_prrst_path_and_star():
     assert par.tolist() == [5] + [0] * 4 + [5] + [0] * 3
 
 
+def _prrst_pin_graphs():
+    yield from _families()
+    yield graphs.grid(30, 20, seed=8)
+    yield graphs.erdos_renyi(500, 1500, seed=9)
+    yield graphs.rmat(9, 8, seed=10, connect=True, offsets_bits=32)
+
+
+def _tree_edge_set(par):
+    return {(min(v, int(p)), max(v, int(p))) for v, p in enumerate(par) if p != v}
+
+
+@pytest.mark.parametrize("gi", range(8))
+def test_prrst_keeps_the_first_two_rounds_grafts(gi):
+    """Grafting only adds edges and path reversal only turns them around, so
+    the final tree contains every edge the first two rounds graft, and those
+    follow from the round rules alone (Section III-C, reading R9).
+    Round 0 (minimum rule) on singletons: every vertex with a smaller
+    neighbour grafts onto its smallest neighbour.  The trees after it are the
+    components of those edges, each rooted at its smallest vertex (the grafts
+    follow decreasing ids).  Round 1 (maximum rule): each such tree grafts along
+    its smallest arc (u, v) (u in the tree) into a tree with a larger root.
+    A swapped rule, a reversed key order or a graft that loses an edge fails
+    here; the components come from scipy, not from the oracle's pointers."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    g = list(_prrst_pin_graphs())[gi]
+    n = g.n
+    par, rounds = oracle.prrst(n, g.offsets, g.cols, g.root)
+    tree = _tree_edge_set(par)
+    off = g.offsets.astype(np.int64)
+    src = np.repeat(np.arange(n), np.diff(off))
+    dst = g.cols.astype(np.int64)
+    # round 0
+    smaller = dst < src
+    minnbr = np.full(n, -1)
+    for u, v in zip(src[smaller], dst[smaller]):
+        if minnbr[u] < 0 or v < minnbr[u]:
+            minnbr[u] = v
+    r0 = [(int(min(v, m)), int(max(v, m))) for v, m in enumerate(minnbr) if m >= 0]
+    assert set(r0) <= tree
+    # trees after round 0 and their roots (smallest vertex)
+    has = minnbr >= 0
+    a = coo_matrix((np.ones(has.sum()), (np.arange(n)[has], minnbr[has])), shape=(n, n))
+    _, comp = connected_components(a, directed=False)
+    root_of_comp = np.full(comp.max() + 1, n)
+    np.minimum.at(root_of_comp, comp, np.arange(n))
+    rt = root_of_comp[comp]
+    # round 1: smallest (u, v) with u in the tree and a larger root across the arc
+    elig = rt[dst] > rt[src]
+    best = {}
+    for u, v in zip(src[elig], dst[elig]):
+        c = comp[u]
+        if c not in best or (u, v) < best[c]:
+            best[c] = (int(u), int(v))
+    r1 = {(min(u, v), max(u, v)) for u, v in best.values()}
+    assert r1 <= tree
+    assert len(tree) >= len(set(r0) | r1)
+
+
 # ------------------------------------------------------------------ tree depth
 
 @pytest.mark.parametrize("n,r", [(1, 0), (10, 0), (10, 4), (10, 9)])
