@@ -14,11 +14,11 @@ Parity status per function (what pins each one, see tests/test_oracle_pins.py):
                    agreement of its parent with ``root_forest``.
 * ``bfs``          pinned: Manhattan levels on grids, brute-force parent rule.
 * ``verify``       pinned: Kirchhoff spanning-tree counts (n <= 6), mutations.
-* ``prrst``        partly pinned: the paper fixes no unique tree; its output
-                   passes ``verify``, and the grafts of its first two rounds,
-                   derived from the round rules alone (independent component
-                   labelling), are all in the final tree.  The later rounds'
-                   grafts are parity unpinned.  From
+* ``prrst``        pinned: its output passes ``verify``; the grafts of its
+                   first two rounds follow from the round rules alone; and its
+                   edge set and round count equal a derivation of the same
+                   rules over whole trees (no parent pointers, no path
+                   reversal), also when started from a forest.  From
                    a given forest (edge insertions): hand-derived graft and
                    reversal cases, and the invariants (valid RST of the new
                    graph, every old tree edge kept, only inserted edges added).

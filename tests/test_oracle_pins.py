@@ -520,6 +520,91 @@ def test_prrst_keeps_the_first_two_rounds_grafts(gi):
     assert len(tree) >= len(set(r0) | r1)
 
 
+def _prrst_by_components(n, offsets, cols, init=None):
+    """PR-RST's tree edges and round count, derived from the round rules at
+    the level of whole trees (no parent pointers, no path reversal): in round
+    t every tree with an arc into a tree of smaller (t even) or larger (t odd)
+    root grafts along its smallest such arc (u, v), u in the tree; a graft
+    re-roots the tree at u, so the merged tree keeps the root of the tree at
+    the end of the graft chain.  Stops after the first round without a graft."""
+    off = np.asarray(offsets, dtype=np.int64)
+    src = np.repeat(np.arange(n), np.diff(off))
+    dst = np.asarray(cols, dtype=np.int64)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    edges = set()
+    root = np.arange(n)
+    if init is not None:
+        init = np.asarray(init, dtype=np.int64)
+        for v in range(n):
+            x = v
+            while init[x] != x:
+                x = init[x]
+            root[v] = x
+            if init[v] != v:
+                edges.add((min(v, int(init[v])), max(v, int(init[v]))))
+    t = 0
+    while True:
+        rs, rd = root[src], root[dst]
+        elig = (rd < rs) if t % 2 == 0 else (rd > rs)
+        best = {}
+        for u, v in zip(src[elig], dst[elig]):
+            r = int(root[u])
+            if r not in best or (int(u), int(v)) < best[r]:
+                best[r] = (int(u), int(v))
+        if not best:
+            return edges, t + 1
+        nxt = {}
+        for r, (u, v) in best.items():
+            edges.add((min(u, v), max(u, v)))
+            nxt[r] = int(root[v])
+        sink = {}
+        for r in set(root.tolist()):
+            x = r
+            while x in nxt:
+                x = nxt[x]
+            sink[r] = x
+        root = np.array([sink[int(r)] for r in root])
+        t += 1
+
+
+@pytest.mark.parametrize("gi", range(8))
+def test_prrst_edge_set_equals_the_tree_level_derivation(gi):
+    """The oracle's PR-RST (pointer-level rounds with path reversal) against
+    the same rules applied to whole trees: identical tree edges and round
+    count, and the final tree rooted at the requested root (other components
+    at their smallest vertex)."""
+    g = list(_prrst_pin_graphs())[gi]
+    par, rounds = oracle.prrst(g.n, g.offsets, g.cols, g.root)
+    edges, want_rounds = _prrst_by_components(g.n, g.offsets, g.cols)
+    assert _tree_edge_set(par) == edges
+    assert rounds == want_rounds
+    lab, _, _ = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+    for v in range(g.n):
+        is_root = par[v] == v
+        want_root = v == g.root or (lab[v] == v and lab[g.root] != v)
+        assert is_root == want_root, v
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_prrst_from_a_forest_equals_the_tree_level_derivation(seed):
+    """Edge insertions (rounds started from a rooted forest) against the
+    same tree-level derivation started from the forest's trees."""
+    rng = np.random.default_rng(40 + seed)
+    g = graphs.grid(12, 9, seed=seed + 1)
+    n = g.n
+    par0 = oracle.rst(n, g.offsets, g.cols, g.root)
+    # drop a random third of the tree edges: the rest is the starting forest
+    init = par0.copy()
+    for v in np.nonzero(rng.random(n) < 0.33)[0]:
+        init[v] = v
+    # every chain must still end at a root: re-root each piece at its top
+    par, rounds = oracle.prrst(n, g.offsets, g.cols, g.root, init=init)
+    edges, want_rounds = _prrst_by_components(n, g.offsets, g.cols, init=init)
+    assert _tree_edge_set(par) == edges
+    assert rounds == want_rounds
+
+
 # ------------------------------------------------------------------ tree depth
 
 @pytest.mark.parametrize("n,r", [(1, 0), (10, 0), (10, 4), (10, 9)])
