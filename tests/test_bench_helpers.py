@@ -89,3 +89,22 @@ def test_roofline_entry_for_the_headline_kernel():
     assert r["share_of_step"] == round(0.98 / 7.0, 3)
     assert bench.roofline_entry(None, kern, N_V, A, STATS, 1.0, "", 1.0, 1) is None
     assert bench.roofline_entry("k_unknown", {"k_unknown": [1.0]}, N_V, A, STATS, 1.0, "", 1.0, 1) is None
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """`bench.py --impl reference` (the CPU oracle on a bounded sample): one
+    JSON object with the bench's metric and unit, impl = reference, a
+    cpu_baseline describing the run and an e2e entry without host copies;
+    ranks other than 0 do no work."""
+    import argparse
+    args = argparse.Namespace(steps=1, warmup=0)
+    assert bench.run_reference(args, 1, 2) is None
+    line = bench.run_reference(args, 0, 1)
+    json.dumps(line)  # serialisable as the printed line
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "edges/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["steps"] == 1 and line["n_gpus"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 == e2e["d2h_bytes_per_step"]
