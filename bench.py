@@ -11,8 +11,10 @@ C ABI with host buffers, and the CPU oracle timed on the host's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank builds the same graph on its own GPU: the
-single-graph path does not shard, so ranks are replicas ("scaling": "weak").
+With --gpus N > 1 the script starts N ranks itself (torchrun, one process per
+GPU) unless a launcher already did.  Every rank builds the same graph on its
+own GPU: the single-graph path does not shard, so ranks are replicas
+("scaling": "weak"); the batch of graphs is split by arc count.
 """
 from __future__ import annotations
 
@@ -134,6 +136,51 @@ def kernel_bytes(name, n, A, st, o):
         "k_parent_from_owner": 16 * T + K * (8 + 8 + 4),
     }
     return models.get(name)
+
+
+def step_bytes_model(n, A, T, o):
+    """Algorithmic bytes of one whole CC+Euler step (the hot-path byte model):
+    connectivity reads the offsets and every column once, gathers one 4-byte
+    label per arc, reads and writes the labels and writes the tree edges
+    (o(n+1) + 8A + 16n + 8T); the Euler stage moves about 60 bytes per tree
+    arc (arc generation, one counting pass over key and value, next, succ,
+    rank read and write, twin reads) plus 12 per vertex (60E + 12n, E = 2T)."""
+    return o * (n + 1) + 8 * A + 16 * n + 8 * T + 60 * (2 * T) + 12 * n
+
+
+def step_roofline(n, A, T, o, ms, peak):
+    """The whole step against the byte model: bytes / time over the peak."""
+    byts = step_bytes_model(n, A, T, o)
+    achieved = byts / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "algorithmic_bytes": int(byts), "ms": round(ms, 4),
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "roof_ms": round(byts / (peak * 1e9) * 1e3, 4)}
+
+
+def host_cpu():
+    """Model name and logical core count of the host the oracle runs on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":", 1)
+                if len(k) == 2 and k[0].strip() in ("model name", "Model name", "CPU part", "Hardware"):
+                    model = model or k[1].strip()
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
 
 
 def _function_source(path, name):
@@ -362,18 +409,21 @@ def run_ours(args, rank, world, local_rank):
         step(strat)
         heights[strat] = rst.tree_depth(par, want_depths=False)[1]
 
-    batch = None if args.no_batch else run_batch(args, dev, stream, rst, graphs, torch, rank, world)
-    families = None if args.no_families else run_families(args, dev, stream, rst, graphs, torch)
+    cpu_on = world == 1 and not args.no_cpu_baseline
+    grid256 = run_grid256(args, dev, stream, rst, graphs, torch, cpu_on)
+    batch = None if args.no_batch else run_batch(args, dev, stream, rst, graphs, torch, rank, world, cpu_on)
+    families = None if args.no_families else run_families(args, dev, stream, rst, graphs, torch, peak, cpu_on)
     selector = run_selector_report(off, col, g.root, torch)
 
     out = None
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
+        if cpu_on:
             v, t = oracle_edges_per_s(g, 1)
             cpu = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
                    "sample": f"one run of the sequential oracle (Kruskal over (min,max) keys + "
-                             f"sequential Euler tour) on the full 4096x4096 workload, {t:.1f} s"}
+                             f"sequential Euler tour) on the full 4096x4096 workload, {t:.1f} s",
+                   **host_cpu()}
         out = {
             "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -387,6 +437,7 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": int(4 * g.n)},
             "gpu_launches": int(launches),
             "roofline": roofline,
+            "roofline_step": step_roofline(g.n, g.A, st["T"], 4, ms_step, peak),
             "cpu_baseline": cpu,
             "clocks": clk,
             "bfs": {"value": g.m / (bfs_med / 1e3), "unit": "edges/s", "ms_per_step": bfs_med,
@@ -399,6 +450,7 @@ def run_ours(args, rank, world, local_rank):
             "tree_height": heights,
             "bcc": bcc_rep,
             "insert": ins_rep,
+            "grid256": grid256,
             "batch": batch,
             "families": families,
             "selector": selector,
@@ -408,7 +460,7 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def run_batch(args, dev, stream, rst, graphs, torch, rank=0, world=1):
+def run_batch(args, dev, stream, rst, graphs, torch, rank=0, world=1, cpu_on=False):
     """4096 mixed graphs: one rst_build_batch call vs one rst_build call per
     graph.  With several ranks the graphs are split by arc count (LPT) and
     each rank builds its share; times are the slowest rank's."""
@@ -455,7 +507,18 @@ def run_batch(args, dev, stream, rst, graphs, torch, rank=0, world=1):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     per_graph = multi.max_over_ranks(e0.elapsed_time(e1), dev)
-    return {"ranks": world,
+    cpu = None
+    if cpu_on and rank == 0:
+        import oracle
+        t0 = time.perf_counter()
+        for gr in full.graphs:
+            lab, tu, tv = oracle.cc_kruskal(gr.n, gr.offsets, gr.cols)
+            oracle.euler_tour(gr.n, tu, tv, gr.root)
+        t = time.perf_counter() - t0
+        cpu = {"value": full.m / t, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"one pass of the sequential oracle (Kruskal + Euler tour) over all "
+                         f"{full.G} graphs of the batch, {t:.1f} s", **host_cpu()}
+    return {"ranks": world, "cpu_baseline": cpu,
             "workload": f"{full.G} graphs (grid / chain+chords / R-MAT in turn), n log-uniform "
                         f"1K-{args.batch_hi // 1024}K, "
                         f"{full.N} vertices, {full.A} arcs, int32 packed CSR"
@@ -517,25 +580,88 @@ def _time(fn, reps, torch, dev, stream, flush=None):
     return statistics.median(ts)
 
 
-def run_families(args, dev, stream, rst, graphs, torch):
-    """The power-law family: R-MAT scale 22 (edge factor 16, connected, int64 offsets)."""
-    g = graphs.rmat(22, 16, seed=3, connect=True, offsets_bits=64)
+def _stats(L):
+    stats = (ctypes.c_longlong * 8)()
+    L.rst_last_stats(stats, 8)
+    return {"rounds": stats[0], "c1": stats[1], "E2": stats[2], "T": stats[3], "nroots": stats[4],
+            "lr_levels": stats[5], "lr_n": stats[6]}
+
+
+def run_families(args, dev, stream, rst, graphs, torch, peak, cpu_on):
+    """The power-law workload: R-MAT scale 24, edge factor 16, (0.57, 0.19,
+    0.19, 0.05), symmetrised, deduplicated, connected to vertex 0, int64
+    offsets, root 0.  Every strategy, the whole CC+Euler step against the
+    byte model, and the sequential oracle on the same graph."""
+    g = graphs.workload_rmat24()
     from paper_2603_11645_gb300 import autotune
     autotune.apply(g.n, g.A)
     off = torch.from_numpy(g.offsets).to(dev)
     col = torch.from_numpy(g.cols).to(dev)
     par = torch.empty(g.n, dtype=torch.int32, device=dev)
-    out = {"workload": f"R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), connected to 0, "
-                       f"int64 offsets, root 0: {g.n} vertices, {g.m} edges", "m": g.m}
-    for strat in ("cc_euler", "bfs", "pr_rst", "cc_fast"):
-        ms = _time(lambda: rst.build(off, col, g.root, strat, out=par), 3, torch, dev, stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    out = {"workload": f"R-MAT scale 24, edge factor 16, (0.57,0.19,0.19,0.05), symmetrised, "
+                       f"deduplicated, connected to 0, int64 offsets, root 0: {g.n} vertices, "
+                       f"{g.m} edges ({g.A} arcs)", "n": g.n, "m": g.m}
+    L = rst.lib()
+    for strat in ("cc_euler", "bfs", "bfs_device", "pr_rst", "cc_fast"):
+        if strat not in rst.STRATEGIES:
+            continue
+        reps = max(3, min(args.steps, 10)) if strat == "cc_euler" else 3
+        ms = _time(lambda: rst.build(off, col, g.root, strat, out=par), reps, torch, dev, stream, flush)
         out[strat] = {"ms": ms, "value": g.m / (ms / 1e3), "unit": "edges/s"}
+        if strat == "cc_euler":
+            st = _stats(L)
+            out["cc_euler"]["roofline_step"] = step_roofline(g.n, g.A, st["T"], 8, ms, peak)
+            out["cc_euler"]["stats"] = st
     out["cc_euler_speedup_over_bfs"] = out["bfs"]["ms"] / out["cc_euler"]["ms"]
-    ms = _time(lambda: rst.bcc(off, col), 3, torch, dev, stream)
+    ms = _time(lambda: rst.bcc(off, col), 3, torch, dev, stream, flush)
     _, cut, nb = rst.bcc(off, col)
     out["bcc"] = {"ms": ms, "value": g.m / (ms / 1e3), "unit": "edges/s", "blocks": nb,
                   "cut_vertices": int(cut.sum().item())}
-    return {"rmat22": out}
+    if cpu_on:
+        v, t = oracle_edges_per_s(g, 1)
+        out["cpu_baseline"] = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                               "sample": f"one run of the sequential oracle (Kruskal + Euler tour) on "
+                                         f"the full R-MAT scale-24 graph, {t:.1f} s", **host_cpu()}
+    del off, col, par, flush
+    torch.cuda.empty_cache()
+    return {"rmat24": out}
+
+
+def run_grid256(args, dev, stream, rst, graphs, torch, cpu_on):
+    """The 256 x 256 permuted grid (65,536 vertices, root = the permuted
+    corner): small enough to live in L2, so it measures latency and launch
+    counts rather than bandwidth."""
+    g = graphs.workload_grid256()
+    off = torch.from_numpy(g.offsets).to(dev)
+    col = torch.from_numpy(g.cols).to(dev)
+    par = torch.empty(g.n, dtype=torch.int32, device=dev)
+    L = rst.lib()
+    out = {"workload": "grid 256x256 4-neighbour, ids permuted by seed 1, root = permuted corner, "
+                       "int32 CSR (65,536 vertices, 130,560 edges)", "n": g.n, "m": g.m}
+    for strat in ("cc_euler", "bfs", "bfs_device", "pr_rst"):
+        if strat not in rst.STRATEGIES:
+            continue
+        rst.build(off, col, g.root, strat, out=par)
+        c0 = L.rst_launch_count()
+        rst.build(off, col, g.root, strat, out=par)
+        launches = L.rst_launch_count() - c0
+        ms = _time(lambda: rst.build(off, col, g.root, strat, out=par), 20, torch, dev, stream)
+        out[strat] = {"us": round(ms * 1e3, 1), "value": g.m / (ms / 1e3), "unit": "edges/s",
+                      "launches": int(launches)}
+    if cpu_on:
+        import oracle
+        ts = []
+        for _ in range(6):
+            t0 = time.perf_counter()
+            lab, tu, tv = oracle.cc_kruskal(g.n, g.offsets, g.cols)
+            oracle.euler_tour(g.n, tu, tv, g.root)
+            ts.append(time.perf_counter() - t0)
+        t = statistics.median(ts[1:])
+        out["cpu_baseline"] = {"value": g.m / t, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                               "sample": "sequential oracle (Kruskal + Euler tour) on the full graph, "
+                                         "median of 5 runs after 1 warm-up", **host_cpu()}
+    return out
 
 
 def run_selector_report(off, col, root, torch):
@@ -608,6 +734,21 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def launch_command(argv, gpus, port):
+    """The torchrun command that starts `gpus` ranks of this script on one node
+    (rendezvous on 127.0.0.1), used when --gpus N > 1 is given without a
+    launcher."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *argv]
+
+
+def _free_port():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -629,9 +770,14 @@ def main():
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: start the ranks and hand back their exit status
+        sys.exit(subprocess.call(launch_command(sys.argv[1:], args.gpus, _free_port())))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but the launcher started {world} ranks")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

@@ -13,8 +13,10 @@
  *   entries (m counts DIRECTED arcs, i.e. twice the undirected edges).  Every
  *   undirected edge {u,v} is stored as both u->v and v->u, every row is sorted
  *   ascending, column ids are in [0, n).  Self-loops and repeated arcs are
- *   tolerated and never become tree edges.  Vertex ids are int32 (n < 2^31);
- *   m must be below 2^32.
+ *   tolerated and never become tree edges.  Vertex ids are int32 and n must be
+ *   below 2^30 (larger n returns RST_ERR_UNSUPPORTED: the up to 2(n-1) tree
+ *   arcs of the Euler tour are indexed by int32); m must be below 2^32 (below 2^31 with
+ *   32-bit offsets).
  * Memory: every array argument is caller-owned DEVICE memory unless marked
  *   "host".  The library never frees caller memory.  It keeps an internal
  *   per-device workspace that grows on demand (cudaMalloc) and is released by
@@ -97,11 +99,14 @@ int rst_version(void);
  *               vertices outside the largest component with the rest of
  *               their rows, merging by compare-and-swap), then the same
  *               Euler-tour rooting.
- * CC+Euler and BFS results are unique: CC+Euler roots the minimum spanning
- * forest under edge keys (min(u,v), max(u,v)); BFS takes for every vertex the
- * minimum-id neighbour on the previous level.  PR-RST and RST_CC_FAST return
- * a valid RST (components and tree roots fixed, the tree edges chosen by
- * races: not reproducible run to run).
+ * CC+Euler, BFS and PR-RST results are unique and identical run to run:
+ * CC+Euler roots the minimum spanning forest under edge keys (min(u,v),
+ * max(u,v)); BFS takes for every vertex the minimum-id neighbour on the
+ * previous level; PR-RST returns the forest its rounds build when every tree
+ * grafts by its eligible edge of smallest (u, v) key (minimum rule first,
+ * then alternating), re-rooted at the requested root.  RST_CC_FAST returns a
+ * valid RST with the same components and tree roots, but its tree edges are
+ * chosen by races (not reproducible run to run).
  */
 rst_status rst_build(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols,
                      int64_t n, int64_t m, int32_t root, rst_strategy strategy,
@@ -240,19 +245,26 @@ rst_status rst_tree_depth(const int32_t *parent, int64_t n, int32_t *depth_out, 
 
 /*
  * rst_build_noalloc -- the CC+Euler rooted spanning tree of rst_build, for
- * callers that cannot allocate memory: code running while a stream is being
- * captured into a CUDA graph (cudaMalloc is not permitted then), or hosts
- * whose device-memory budget is fixed in advance.  The paper has no
- * counterpart; this is a deployment variant of the same computation.
+ * callers that cannot allocate device memory.  Such callers include a
+ * serving process or an embedding runtime that reserves its whole device
+ * memory budget at start-up (a pool that the library cannot draw from), and
+ * hosts whose allocator must not be entered from the calling thread.  The
+ * paper has no counterpart; this is a deployment variant of the same
+ * computation, with the same result.
  *   Arguments and output are those of rst_build with RST_CC_EULER; the
  *   caller still provides the graph and parent_out in device memory.
  *   Limits: n <= 65,536 vertices and m <= 524,288 arcs; larger inputs return
  *   RST_ERR_UNSUPPORTED before any GPU work.
  *   Memory: it never calls cudaMalloc, cudaFree, cudaMallocHost or any other
- *   allocating routine.  Its workspace is a 16 MiB array defined inside the
- *   library that every GPU loading the library holds until process exit.
- *   The first call on a device looks up that array's device address; make
- *   that first call before starting any stream capture.
+ *   allocating routine (nor creates events, streams or graphs).  Its
+ *   workspace is a 16 MiB array defined inside the library that every GPU
+ *   loading the library holds until process exit.
+ *   Set-up: the first call on a device looks up that array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture begins.
+ *   Like every entry point it returns after its work has completed on
+ *   `stream`: it reads the round count and its status word back between
+ *   rounds and at the end.
  *   Sharing: every call on a device uses the same array, which keeps the
  *   previous call's contents (the call clears what must start at zero).
  *   Calls whose GPU work overlaps (different streams without ordering) race

@@ -986,7 +986,7 @@ template <class OffT>
 rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A,
                   int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s, bool prefetch_euler) {
   CcBuffers b = cc_layout(ar, n, A);
-  if (!b.P || !b.ctl) return RST_ERR_OOM;
+  if (ar.used > ar.cap) return RST_ERR_OOM;  // some buffer of the layout did not fit (null)
   // Euler-stage buffers taken here when its first steps are queued early
   // (the Euler stage then takes them no more, so the total is unchanged)
   const int64_t W = A / 32 + 1;

@@ -298,8 +298,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
   const int sh = tuning().lr_shift;
   lr_layout(ar, N, nheads, sh, &levels, &wpj, &wval, &wflag);
   if (levels.count > kLrMaxLevels) return RST_ERR_UNSUPPORTED;
-  for (int l = 0; l < levels.count; ++l)
-    if (!levels.b[l].spos) return RST_ERR_OOM;
+  if (ar.used > ar.cap) return RST_ERR_OOM;  // some buffer of the layout did not fit (null)
   set_stat(STAT_LEVELS, (long long)levels.count);
   set_stat(STAT_LR_N, N);
   uint32_t* status = state().status;

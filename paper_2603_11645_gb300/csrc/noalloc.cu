@@ -1,12 +1,16 @@
 // rst_build_noalloc: CC+Euler rooted spanning tree without any allocation.
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA
-// stream is being captured into a graph (cudaMalloc is not allowed there),
-// callers whose memory budget is fixed up front by a pool or an embedding
-// runtime, and hosts whose allocator is not safe to call from the calling
-// thread.  For them this entry point carves its whole workspace out of a
-// fixed device array defined in this file, so it never calls cudaMalloc,
-// cudaFree, cudaMallocHost or any allocating library routine.
+// Some callers cannot allocate device memory: a serving process or an
+// embedding runtime that reserves its whole device-memory budget at start-up
+// (a pool this library cannot draw from), and hosts whose allocator must not
+// be entered from the calling thread.  For them this entry point carves its
+// whole workspace out of a fixed device array defined in this file, so it
+// never calls cudaMalloc, cudaFree, cudaMallocHost or any allocating library
+// routine, and creates no event, stream or graph (the contraction rounds run
+// from the host, one round at a time, reading the round count back into a
+// static host buffer).  The first call on a device looks up the array's
+// device address (cudaGetSymbolAddress, with that device current); that
+// first call should come before any stream capture begins.
 //
 // The array is a file-scope __device__ object: every GPU that loads this
 // library holds it (kNoAllocScratchBytes + 256 bytes) until the process

@@ -94,7 +94,9 @@ static rst_status ensure_small(DeviceState& st) {
   if (!st.hostbuf) {
     RST_CUDA(cudaMallocHost(&st.hostbuf, kHostBufWords * sizeof(unsigned long long)));
   }
-  if (!st.readback) {
+  // the read-back event only serves calls with their own workspace; a call
+  // running on fixed buffers (state override) creates nothing
+  if (!st.readback && !state_overridden()) {
     RST_CUDA(cudaEventCreateWithFlags(&st.readback, cudaEventDisableTiming));
   }
   return RST_OK;

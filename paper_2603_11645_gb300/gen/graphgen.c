@@ -13,9 +13,53 @@
  * Randomness: SplitMix64 (Steele, Lea, Flood 2014), used as a counter-based
  * stream so that every edge draw depends only on (seed, index).
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
+
+/* ---- work splitting over threads ------------------------------------------
+ * Every parallel loop below splits an index range into contiguous pieces and
+ * writes disjoint outputs, so its result is the same for any thread count. */
+typedef void (*gg_range_fn)(void *ctx, int64_t lo, int64_t hi);
+typedef struct { gg_range_fn fn; void *ctx; int64_t lo, hi; } gg_piece;
+
+static void *gg_piece_run(void *arg) {
+    gg_piece *p = (gg_piece *)arg;
+    p->fn(p->ctx, p->lo, p->hi);
+    return NULL;
+}
+
+static int gg_threads(void) {
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    const char *env = getenv("GG_THREADS");
+    if (env && atoi(env) > 0) c = atoi(env);
+    if (c < 1) c = 1;
+    if (c > 64) c = 64;
+    return (int)c;
+}
+
+/* Runs fn over [0, k) in up to gg_threads() pieces (inline when small); a
+ * piece whose thread cannot be started runs on the calling thread. */
+static void gg_parallel(gg_range_fn fn, void *ctx, int64_t k) {
+    int t = gg_threads();
+    if (k < 65536 || t == 1) { fn(ctx, 0, k); return; }
+    pthread_t th[64];
+    gg_piece pc[64];
+    int joined[64] = {0};
+    for (int i = 0; i < t; ++i) {
+        pc[i].fn = fn; pc[i].ctx = ctx;
+        pc[i].lo = k * i / t; pc[i].hi = k * (i + 1) / t;
+    }
+    for (int i = 1; i < t; ++i)
+        joined[i] = pthread_create(&th[i], NULL, gg_piece_run, &pc[i]) == 0;
+    gg_piece_run(&pc[0]);
+    for (int i = 1; i < t; ++i) {
+        if (joined[i]) pthread_join(th[i], NULL);
+        else gg_piece_run(&pc[i]);
+    }
+}
 
 static inline uint64_t sm64_next(uint64_t *x) {
     uint64_t z = (*x += 0x9e3779b97f4a7c15ULL);
@@ -59,30 +103,46 @@ void gg_uniform(int64_t k, uint64_t bound, uint64_t seed, int64_t *out) {
  * 32 bits of a SplitMix64 draw. Self-loops and duplicates are left in; the
  * CSR builder removes them.
  */
-void gg_rmat_edges(int scale, int64_t m, double a, double b, double c,
-                   uint64_t seed, int32_t *u, int32_t *v) {
-    const double two32 = 4294967296.0;
-    uint64_t ta = (uint64_t)(a * two32);
-    uint64_t tab = (uint64_t)((a + b) * two32);
-    uint64_t tabc = (uint64_t)((a + b + c) * two32);
-    for (int64_t e = 0; e < m; ++e) {
-        uint64_t x = sm64_stream(seed, (uint64_t)e);
+typedef struct {
+    int scale;
+    uint64_t ta, tab, tabc, seed;
+    int32_t *u, *v;
+} gg_rmat_ctx;
+
+static void gg_rmat_range(void *c, int64_t lo, int64_t hi) {
+    const gg_rmat_ctx *k = (const gg_rmat_ctx *)c;
+    for (int64_t e = lo; e < hi; ++e) {
+        uint64_t x = sm64_stream(k->seed, (uint64_t)e);
         uint32_t uu = 0, vv = 0;
         uint64_t bits = 0;
-        for (int l = 0; l < scale; ++l) {
+        for (int l = 0; l < k->scale; ++l) {
             if ((l & 1) == 0) bits = sm64_next(&x);
             uint64_t r = (l & 1) ? (bits >> 32) : (bits & 0xffffffffULL);
             uint32_t bu, bv;
-            if (r < ta) { bu = 0; bv = 0; }
-            else if (r < tab) { bu = 0; bv = 1; }
-            else if (r < tabc) { bu = 1; bv = 0; }
+            if (r < k->ta) { bu = 0; bv = 0; }
+            else if (r < k->tab) { bu = 0; bv = 1; }
+            else if (r < k->tabc) { bu = 1; bv = 0; }
             else { bu = 1; bv = 1; }
             uu = (uu << 1) | bu;
             vv = (vv << 1) | bv;
         }
-        u[e] = (int32_t)uu;
-        v[e] = (int32_t)vv;
+        k->u[e] = (int32_t)uu;
+        k->v[e] = (int32_t)vv;
     }
+}
+
+void gg_rmat_edges(int scale, int64_t m, double a, double b, double c,
+                   uint64_t seed, int32_t *u, int32_t *v) {
+    const double two32 = 4294967296.0;
+    gg_rmat_ctx k;
+    k.scale = scale;
+    k.ta = (uint64_t)(a * two32);
+    k.tab = (uint64_t)((a + b) * two32);
+    k.tabc = (uint64_t)((a + b + c) * two32);
+    k.seed = seed;
+    k.u = u;
+    k.v = v;
+    gg_parallel(gg_rmat_range, &k, m);
 }
 
 /* ---- symmetric CSR construction --------------------------------------- */
@@ -111,6 +171,62 @@ static void rsort_i32(int32_t *a, int32_t *tmp, int64_t k) {
     /* four passes: result is back in a */
 }
 
+typedef struct {
+    int64_t n, m;
+    const int32_t *u, *v;
+    int64_t *cur;   /* per row: count (cols == NULL) or next free slot */
+    int32_t *cols;  /* NULL: count only */
+} gg_scatter_ctx;
+
+static void gg_scatter_range(void *c, int64_t r0, int64_t r1) {
+    const gg_scatter_ctx *k = (const gg_scatter_ctx *)c;
+    for (int64_t e = 0; e < k->m; ++e) {
+        int32_t a = k->u[e], b = k->v[e];
+        if (a == b) continue;
+        if (a >= r0 && a < r1) {
+            if (k->cols) k->cols[k->cur[a]] = b;
+            k->cur[a]++;
+        }
+        if (b >= r0 && b < r1) {
+            if (k->cols) k->cols[k->cur[b]] = a;
+            k->cur[b]++;
+        }
+    }
+}
+
+typedef struct {
+    const int64_t *offsets;  /* row starts before compaction (offsets[i+1] = end of row i) */
+    int32_t *cols;
+    int64_t *deg;            /* out: row length after deduplication */
+} gg_rows_ctx;
+
+static void gg_rows_range(void *c, int64_t lo_row, int64_t hi_row) {
+    const gg_rows_ctx *k = (const gg_rows_ctx *)c;
+    int64_t cap = 0;
+    int32_t *tmp = NULL;
+    for (int64_t i = lo_row; i < hi_row; ++i) {
+        int64_t lo = k->offsets[i], d = k->offsets[i + 1] - lo;
+        int32_t *row = k->cols + lo;
+        if (d <= 64) {
+            isort_i32(row, d);
+        } else {
+            if (d > cap) {
+                free(tmp);
+                cap = d;
+                tmp = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+            }
+            rsort_i32(row, tmp, d);
+        }
+        int64_t w = 0;
+        for (int64_t j = 0; j < d; ++j) {
+            if (w > 0 && row[w - 1] == row[j]) continue;
+            row[w++] = row[j];
+        }
+        k->deg[i] = w;
+    }
+    free(tmp);
+}
+
 /*
  * Build the symmetric CSR of an undirected edge list over vertices [0, n).
  * Self-loops are dropped; both arcs of every edge are stored; each row is
@@ -121,44 +237,34 @@ static void rsort_i32(int32_t *a, int32_t *tmp, int64_t k) {
  */
 int64_t gg_build_csr(int64_t n, int64_t m, const int32_t *u, const int32_t *v,
                      int64_t *offsets, int32_t *cols) {
+    for (int64_t e = 0; e < m; ++e)
+        if (u[e] < 0 || v[e] < 0 || u[e] >= n || v[e] >= n) return -1;
     int64_t *cur = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     if (!cur) return -2;
-    for (int64_t e = 0; e < m; ++e) {
-        int32_t a = u[e], b = v[e];
-        if (a < 0 || b < 0 || a >= n || b >= n) { free(cur); return -1; }
-        if (a == b) continue;
-        cur[a]++; cur[b]++;
-    }
+    /* row lengths, then the arcs scattered into their rows; every thread owns
+     * a range of rows and scans the whole edge list for them */
+    gg_scatter_ctx sc = {n, m, u, v, cur, NULL};
+    gg_parallel(gg_scatter_range, &sc, n);
     offsets[0] = 0;
     for (int64_t i = 0; i < n; ++i) offsets[i + 1] = offsets[i] + cur[i];
     for (int64_t i = 0; i < n; ++i) cur[i] = offsets[i];
-    for (int64_t e = 0; e < m; ++e) {
-        int32_t a = u[e], b = v[e];
-        if (a == b) continue;
-        cols[cur[a]++] = b;
-        cols[cur[b]++] = a;
-    }
-    /* sort each row, then dedup and compact */
-    int64_t maxdeg = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        int64_t d = offsets[i + 1] - offsets[i];
-        if (d > maxdeg) maxdeg = d;
-    }
-    int32_t *tmp = maxdeg > 64 ? (int32_t *)malloc((size_t)maxdeg * sizeof(int32_t)) : NULL;
+    sc.cols = cols;
+    gg_parallel(gg_scatter_range, &sc, n);
+    /* sort and deduplicate every row in place (rows in parallel), then
+     * compact the rows to the front */
+    int64_t *deg = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    if (!deg) { free(cur); return -2; }
+    gg_rows_ctx rc = {offsets, cols, deg};
+    gg_parallel(gg_rows_range, &rc, n);
     int64_t w = 0;
     for (int64_t i = 0; i < n; ++i) {
-        int64_t lo = offsets[i], hi = offsets[i + 1], d = hi - lo;
-        int32_t *row = cols + lo;
-        if (d <= 64) isort_i32(row, d); else rsort_i32(row, tmp, d);
-        int64_t start = w;
-        for (int64_t k = 0; k < d; ++k) {
-            if (w > start && cols[w - 1] == row[k]) continue;
-            cols[w++] = row[k];
-        }
-        offsets[i] = start;
+        int64_t lo = offsets[i], d = deg[i];
+        if (w != lo) memmove(cols + w, cols + lo, (size_t)d * sizeof(int32_t));
+        offsets[i] = w;
+        w += d;
     }
     offsets[n] = w;
-    free(tmp);
+    free(deg);
     free(cur);
     return w;
 }

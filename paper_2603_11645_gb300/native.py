@@ -33,7 +33,8 @@ def _run(cmd):
 
 
 def build_generator() -> str:
-    _run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", GEN_SRC, "-o", GEN_LIB])
+    _run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-pthread", "-D_DEFAULT_SOURCE",
+          GEN_SRC, "-o", GEN_LIB, "-lpthread"])
     return GEN_LIB
 
 

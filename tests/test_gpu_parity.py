@@ -192,6 +192,9 @@ def test_grid256_all_outputs(grid256):
     assert np.array_equal(rst.build(off, col, g.root, "bfs").cpu().numpy(),
                           oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
     assert rst.verify(off, col, g.root, torch.from_numpy(want).cuda()) == 0
+    pr = rst.build(off, col, g.root, "pr_rst")
+    assert np.array_equal(pr.cpu().numpy(), oracle.prrst(g.n, g.offsets, g.cols, g.root)[0])
+    assert rst.verify(off, col, g.root, pr) == 0
 
 
 @pytest.fixture(scope="module")
@@ -212,6 +215,20 @@ def test_grid4096_cc_euler_and_bfs(grid4096):
     assert np.array_equal(bpar, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
 
 
+@pytest.mark.slow
+def test_grid4096_prrst(grid4096):
+    """PR-RST on the full-size high-diameter workload (the graph and launch
+    configuration the benchmark times), bit-exact against the oracle's
+    round-by-round simulation, and a valid RST."""
+    g = grid4096
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    got = rst.build(off, col, g.root, "pr_rst")
+    want, rounds = oracle.prrst(g.n, g.offsets, g.cols, g.root)
+    assert np.array_equal(got.cpu().numpy(), want)
+    assert rst.verify(off, col, g.root, got) == 0
+
+
 @pytest.fixture(scope="module")
 def rmat24():
     return graphs.workload_rmat24()
@@ -227,6 +244,19 @@ def test_rmat24_cc_euler(rmat24):
     assert np.array_equal(got.cpu().numpy(), want)
     bpar = rst.build(off, col, g.root, "bfs").cpu().numpy()
     assert np.array_equal(bpar, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+
+
+@pytest.mark.slow
+def test_rmat24_prrst(rmat24):
+    """PR-RST on the power-law workload (int64 offsets, a hub of ~8M extra
+    arcs), bit-exact against the oracle, and a valid RST."""
+    g = rmat24
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    got = rst.build(off, col, g.root, "pr_rst")
+    want, rounds = oracle.prrst(g.n, g.offsets, g.cols, g.root)
+    assert np.array_equal(got.cpu().numpy(), want)
+    assert rst.verify(off, col, g.root, got) == 0
 
 
 # ------------------------------------------------------------------ PR-RST

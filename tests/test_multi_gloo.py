@@ -35,6 +35,16 @@ def _worker(rank, world, port, q):
         shards = multi.lpt_shards([g.A for g in b.graphs], world)
         mine = shards[rank]
         sub = graphs.pack_batch([b.graphs[i] for i in mine])
+        # the rank's packed shard holds exactly its graphs: the oracle's tree
+        # of every graph read back from the packed arrays equals the one of
+        # the original graph
+        import oracle
+        for j, gi in enumerate(mine):
+            g = b.graphs[gi]
+            o, c = sub.graph_offsets(j), sub.graph_cols(j)
+            assert int(sub.roots[j]) == g.root
+            assert np.array_equal(oracle.rst(g.n, o, c, int(sub.roots[j])),
+                                  oracle.rst(g.n, g.offsets, g.cols, g.root))
         tot = torch.tensor([float(sub.m), float(len(mine))], dtype=torch.float64)
         dist.all_reduce(tot)
         gathered = [None] * world
@@ -79,3 +89,26 @@ def test_lpt_split_is_balanced_and_deterministic():
 def test_single_process_needs_no_group():
     assert multi.max_over_ranks(3.5) == 3.5
     assert multi.whole_job_rate(10.0, 1, 2.0) == 5.0
+
+
+def test_bench_starts_one_rank_per_gpu():
+    """`bench.py --gpus 2` without a launcher starts two ranks itself; rank 0
+    alone prints the JSON line, with n_gpus = 2 (the reference arm runs on
+    the host, so this works without a GPU)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    import bench
+    cmd = bench.launch_command(["--gpus", "2"], 2, 12345)
+    assert cmd[:3] == [sys.executable, "-m", "torch.distributed.run"]
+    assert "--nproc-per-node=2" in cmd and "127.0.0.1" in cmd and cmd[-2:] == ["--gpus", "2"]
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, env=env,
+                       timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["n_gpus"] == 2 and line["impl"] == "reference" and line["value"] > 0
