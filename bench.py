@@ -376,6 +376,12 @@ def run_ours(args, rank, world, local_rank):
     bfs_med = statistics.median(bfs_ms)
     ms_step = total_ms / args.steps
 
+    # the same search with the level loop on the device (no host round trip per level)
+    c0 = L.rst_launch_count()
+    step("bfs_device")
+    bfsd_launches = L.rst_launch_count() - c0
+    bfsd_med = _time(lambda: step("bfs_device"), args.bfs_steps, torch, dev, stream, flush)
+
     # PR-RST on the same graph
     pr_ms = []
     step("pr_rst")
@@ -441,8 +447,12 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "clocks": clk,
             "bfs": {"value": g.m / (bfs_med / 1e3), "unit": "edges/s", "ms_per_step": bfs_med,
-                    "levels": int(bfs_levels),
+                    "levels": int(bfs_levels), "loop": "host reads the frontier size every level",
                     "cc_euler_speedup": bfs_med / ms_step},
+            "bfs_device": {"value": g.m / (bfsd_med / 1e3), "unit": "edges/s", "ms_per_step": bfsd_med,
+                           "levels": int(bfs_levels), "launches": int(bfsd_launches),
+                           "loop": "one kernel per level inside a CUDA-graph while loop",
+                           "cc_euler_speedup": bfsd_med / ms_step},
             "pr_rst": {"value": g.m / (pr_med / 1e3), "unit": "edges/s", "ms_per_step": pr_med,
                        "cc_euler_speedup": pr_med / ms_step},
             "cc_fast": {"value": g.m / (fast_ms / 1e3), "unit": "edges/s", "ms_per_step": fast_ms,

@@ -64,7 +64,8 @@ typedef enum {
     RST_BFS = 1,       /* level-synchronous, direction-optimising BFS (III-A)  */
     RST_CC_EULER = 2,  /* hook/compress connectivity + Euler-tour rooting      */
     RST_PR_RST = 3,    /* path-reversal RST (III-C)                            */
-    RST_CC_FAST = 4    /* sampled union-find connectivity + Euler rooting      */
+    RST_CC_FAST = 4,   /* sampled union-find connectivity + Euler rooting      */
+    RST_BFS_DEVICE = 5 /* RST_BFS with the level loop on the device (III-A)    */
 } rst_strategy;
 
 /* Verdict codes written by rst_verify (the smallest failing code wins). */
@@ -93,7 +94,11 @@ int rst_version(void);
  *               III-D), RST_BFS (Section III-A), RST_PR_RST (Section III-C) or
  *               RST_AUTO (rst_select's choice).
  *   parent_out: n int32 (device), receives P.
- *               RST_CC_FAST: connectivity by sampled union-find hooking
+ *               RST_BFS_DEVICE: the same search and result as RST_BFS with
+               the level loop driven from the device (one kernel launch per
+               level inside a CUDA-graph while loop, no host round trip per
+               level): the stronger step-bound baseline.
+               RST_CC_FAST: connectivity by sampled union-find hooking
  *               (Section III-B leaves the hooking rule open; this one links
  *               every vertex with its first two neighbours, then only the
  *               vertices outside the largest component with the rest of

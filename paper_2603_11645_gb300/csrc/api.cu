@@ -128,6 +128,8 @@ rst_status rst_build(const void* csr_offsets, int offsets_bits, const int32_t* c
                                      nullptr, s);
     case RST_BFS:
       return run_bfs(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, nullptr, s);
+    case RST_BFS_DEVICE:
+      return run_bfs_device(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, nullptr, s);
     case RST_PR_RST:
       return run_prrst(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, s);
     case RST_CC_FAST:
@@ -237,6 +239,7 @@ rst_status rst_tree_depth(const int32_t* parent, int64_t n, int32_t* depth_out, 
 rst_status rst_shutdown(void) {
   CallGuard g;
   destroy_round_graphs();
+  destroy_bfs_graphs();
   DeviceState& st = state();
   if (st.ws) cudaFree(st.ws);
   if (st.status) cudaFree(st.status);

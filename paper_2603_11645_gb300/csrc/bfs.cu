@@ -332,6 +332,571 @@ rst_status run_bfs(const void* off, int offsets_bits, const int32_t* cols, int64
   return bfs_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, level_out, s);
 }
 
+// ------------------------------------------------------------------ device-driven BFS
+//
+// The same search (same levels, same minimum-id parents, leftover components
+// from their minimum vertex) with the level loop on the device: the body of a
+// CUDA-graph while node is one kernel per level, and the last block of each
+// launch decides the next step (top-down, bottom-up, or the seek for the next
+// component's minimum vertex) and sets the loop condition.  No host
+// synchronisation per level.
+//
+// Top-down expansion gathers Merrill-style in three tiers: rows of up to 32
+// arcs are walked by their own thread, rows of up to one block by a warp,
+// longer rows by the whole block; rows longer than kBigDeg are queued apart
+// when discovered and expanded by several blocks (a group of kGroupBlocks per
+// row, the whole grid for rows of kHugeDeg or more).  Frontier entries carry
+// the row start and degree read when the vertex was discovered, so the next
+// level reads no offsets.
+
+constexpr uint32_t kBigDeg = 4096;
+constexpr uint32_t kHugeDeg = 1u << 18;
+constexpr int kGroupBlocks = 16;
+constexpr unsigned long long kSeekWindow0 = 1ull << 16;
+
+struct __align__(16) FEntry {
+  int32_t v;
+  uint32_t deg;
+  int64_t start;
+};
+
+enum { BD_TD = 0, BD_BU = 1, BD_SEEK = 2, BD_DONE = 3 };
+
+struct BfsDevCtl {
+  int L;     // level of the frontier being expanded
+  int mode;  // BD_*
+  int par;   // parity of the frontier queues
+  int bu_div;
+  long long cap;                 // level cap (0: none)
+  unsigned long long max_iters;  // bound on loop iterations
+  unsigned long long nf;         // frontier entries (short rows)
+  unsigned long long nbig;       // frontier entries (long rows)
+  unsigned long long nn;         // next frontier, short rows (append counter)
+  unsigned long long nbn;        // next frontier, long rows (append counter)
+  unsigned long long cursor;     // every vertex below it is visited
+  unsigned long long window;     // seek window length
+  unsigned long long seek_min;   // smallest unvisited vertex found by a seek
+  unsigned long long iters;      // loop iterations so far
+  unsigned long long levels;     // levels expanded over all searches
+  unsigned int done;             // blocks of the current launch that finished
+};
+
+// The fields one launch reads (a register copy of the control block).
+struct BfsStep {
+  int L, mode, par;
+  unsigned long long nf, nbig, cursor, window;
+};
+
+template <class OffT>
+struct BfsDevArgs {
+  const OffT* off;
+  const int32_t* col;
+  int64_t n;
+  int32_t* level;
+  int32_t* parent;
+  FEntry* q[2];
+  FEntry* big[2];
+  int64_t bigcap;
+  BfsDevCtl* ctl;
+  uint32_t* status;
+};
+
+// Visit arc u -> v of a top-down step (valid lanes only) and append v to the
+// next frontier when this arc reached it first.  Warp-collective: every lane
+// of the warp calls it.
+template <class OffT>
+__device__ __forceinline__ void bfsd_visit(const BfsDevArgs<OffT>& a, int32_t L, int nxt, bool valid,
+                                           int32_t v, int32_t u) {
+  bool fresh = false;
+  int64_t vs = 0;
+  uint32_t vd = 0;
+  if (valid) {
+    if (v < 0 || (int64_t)v >= a.n) {
+      raise_error(a.status, DERR_INDEX);
+    } else {
+      const int32_t old = atomicCAS(&a.level[v], -1, L + 1);
+      if (old == -1 || old == L + 1) atomicMin(&a.parent[v], u);
+      fresh = old == -1;
+      if (fresh) {
+        vs = (int64_t)a.off[v];
+        vd = (uint32_t)((int64_t)a.off[v + 1] - vs);
+      }
+    }
+  }
+  const bool big = fresh && vd > kBigDeg;
+  const bool norm = fresh && !big;
+  const long long slot = warp_reserve(&a.ctl->nn, norm);
+  if (norm) {
+    FEntry e;
+    e.v = v;
+    e.deg = vd;
+    e.start = vs;
+    a.q[nxt][slot] = e;
+  }
+  if (big) {
+    const unsigned long long b = atomicAdd(&a.ctl->nbn, 1ull);
+    if ((int64_t)b < a.bigcap) {
+      FEntry e;
+      e.v = v;
+      e.deg = vd;
+      e.start = vs;
+      a.big[nxt][b] = e;
+    } else {
+      raise_error(a.status, DERR_CAPACITY);
+    }
+  }
+}
+
+template <class OffT>
+__device__ __forceinline__ void bfsd_top_down(const BfsDevArgs<OffT>& a, const BfsStep& c) {
+  __shared__ FEntry s_e[kBlock];
+  __shared__ int s_owner;
+  __shared__ int32_t s_u;
+  __shared__ int64_t s_j, s_hi;
+  const int32_t L = c.L;
+  const int par = c.par, nxt = par ^ 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // long rows: loaded a block's worth at a time; a row of kHugeDeg or more is
+  // walked by the whole grid, any other by one group of kGroupBlocks blocks
+  const int64_t nbig = (int64_t)c.nbig;
+  const FEntry* __restrict__ bq = a.big[par];
+  const int groups = gridDim.x >= kGroupBlocks ? (int)(gridDim.x / kGroupBlocks) : 1;
+  const int gsize = gridDim.x >= kGroupBlocks ? kGroupBlocks : (int)gridDim.x;
+  const int my_group = (int)(blockIdx.x / gsize);
+  const int64_t gstride = (int64_t)gsize * blockDim.x;
+  for (int64_t b0 = 0; b0 < nbig; b0 += blockDim.x) {
+    if (b0 + threadIdx.x < nbig) s_e[threadIdx.x] = bq[b0 + threadIdx.x];
+    __syncthreads();
+    const int cnt = (int)(nbig - b0 < (int64_t)blockDim.x ? nbig - b0 : (int64_t)blockDim.x);
+    for (int r = 0; r < cnt; ++r) {
+      const FEntry e = s_e[r];
+      int64_t first, step;
+      if (e.deg >= kHugeDeg) {
+        first = (int64_t)blockIdx.x * blockDim.x;
+        step = stride;
+      } else if ((int)((b0 + r) % groups) == my_group && my_group < groups) {
+        first = (int64_t)(blockIdx.x - (unsigned)my_group * gsize) * blockDim.x;
+        step = gstride;
+      } else {
+        continue;
+      }
+      for (int64_t k0 = first + (threadIdx.x & ~31); k0 < (int64_t)e.deg; k0 += step) {
+        const int64_t k = k0 + lane;
+        const bool valid = k < (int64_t)e.deg;
+        bfsd_visit(a, L, nxt, valid, valid ? a.col[e.start + k] : 0, e.v);
+      }
+    }
+    __syncthreads();
+  }
+  // short rows: thread, warp and block tiers
+  const int64_t nf = (int64_t)c.nf;
+  const FEntry* __restrict__ q = a.q[par];
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nf; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    int32_t u = -1;
+    int64_t j = 0, hi = 0;
+    if (i < nf) {
+      const FEntry e = q[i];
+      u = e.v;
+      j = e.start;
+      hi = e.start + (int64_t)e.deg;
+    }
+    while (true) {  // block tier: rows longer than a block
+      if (threadIdx.x == 0) s_owner = -1;
+      __syncthreads();
+      if (hi - j > (int64_t)blockDim.x) s_owner = (int)threadIdx.x;
+      __syncthreads();
+      const int owner = s_owner;
+      if (owner < 0) break;
+      if ((int)threadIdx.x == owner) {
+        s_u = u;
+        s_j = j;
+        s_hi = hi;
+        j = hi;
+      }
+      __syncthreads();
+      const int32_t cu = s_u;
+      const int64_t cj = s_j, chi = s_hi;
+      for (int64_t k0 = cj; k0 < chi; k0 += blockDim.x) {
+        const int64_t k = k0 + threadIdx.x;
+        const bool valid = k < chi;
+        bfsd_visit(a, L, nxt, valid, valid ? a.col[k] : 0, cu);
+      }
+      __syncthreads();
+    }
+    while (true) {  // warp tier: rows longer than 32 arcs
+      const unsigned m = __ballot_sync(0xffffffffu, hi - j > 32);
+      if (!m) break;
+      const int leader = __ffs(m) - 1;
+      const int32_t wu = __shfl_sync(0xffffffffu, u, leader);
+      const int64_t wj = __shfl_sync(0xffffffffu, j, leader);
+      const int64_t whi = __shfl_sync(0xffffffffu, hi, leader);
+      if (lane == leader) j = hi;
+      for (int64_t k0 = wj; k0 < whi; k0 += 32) {
+        const int64_t k = k0 + lane;
+        const bool valid = k < whi;
+        bfsd_visit(a, L, nxt, valid, valid ? a.col[k] : 0, wu);
+      }
+    }
+    // thread tier: at most 32 arcs each
+    const int rem = (int)(hi - j);
+    int mx = rem;
+    for (int d = 16; d > 0; d >>= 1) {
+      const int o = __shfl_xor_sync(0xffffffffu, mx, d);
+      mx = o > mx ? o : mx;
+    }
+    for (int t = 0; t < mx; ++t) {
+      const bool valid = t < rem;
+      bfsd_visit(a, L, nxt, valid, valid ? a.col[j + t] : 0, u);
+    }
+  }
+}
+
+// Bottom-up: each unvisited vertex takes the first neighbour of its sorted
+// row on level L (the minimum-id one).  Its level is written at once: L + 1
+// is never mistaken for L by a neighbour in the same step.
+template <class OffT>
+__device__ __forceinline__ void bfsd_bottom_up(const BfsDevArgs<OffT>& a, const BfsStep& c) {
+  const int32_t L = c.L;
+  const int nxt = c.par ^ 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+    const int64_t v = base + threadIdx.x;
+    bool fresh = false;
+    int64_t lo = 0, hi = 0;
+    if (v < a.n && a.level[v] == -1) {
+      lo = (int64_t)a.off[v];
+      hi = (int64_t)a.off[v + 1];
+      for (int64_t j = lo; j < hi; ++j) {
+        const int32_t u = a.col[j];
+        if (u < 0 || (int64_t)u >= a.n) {
+          raise_error(a.status, DERR_INDEX);
+          break;
+        }
+        if (a.level[u] == L) {
+          a.parent[v] = u;
+          a.level[v] = L + 1;
+          fresh = true;
+          break;
+        }
+      }
+    }
+    const uint32_t deg = (uint32_t)(hi - lo);
+    const bool big = fresh && deg > kBigDeg;
+    const bool norm = fresh && !big;
+    const long long slot = warp_reserve(&a.ctl->nn, norm);
+    FEntry e;
+    e.v = (int32_t)v;
+    e.deg = deg;
+    e.start = lo;
+    if (norm) a.q[nxt][slot] = e;
+    if (big) {
+      const unsigned long long b = atomicAdd(&a.ctl->nbn, 1ull);
+      if ((int64_t)b < a.bigcap)
+        a.big[nxt][b] = e;
+      else
+        raise_error(a.status, DERR_CAPACITY);
+    }
+  }
+}
+
+// The smallest unvisited vertex in the current seek window.
+template <class OffT>
+__device__ __forceinline__ void bfsd_seek(const BfsDevArgs<OffT>& a, const BfsStep& c) {
+  const int64_t lo = (int64_t)c.cursor;
+  const int64_t hi = lo + (int64_t)c.window < a.n ? lo + (int64_t)c.window : a.n;
+  unsigned long long best = ~0ull;
+  for (int64_t v = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < hi;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (a.level[v] == -1) {
+      best = (unsigned long long)v;
+      break;  // grid-stride order: a thread's first hit is its smallest
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, best, d);
+    best = o < best ? o : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&a.ctl->seek_min, best);
+}
+
+// Starts the search at `src` (a vertex with edges, level already -1 or set).
+template <class OffT>
+__device__ void bfsd_seed(const BfsDevArgs<OffT>& a, BfsDevCtl* c, int32_t src) {
+  a.level[src] = 0;
+  a.parent[src] = src;
+  FEntry e;
+  e.v = src;
+  e.start = (int64_t)a.off[src];
+  e.deg = (uint32_t)((int64_t)a.off[src + 1] - e.start);
+  c->L = 0;
+  if (e.deg > kBigDeg) {
+    a.big[c->par][0] = e;
+    c->nbig = 1;
+    c->nf = 0;
+  } else {
+    a.q[c->par][0] = e;
+    c->nf = 1;
+    c->nbig = 0;
+  }
+  c->mode = (1 > a.n / c->bu_div) ? BD_BU : BD_TD;
+}
+
+template <class OffT>
+__global__ void k_bfsd_start(BfsDevArgs<OffT> a, int32_t root, int bu_div, long long cap,
+                             unsigned long long max_iters) {
+  BfsDevCtl* c = a.ctl;
+  c->par = 0;
+  c->bu_div = bu_div;
+  c->cap = cap;
+  c->max_iters = max_iters;
+  c->nn = c->nbn = 0;
+  c->cursor = 0;
+  c->window = kSeekWindow0;
+  c->seek_min = ~0ull;
+  c->iters = 0;
+  c->levels = 0;
+  c->done = 0;
+  c->nf = c->nbig = 0;
+  c->L = 0;
+  if (a.off[root + 1] - a.off[root] > 0) {
+    bfsd_seed(a, c, root);
+  } else {
+    c->mode = BD_SEEK;  // an isolated root is already its own tree
+  }
+}
+
+// After a launch (one thread): the next step and the loop condition.
+template <class OffT>
+__device__ void bfsd_finish(const BfsDevArgs<OffT>& a, cudaGraphConditionalHandle h, int use_handle) {
+  BfsDevCtl* c = a.ctl;
+  const int mode = c->mode;
+  bool more = true;
+  c->iters += 1;
+  if (mode == BD_TD || mode == BD_BU) {
+    c->levels += 1;
+    const unsigned long long nn = c->nn, nb = c->nbn;
+    if (nn + nb > 0) {
+      const int L2 = c->L + 1;
+      if (c->cap > 0 && (long long)L2 >= c->cap) {
+        raise_error(a.status, DERR_ROUND_LIMIT);
+        more = false;
+      }
+      c->L = L2;
+      c->par ^= 1;
+      c->nf = nn;
+      c->nbig = nb;
+      c->mode = ((long long)(nn + nb) > a.n / c->bu_div) ? BD_BU : BD_TD;
+    } else {
+      c->nf = c->nbig = 0;
+      c->window = kSeekWindow0;
+      c->mode = BD_SEEK;
+    }
+  } else if (mode == BD_SEEK) {
+    const unsigned long long m = c->seek_min;
+    if (m != ~0ull) {
+      bfsd_seed(a, c, (int32_t)m);
+      c->cursor = m + 1;
+    } else {
+      c->cursor += c->window;
+      c->window = c->window * 2 < (unsigned long long)a.n ? c->window * 2 : (unsigned long long)a.n;
+      if (c->cursor >= (unsigned long long)a.n) {
+        c->mode = BD_DONE;
+        more = false;
+      }
+    }
+  } else {
+    more = false;
+  }
+  if (c->iters >= c->max_iters && more) {
+    raise_error(a.status, DERR_ROUND_LIMIT);
+    more = false;
+  }
+  c->nn = 0;
+  c->nbn = 0;
+  c->seek_min = ~0ull;
+  c->done = 0;
+  if (!more) c->mode = BD_DONE;
+  if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+template <class OffT>
+__global__ void __launch_bounds__(kBlock) k_bfsd_step(BfsDevArgs<OffT> a, cudaGraphConditionalHandle h,
+                                                      int use_handle) {
+  // the step's fields, read before any block can finish the launch
+  BfsStep c;
+  c.mode = a.ctl->mode;
+  c.L = a.ctl->L;
+  c.par = a.ctl->par;
+  c.nf = a.ctl->nf;
+  c.nbig = a.ctl->nbig;
+  c.cursor = a.ctl->cursor;
+  c.window = a.ctl->window;
+  if (c.mode == BD_TD)
+    bfsd_top_down(a, c);
+  else if (c.mode == BD_BU)
+    bfsd_bottom_up(a, c);
+  else if (c.mode == BD_SEEK)
+    bfsd_seek(a, c);
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&a.ctl->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    bfsd_finish(a, h, use_handle);
+  }
+}
+
+static int bfsd_grid() { return device_info().sms * 8; }
+
+size_t bfs_device_workspace_bytes(int64_t n, int64_t A) {
+  Arena a;
+  a.counting = true;
+  a.take<int32_t>(n);
+  a.take<FEntry>(n + 1);
+  a.take<FEntry>(n + 1);
+  a.take<FEntry>(A / kBigDeg + 2);
+  a.take<FEntry>(A / kBigDeg + 2);
+  a.take<BfsDevCtl>(1);
+  return a.used;
+}
+
+// One instantiated while-loop graph per binding of buffers and grid.
+struct BfsGraph {
+  bool valid = false;
+  const void* key_off = nullptr;
+  const void* key_col = nullptr;
+  const void* key_ctl = nullptr;
+  const void* key_parent = nullptr;
+  const void* key_level = nullptr;
+  int64_t key_n = 0;
+  int key_dev = -1, key_grid = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+constexpr int kBfsGraphCache = 4;
+static BfsGraph g_bfs_graphs[kBfsGraphCache];
+static int g_bfs_graph_next = 0;
+static cudaStream_t g_bfs_capture[64] = {};
+
+void destroy_bfs_graphs() {
+  for (auto& g : g_bfs_graphs) {
+    if (g.valid && g.exec) cudaGraphExecDestroy(g.exec);
+    g = BfsGraph{};
+  }
+}
+
+template <class OffT>
+static rst_status bfsd_graph_for(const BfsDevArgs<OffT>& a, cudaGraphExec_t* out) {
+  int dev = 0;
+  RST_CUDA(cudaGetDevice(&dev));
+  const int grid = bfsd_grid();
+  for (auto& g : g_bfs_graphs)
+    if (g.valid && g.key_off == a.off && g.key_col == a.col && g.key_ctl == a.ctl &&
+        g.key_parent == a.parent && g.key_level == a.level && g.key_n == a.n && g.key_dev == dev &&
+        g.key_grid == grid) {
+      *out = g.exec;
+      return RST_OK;
+    }
+  if (dev < 0 || dev >= 64) return RST_ERR_UNSUPPORTED;
+  if (!g_bfs_capture[dev]) RST_CUDA(cudaStreamCreateWithFlags(&g_bfs_capture[dev], cudaStreamNonBlocking));
+  cudaStream_t cs = g_bfs_capture[dev];
+  cudaGraph_t graph = nullptr;
+  RST_CUDA(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h;
+  RST_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  RST_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  RST_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  k_bfsd_step<OffT><<<grid, kBlock, 0, cs>>>(a, h, 1);
+  cudaGraph_t captured = nullptr;
+  RST_CUDA(cudaStreamEndCapture(cs, &captured));
+  cudaGraphExec_t exec = nullptr;
+  RST_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  RST_CUDA(cudaGraphDestroy(graph));
+  BfsGraph& slot = g_bfs_graphs[g_bfs_graph_next];
+  g_bfs_graph_next = (g_bfs_graph_next + 1) % kBfsGraphCache;
+  if (slot.valid && slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot.valid = true;
+  slot.key_off = a.off;
+  slot.key_col = a.col;
+  slot.key_ctl = a.ctl;
+  slot.key_parent = a.parent;
+  slot.key_level = a.level;
+  slot.key_n = a.n;
+  slot.key_dev = dev;
+  slot.key_grid = grid;
+  slot.exec = exec;
+  *out = exec;
+  return RST_OK;
+}
+
+template <class OffT>
+static rst_status bfs_device_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
+                                  int32_t* parent, int32_t* level_out, cudaStream_t s) {
+  RST_TRY(ensure_workspace(bfs_device_workspace_bytes(n, A)));
+  RST_TRY(reset_device_error(s));
+  DeviceState& st = state();
+  Arena ar{st.ws, st.ws_cap, 0, false};
+  BfsDevArgs<OffT> a;
+  a.off = off;
+  a.col = col;
+  a.n = n;
+  int32_t* lv = ar.take<int32_t>(n);
+  a.level = level_out ? level_out : lv;
+  a.parent = parent;
+  a.q[0] = ar.take<FEntry>(n + 1);
+  a.q[1] = ar.take<FEntry>(n + 1);
+  a.bigcap = A / kBigDeg + 2;
+  a.big[0] = ar.take<FEntry>(a.bigcap);
+  a.big[1] = ar.take<FEntry>(a.bigcap);
+  a.ctl = ar.take<BfsDevCtl>(1);
+  a.status = st.status;
+  if (ar.used > ar.cap) return RST_ERR_OOM;
+  unsigned long long* cnt = dev_counter(0);
+  RST_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
+  RST_LAUNCH(k_bfs_init<OffT>, grid_for(n), kBlock, 0, s)(off, n, a.level, parent, cnt);
+  const unsigned long long max_iters = 4ull * (unsigned long long)n + 1024;
+  RST_LAUNCH(k_bfsd_start<OffT>, 1, 1, 0, s)(a, root, tuning().bfs_bu_div, g_bfs_max_levels, max_iters);
+  static const bool eager = getenv("RST_EAGER") != nullptr;
+  if (!eager) {
+    cudaGraphExec_t exec = nullptr;
+    RST_TRY(bfsd_graph_for<OffT>(a, &exec));
+    RST_CUDA(cudaGraphLaunch(exec, s));
+  } else {
+    for (unsigned long long it = 0; it < max_iters + 1; ++it) {
+      RST_LAUNCH(k_bfsd_step<OffT>, bfsd_grid(), kBlock, 0, s)(a, cudaGraphConditionalHandle{}, 0);
+      RST_CUDA(cudaGetLastError());
+      unsigned long long w = 0;
+      RST_TRY(fetch_u64(reinterpret_cast<const unsigned long long*>(&a.ctl->L), 1, &w, s));
+      if ((int)(w >> 32) == BD_DONE) break;  // {L, mode} read as one word
+    }
+  }
+  RST_CUDA(cudaGetLastError());
+  unsigned long long h[2];
+  RST_TRY(fetch_u64(&a.ctl->iters, 2, h, s));
+  if (!eager) count_launches((long long)h[0]);
+  set_stat(STAT_LEVELS, (long long)h[1]);
+  return read_device_error(s);
+}
+
+rst_status run_bfs_device(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
+                          int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s) {
+  if (offsets_bits == 32)
+    return bfs_device_impl<int32_t>((const int32_t*)off, cols, n, m, root, parent, level_out, s);
+  return bfs_device_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, level_out, s);
+}
+
 rst_status bfs_probe_in(Arena& ar, const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                         int32_t root, int32_t* parent_scratch, BfsProbe* probe, cudaStream_t s) {
   if (offsets_bits == 32)

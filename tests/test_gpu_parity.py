@@ -139,6 +139,65 @@ def test_bfs_edge_cases(g):
     assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
 
 
+@pytest.mark.parametrize("gi", range(N_SMALL))
+def test_bfs_device_parent_small(gi):
+    """The device-driven level loop gives the oracle's BFS tree."""
+    g = _small()[gi]
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    par = rst.build(off, col, g.root, "bfs_device").cpu().numpy()
+    assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]), g.name
+
+
+@pytest.mark.parametrize("g", edge_cases(), ids=_ids(edge_cases()))
+def test_bfs_device_edge_cases(g):
+    import paper_2603_11645_gb300 as rst
+    off, col = dev(g)
+    par = rst.build(off, col, g.root, "bfs_device").cpu().numpy()
+    assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+
+
+def test_bfs_device_long_rows_and_many_components():
+    """Rows longer than one block and than the long-row threshold (a star
+    centre with 300,000 leaves, a hub of 5,000), both search directions, and
+    components found by the device-side seek far apart in id order."""
+    import paper_2603_11645_gb300 as rst
+    n = 400_000
+    u = [0] * 300_000 + [300_001] * 5_000 + list(range(350_000, 399_999))
+    v = list(range(1, 300_001)) + list(range(300_002, 305_002)) + list(range(350_001, 400_000))
+    # a few isolated vertices and two-vertex components in the gaps
+    u += [310_000, 320_000, 340_000]
+    v += [310_001, 320_002, 345_000]
+    for root in (0, 300_001, 350_500, 310_000, 305_500):
+        g = graphs.from_edges(n, u, v, name="hubs", root=root)
+        off, col = dev(g)
+        want = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
+        for div in (20, 1, 10**6):  # default, always top-down, always bottom-up
+            rst.set_option("bfs_bottom_up_divisor", div)
+            try:
+                par = rst.build(off, col, g.root, "bfs_device").cpu().numpy()
+            finally:
+                rst.set_option("bfs_bottom_up_divisor", 20)
+            assert np.array_equal(par, want), (root, div)
+
+
+def test_bfs_device_level_cap():
+    """The level cap ends the device loop with an error status, and the next
+    call without a cap is exact again."""
+    import paper_2603_11645_gb300 as rst
+    g = graphs.chain_chords(5000, 0.0, seed=3)
+    off, col = dev(g)
+    rst.set_option("bfs_max_levels", 100)
+    try:
+        with pytest.raises(rst.RstError) as e:
+            rst.build(off, col, g.root, "bfs_device")
+        assert e.value.code == 4
+    finally:
+        rst.set_option("bfs_max_levels", 0)
+    par = rst.build(off, col, g.root, "bfs_device").cpu().numpy()
+    assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+
+
 @pytest.mark.parametrize("gi", [0, 3, 6, 8, 10, 12, 15])
 def test_verify_matches_oracle(gi):
     g = _small()[gi]
@@ -189,8 +248,9 @@ def test_grid256_all_outputs(grid256):
     par, rank = rst.euler_root(g.n, uv, g.root)
     s, d, r, p = oracle.euler_tour(g.n, tu, tv, g.root)
     assert np.array_equal(rank.cpu().numpy(), r)
-    assert np.array_equal(rst.build(off, col, g.root, "bfs").cpu().numpy(),
-                          oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+    wb = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
+    assert np.array_equal(rst.build(off, col, g.root, "bfs").cpu().numpy(), wb)
+    assert np.array_equal(rst.build(off, col, g.root, "bfs_device").cpu().numpy(), wb)
     assert rst.verify(off, col, g.root, torch.from_numpy(want).cuda()) == 0
     pr = rst.build(off, col, g.root, "pr_rst")
     assert np.array_equal(pr.cpu().numpy(), oracle.prrst(g.n, g.offsets, g.cols, g.root)[0])
@@ -211,8 +271,10 @@ def test_grid4096_cc_euler_and_bfs(grid4096):
     got = rst.build(off, col, g.root, "cc_euler")
     assert np.array_equal(got.cpu().numpy(), want)
     assert rst.verify(off, col, g.root, got) == 0
+    wb = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
     bpar = rst.build(off, col, g.root, "bfs").cpu().numpy()
-    assert np.array_equal(bpar, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+    assert np.array_equal(bpar, wb)
+    assert np.array_equal(rst.build(off, col, g.root, "bfs_device").cpu().numpy(), wb)
 
 
 @pytest.mark.slow
@@ -242,8 +304,10 @@ def test_rmat24_cc_euler(rmat24):
     want = oracle.rst(g.n, g.offsets, g.cols, g.root)
     got = rst.build(off, col, g.root, "cc_euler")
     assert np.array_equal(got.cpu().numpy(), want)
+    wb = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
     bpar = rst.build(off, col, g.root, "bfs").cpu().numpy()
-    assert np.array_equal(bpar, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
+    assert np.array_equal(bpar, wb)
+    assert np.array_equal(rst.build(off, col, g.root, "bfs_device").cpu().numpy(), wb)
 
 
 @pytest.mark.slow
