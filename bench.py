@@ -376,11 +376,17 @@ def run_ours(args, rank, world, local_rank):
     bfs_med = statistics.median(bfs_ms)
     ms_step = total_ms / args.steps
 
-    # the same search with the level loop on the device (no host round trip per level)
-    c0 = L.rst_launch_count()
-    step("bfs_device")
-    bfsd_launches = L.rst_launch_count() - c0
-    bfsd_med = _time(lambda: step("bfs_device"), args.bfs_steps, torch, dev, stream, flush)
+    # the same search with the level loop on the device (no host round trip per
+    # level): one launch per level inside a CUDA-graph while node, and one
+    # persistent cooperative launch for all levels
+    dev_bfs = {}
+    for strat in ("bfs_device", "bfs_persistent"):
+        c0 = L.rst_launch_count()
+        step(strat)
+        nl = L.rst_launch_count() - c0
+        dev_bfs[strat] = (_time(lambda: step(strat), args.bfs_steps, torch, dev, stream, flush), nl)
+    bfsd_med, bfsd_launches = dev_bfs["bfs_device"]
+    bfsp_med, bfsp_launches = dev_bfs["bfs_persistent"]
 
     # PR-RST on the same graph
     pr_ms = []
@@ -453,6 +459,10 @@ def run_ours(args, rank, world, local_rank):
                            "levels": int(bfs_levels), "launches": int(bfsd_launches),
                            "loop": "one kernel per level inside a CUDA-graph while loop",
                            "cc_euler_speedup": bfsd_med / ms_step},
+            "bfs_persistent": {"value": g.m / (bfsp_med / 1e3), "unit": "edges/s", "ms_per_step": bfsp_med,
+                               "levels": int(bfs_levels), "launches": int(bfsp_launches),
+                               "loop": "all levels in one cooperative launch, a grid barrier per level",
+                               "cc_euler_speedup": bfsp_med / ms_step},
             "pr_rst": {"value": g.m / (pr_med / 1e3), "unit": "edges/s", "ms_per_step": pr_med,
                        "cc_euler_speedup": pr_med / ms_step},
             "cc_fast": {"value": g.m / (fast_ms / 1e3), "unit": "edges/s", "ms_per_step": fast_ms,
@@ -613,7 +623,7 @@ def run_families(args, dev, stream, rst, graphs, torch, peak, cpu_on):
                        f"deduplicated, connected to 0, int64 offsets, root 0: {g.n} vertices, "
                        f"{g.m} edges ({g.A} arcs)", "n": g.n, "m": g.m}
     L = rst.lib()
-    for strat in ("cc_euler", "bfs", "bfs_device", "pr_rst", "cc_fast"):
+    for strat in ("cc_euler", "bfs", "bfs_device", "bfs_persistent", "pr_rst", "cc_fast"):
         if strat not in rst.STRATEGIES:
             continue
         reps = max(3, min(args.steps, 10)) if strat == "cc_euler" else 3
@@ -649,7 +659,7 @@ def run_grid256(args, dev, stream, rst, graphs, torch, cpu_on):
     L = rst.lib()
     out = {"workload": "grid 256x256 4-neighbour, ids permuted by seed 1, root = permuted corner, "
                        "int32 CSR (65,536 vertices, 130,560 edges)", "n": g.n, "m": g.m}
-    for strat in ("cc_euler", "bfs", "bfs_device", "pr_rst"):
+    for strat in ("cc_euler", "bfs", "bfs_device", "bfs_persistent", "pr_rst"):
         if strat not in rst.STRATEGIES:
             continue
         rst.build(off, col, g.root, strat, out=par)

@@ -65,7 +65,8 @@ typedef enum {
     RST_CC_EULER = 2,  /* hook/compress connectivity + Euler-tour rooting      */
     RST_PR_RST = 3,    /* path-reversal RST (III-C)                            */
     RST_CC_FAST = 4,   /* sampled union-find connectivity + Euler rooting      */
-    RST_BFS_DEVICE = 5 /* RST_BFS with the level loop on the device (III-A)    */
+    RST_BFS_DEVICE = 5,     /* RST_BFS, level loop in a CUDA-graph while node  */
+    RST_BFS_PERSISTENT = 6  /* RST_BFS, all levels in one cooperative launch   */
 } rst_strategy;
 
 /* Verdict codes written by rst_verify (the smallest failing code wins). */
@@ -98,6 +99,10 @@ int rst_version(void);
                the level loop driven from the device (one kernel launch per
                level inside a CUDA-graph while loop, no host round trip per
                level): the stronger step-bound baseline.
+               RST_BFS_PERSISTENT: the same search and result again, all
+               levels inside one cooperative kernel launch whose blocks meet
+               at a grid barrier after each level (bounded waits: a wait that
+               runs out returns RST_ERR_NOT_CONVERGED).
                RST_CC_FAST: connectivity by sampled union-find hooking
  *               (Section III-B leaves the hooking rule open; this one links
  *               every vertex with its first two neighbours, then only the

@@ -16,7 +16,8 @@ __all__ = ["build", "build_batch", "cc", "euler_root", "verify", "tree_depth", "
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librst.so")
 
-STRATEGIES = {"auto": 0, "bfs": 1, "cc_euler": 2, "pr_rst": 3, "cc_fast": 4, "bfs_device": 5}
+STRATEGIES = {"auto": 0, "bfs": 1, "cc_euler": 2, "pr_rst": 3, "cc_fast": 4, "bfs_device": 5,
+              "bfs_persistent": 6}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "iteration bound exceeded", 5: "timeout", 6: "unsupported", 7: "device-detected error"}
 

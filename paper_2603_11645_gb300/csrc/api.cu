@@ -129,7 +129,9 @@ rst_status rst_build(const void* csr_offsets, int offsets_bits, const int32_t* c
     case RST_BFS:
       return run_bfs(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, nullptr, s);
     case RST_BFS_DEVICE:
-      return run_bfs_device(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, nullptr, s);
+      return run_bfs_device(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, nullptr, s, false);
+    case RST_BFS_PERSISTENT:
+      return run_bfs_device(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, nullptr, s, true);
     case RST_PR_RST:
       return run_prrst(csr_offsets, offsets_bits, csr_cols, n, m, root, parent_out, s);
     case RST_CC_FAST:

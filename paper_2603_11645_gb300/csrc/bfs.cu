@@ -379,6 +379,8 @@ struct BfsDevCtl {
   unsigned long long iters;      // loop iterations so far
   unsigned long long levels;     // levels expanded over all searches
   unsigned int done;             // blocks of the current launch that finished
+  unsigned int arrive;           // persistent variant: blocks at the level barrier
+  unsigned int gen;              // persistent variant: barrier generation
 };
 
 // The fields one launch reads (a register copy of the control block).
@@ -658,6 +660,8 @@ __global__ void k_bfsd_start(BfsDevArgs<OffT> a, int32_t root, int bu_div, long 
   c->iters = 0;
   c->levels = 0;
   c->done = 0;
+  c->arrive = 0;
+  c->gen = 0;
   c->nf = c->nbig = 0;
   c->L = 0;
   if (a.off[root + 1] - a.off[root] > 0) {
@@ -668,7 +672,7 @@ __global__ void k_bfsd_start(BfsDevArgs<OffT> a, int32_t root, int bu_div, long 
 }
 
 // After a launch (one thread): the next step and the loop condition.
-template <class OffT>
+template <class OffT, bool kGraph>
 __device__ void bfsd_finish(const BfsDevArgs<OffT>& a, cudaGraphConditionalHandle h, int use_handle) {
   BfsDevCtl* c = a.ctl;
   const int mode = c->mode;
@@ -718,7 +722,9 @@ __device__ void bfsd_finish(const BfsDevArgs<OffT>& a, cudaGraphConditionalHandl
   c->seek_min = ~0ull;
   c->done = 0;
   if (!more) c->mode = BD_DONE;
-  if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
+  if constexpr (kGraph) {
+    if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
 }
 
 template <class OffT>
@@ -748,11 +754,68 @@ __global__ void __launch_bounds__(kBlock) k_bfsd_step(BfsDevArgs<OffT> a, cudaGr
   __syncthreads();
   if (s_last && threadIdx.x == 0) {
     __threadfence();
-    bfsd_finish(a, h, use_handle);
+    bfsd_finish<OffT, true>(a, h, use_handle);
   }
 }
 
-static int bfsd_grid() { return device_info().sms * 8; }
+// Persistent variant: one cooperative launch (every block resident) runs all
+// levels.  Blocks meet at a grid barrier after each level; the last block to
+// arrive decides the next step and releases the others by advancing the
+// barrier generation.  Every wait is bounded: a block that waits longer than
+// kBarrierSpins polls gives up, sets DERR_ROUND_LIMIT and leaves, and so do
+// the others in turn.
+constexpr unsigned long long kBarrierSpins = 1ull << 25;
+
+template <class OffT>
+__global__ void __launch_bounds__(kBlock) k_bfsp(BfsDevArgs<OffT> a) {
+  __shared__ int s_stop;
+  BfsDevCtl* ctl = a.ctl;
+  for (;;) {
+    BfsStep c;
+    c.mode = *(volatile int*)&ctl->mode;
+    c.L = *(volatile int*)&ctl->L;
+    c.par = *(volatile int*)&ctl->par;
+    c.nf = *(volatile unsigned long long*)&ctl->nf;
+    c.nbig = *(volatile unsigned long long*)&ctl->nbig;
+    c.cursor = *(volatile unsigned long long*)&ctl->cursor;
+    c.window = *(volatile unsigned long long*)&ctl->window;
+    if (c.mode == BD_DONE) break;
+    if (c.mode == BD_TD)
+      bfsd_top_down(a, c);
+    else if (c.mode == BD_BU)
+      bfsd_bottom_up(a, c);
+    else
+      bfsd_seek(a, c);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_stop = 0;
+      const unsigned int gen = *(volatile unsigned int*)&ctl->gen;
+      __threadfence();
+      if (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1) {
+        __threadfence();
+        ctl->arrive = 0;
+        bfsd_finish<OffT, false>(a, cudaGraphConditionalHandle{}, 0);
+        __threadfence();
+        atomicAdd(&ctl->gen, 1u);  // release
+      } else {
+        unsigned long long spins = 0;
+        while (*(volatile unsigned int*)&ctl->gen == gen) {
+          if (++spins > kBarrierSpins) {
+            raise_error(a.status, DERR_ROUND_LIMIT);
+            s_stop = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+  }
+}
+
+static int bfsd_grid() { return device_info().sms * tuning().bfsd_bps; }
 
 size_t bfs_device_workspace_bytes(int64_t n, int64_t A) {
   Arena a;
@@ -841,9 +904,21 @@ static rst_status bfsd_graph_for(const BfsDevArgs<OffT>& a, cudaGraphExec_t* out
   return RST_OK;
 }
 
+// Grid of the persistent variant: as many resident blocks as fit (capped by
+// the tuning knob), so that a cooperative launch can hold them all.
+template <class OffT>
+static rst_status bfsp_grid(int* grid) {
+  int per_sm = 0;
+  RST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfsp<OffT>, kBlock, 0));
+  if (per_sm < 1) return RST_ERR_UNSUPPORTED;
+  const int want = tuning().bfsp_bps;
+  *grid = device_info().sms * (per_sm < want ? per_sm : want);
+  return RST_OK;
+}
+
 template <class OffT>
 static rst_status bfs_device_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
-                                  int32_t* parent, int32_t* level_out, cudaStream_t s) {
+                                  int32_t* parent, int32_t* level_out, cudaStream_t s, bool persistent) {
   RST_TRY(ensure_workspace(bfs_device_workspace_bytes(n, A)));
   RST_TRY(reset_device_error(s));
   DeviceState& st = state();
@@ -869,7 +944,13 @@ static rst_status bfs_device_impl(const OffT* off, const int32_t* col, int64_t n
   const unsigned long long max_iters = 4ull * (unsigned long long)n + 1024;
   RST_LAUNCH(k_bfsd_start<OffT>, 1, 1, 0, s)(a, root, tuning().bfs_bu_div, g_bfs_max_levels, max_iters);
   static const bool eager = getenv("RST_EAGER") != nullptr;
-  if (!eager) {
+  if (persistent) {
+    int grid = 0;
+    RST_TRY(bfsp_grid<OffT>(&grid));
+    void* params[] = {&a};
+    count_launch();
+    RST_CUDA(cudaLaunchCooperativeKernel((const void*)k_bfsp<OffT>, dim3(grid), dim3(kBlock), params, 0, s));
+  } else if (!eager) {
     cudaGraphExec_t exec = nullptr;
     RST_TRY(bfsd_graph_for<OffT>(a, &exec));
     RST_CUDA(cudaGraphLaunch(exec, s));
@@ -885,16 +966,16 @@ static rst_status bfs_device_impl(const OffT* off, const int32_t* col, int64_t n
   RST_CUDA(cudaGetLastError());
   unsigned long long h[2];
   RST_TRY(fetch_u64(&a.ctl->iters, 2, h, s));
-  if (!eager) count_launches((long long)h[0]);
+  if (!eager && !persistent) count_launches((long long)h[0]);
   set_stat(STAT_LEVELS, (long long)h[1]);
   return read_device_error(s);
 }
 
 rst_status run_bfs_device(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
-                          int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s) {
+                          int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s, bool persistent) {
   if (offsets_bits == 32)
-    return bfs_device_impl<int32_t>((const int32_t*)off, cols, n, m, root, parent, level_out, s);
-  return bfs_device_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, level_out, s);
+    return bfs_device_impl<int32_t>((const int32_t*)off, cols, n, m, root, parent, level_out, s, persistent);
+  return bfs_device_impl<int64_t>((const int64_t*)off, cols, n, m, root, parent, level_out, s, persistent);
 }
 
 rst_status bfs_probe_in(Arena& ar, const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,

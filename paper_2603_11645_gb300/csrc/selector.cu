@@ -467,6 +467,16 @@ rst_status rst_set_option(const char* key, long long value) {
     t.round_bps = (int)value;
     return RST_OK;
   }
+  if (std::strcmp(key, "bfs_device_blocks_per_sm") == 0) {
+    if (value < 1 || value > 8) return RST_ERR_INVALID_ARG;
+    tuning().bfsd_bps = (int)value;
+    return RST_OK;
+  }
+  if (std::strcmp(key, "bfs_persistent_blocks_per_sm") == 0) {
+    if (value < 1 || value > 8) return RST_ERR_INVALID_ARG;
+    tuning().bfsp_bps = (int)value;
+    return RST_OK;
+  }
   if (std::strcmp(key, "bfs_bottom_up_divisor") == 0) {
     if (value < 1 || value > 1000000) return RST_ERR_INVALID_ARG;
     t.bfs_bu_div = (int)value;
@@ -482,6 +492,8 @@ rst_status rst_get_option(const char* key, long long* value) {
   else if (std::strcmp(key, "lr_spacing") == 0) *value = 1LL << t.lr_shift;
   else if (std::strcmp(key, "round_blocks_per_sm") == 0) *value = t.round_bps;
   else if (std::strcmp(key, "bfs_bottom_up_divisor") == 0) *value = t.bfs_bu_div;
+  else if (std::strcmp(key, "bfs_device_blocks_per_sm") == 0) *value = t.bfsd_bps;
+  else if (std::strcmp(key, "bfs_persistent_blocks_per_sm") == 0) *value = t.bfsp_bps;
   else return RST_ERR_INVALID_ARG;
   return RST_OK;
 }

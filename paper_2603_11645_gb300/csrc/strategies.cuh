@@ -10,10 +10,13 @@ namespace rst {
 rst_status run_bfs(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                    int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s);
 
-// The same search with the level loop on the device (one kernel per level
-// inside a CUDA-graph while node; no host synchronisation per level).
+// The same search with the level loop on the device: one kernel per level
+// inside a CUDA-graph while node, or (persistent) one cooperative launch whose
+// blocks meet at a bounded grid barrier after each level.  No host
+// synchronisation per level.
 rst_status run_bfs_device(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
-                          int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s);
+                          int32_t root, int32_t* parent, int32_t* level_out, cudaStream_t s,
+                          bool persistent);
 void destroy_bfs_graphs();
 
 // A bounded BFS from the root (the selector's probe): frontier sizes of the

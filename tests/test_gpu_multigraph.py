@@ -80,6 +80,7 @@ def test_multigraph_all_strategies(seed):
     lev, want_bfs = oracle.bfs(n, off_h, col_h, root)
     assert np.array_equal(rst.build(off, col, root, "bfs").cpu().numpy(), want_bfs)
     assert np.array_equal(rst.build(off, col, root, "bfs_device").cpu().numpy(), want_bfs)
+    assert np.array_equal(rst.build(off, col, root, "bfs_persistent").cpu().numpy(), want_bfs)
 
     want_pr, _ = oracle.prrst(n, off_h, col_h, root)
     assert np.array_equal(rst.build(off, col, root, "pr_rst").cpu().numpy(), want_pr)

@@ -139,25 +139,32 @@ def test_bfs_edge_cases(g):
     assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
 
 
+DEVICE_BFS = ("bfs_device", "bfs_persistent")
+
+
+@pytest.mark.parametrize("strategy", DEVICE_BFS)
 @pytest.mark.parametrize("gi", range(N_SMALL))
-def test_bfs_device_parent_small(gi):
-    """The device-driven level loop gives the oracle's BFS tree."""
+def test_bfs_device_parent_small(gi, strategy):
+    """The device-driven level loops (graph while node; persistent kernel)
+    give the oracle's BFS tree."""
     g = _small()[gi]
     import paper_2603_11645_gb300 as rst
     off, col = dev(g)
-    par = rst.build(off, col, g.root, "bfs_device").cpu().numpy()
+    par = rst.build(off, col, g.root, strategy).cpu().numpy()
     assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]), g.name
 
 
+@pytest.mark.parametrize("strategy", DEVICE_BFS)
 @pytest.mark.parametrize("g", edge_cases(), ids=_ids(edge_cases()))
-def test_bfs_device_edge_cases(g):
+def test_bfs_device_edge_cases(g, strategy):
     import paper_2603_11645_gb300 as rst
     off, col = dev(g)
-    par = rst.build(off, col, g.root, "bfs_device").cpu().numpy()
+    par = rst.build(off, col, g.root, strategy).cpu().numpy()
     assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
 
 
-def test_bfs_device_long_rows_and_many_components():
+@pytest.mark.parametrize("strategy", DEVICE_BFS)
+def test_bfs_device_long_rows_and_many_components(strategy):
     """Rows longer than one block and than the long-row threshold (a star
     centre with 300,000 leaves, a hub of 5,000), both search directions, and
     components found by the device-side seek far apart in id order."""
@@ -180,13 +187,14 @@ def test_bfs_device_long_rows_and_many_components():
                 continue
             rst.set_option("bfs_bottom_up_divisor", div)
             try:
-                par = rst.build(off, col, g.root, "bfs_device").cpu().numpy()
+                par = rst.build(off, col, g.root, strategy).cpu().numpy()
             finally:
                 rst.set_option("bfs_bottom_up_divisor", 20)
             assert np.array_equal(par, want), (root, div)
 
 
-def test_bfs_device_level_cap():
+@pytest.mark.parametrize("strategy", DEVICE_BFS)
+def test_bfs_device_level_cap(strategy):
     """The level cap ends the device loop with an error status, and the next
     call without a cap is exact again."""
     import paper_2603_11645_gb300 as rst
@@ -195,11 +203,11 @@ def test_bfs_device_level_cap():
     rst.set_option("bfs_max_levels", 100)
     try:
         with pytest.raises(rst.RstError) as e:
-            rst.build(off, col, g.root, "bfs_device")
+            rst.build(off, col, g.root, strategy)
         assert e.value.code == 4
     finally:
         rst.set_option("bfs_max_levels", 0)
-    par = rst.build(off, col, g.root, "bfs_device").cpu().numpy()
+    par = rst.build(off, col, g.root, strategy).cpu().numpy()
     assert np.array_equal(par, oracle.bfs(g.n, g.offsets, g.cols, g.root)[1])
 
 
@@ -255,7 +263,8 @@ def test_grid256_all_outputs(grid256):
     assert np.array_equal(rank.cpu().numpy(), r)
     wb = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
     assert np.array_equal(rst.build(off, col, g.root, "bfs").cpu().numpy(), wb)
-    assert np.array_equal(rst.build(off, col, g.root, "bfs_device").cpu().numpy(), wb)
+    for strategy in DEVICE_BFS:
+        assert np.array_equal(rst.build(off, col, g.root, strategy).cpu().numpy(), wb), strategy
     assert rst.verify(off, col, g.root, torch.from_numpy(want).cuda()) == 0
     pr = rst.build(off, col, g.root, "pr_rst")
     assert np.array_equal(pr.cpu().numpy(), oracle.prrst(g.n, g.offsets, g.cols, g.root)[0])
@@ -279,7 +288,8 @@ def test_grid4096_cc_euler_and_bfs(grid4096):
     wb = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
     bpar = rst.build(off, col, g.root, "bfs").cpu().numpy()
     assert np.array_equal(bpar, wb)
-    assert np.array_equal(rst.build(off, col, g.root, "bfs_device").cpu().numpy(), wb)
+    for strategy in DEVICE_BFS:
+        assert np.array_equal(rst.build(off, col, g.root, strategy).cpu().numpy(), wb), strategy
 
 
 @pytest.mark.slow
@@ -312,7 +322,8 @@ def test_rmat24_cc_euler(rmat24):
     wb = oracle.bfs(g.n, g.offsets, g.cols, g.root)[1]
     bpar = rst.build(off, col, g.root, "bfs").cpu().numpy()
     assert np.array_equal(bpar, wb)
-    assert np.array_equal(rst.build(off, col, g.root, "bfs_device").cpu().numpy(), wb)
+    for strategy in DEVICE_BFS:
+        assert np.array_equal(rst.build(off, col, g.root, strategy).cpu().numpy(), wb), strategy
 
 
 @pytest.mark.slow
