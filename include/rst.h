@@ -324,7 +324,11 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *                             the hook and resolve kernels take at most 6 and
  *                             5, the blocks their registers let reside);
  *     "bfs_bottom_up_divisor" BFS steps bottom-up while the frontier holds more
- *                             than n / divisor vertices, [1, 10^6] (default 20).
+ *                             than n / divisor vertices, [1, 10^6] (default 20);
+ *     "bfs_device_blocks_per_sm"     grid of RST_BFS_DEVICE's level kernel in
+ *                             256-thread blocks per SM, [1, 8] (default 2);
+ *     "bfs_persistent_blocks_per_sm" grid of RST_BFS_PERSISTENT, at most this
+ *                             many resident blocks per SM, [1, 8] (default 1).
  *   Out-of-range values and unknown keys return RST_ERR_INVALID_ARG and change
  *   nothing.  Options are process-wide: set them between calls, not during.
  * rst_get_option: reads the current value of any key above into *value (host). */

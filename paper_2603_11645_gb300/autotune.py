@@ -8,7 +8,10 @@ launches and samples, never a result:
 * ``round_blocks_per_sm``: grid of the contraction-round kernels (the hook
   and resolve kernels cap it at the blocks their registers let reside);
 * ``bfs_bottom_up_divisor``: BFS steps bottom-up while the frontier holds more
-  than n / divisor vertices.
+  than n / divisor vertices;
+* ``bfs_device_blocks_per_sm`` / ``bfs_persistent_blocks_per_sm``: the grid of
+  the device-driven BFS variants (a small grid keeps the per-level cost of
+  deep, narrow searches low; a large one feeds the wide bottom-up levels).
 
 They stand where Section III-C fixes its own launch granularity empirically
 (five pointer jumps per global synchronisation for PR-RST).  ``tune`` times
@@ -31,10 +34,14 @@ KNOBS = {
     "round_blocks_per_sm": [2, 4, 8, 16],
     "lr_spacing": [16, 32, 64, 128, 256, 512],
     "bfs_bottom_up_divisor": [5, 10, 20, 40, 80],
+    "bfs_device_blocks_per_sm": [1, 2, 4, 8],
+    "bfs_persistent_blocks_per_sm": [1, 2, 4],
 }
-DEFAULTS = {"round_blocks_per_sm": 8, "lr_spacing": 16, "bfs_bottom_up_divisor": 20}
+DEFAULTS = {"round_blocks_per_sm": 8, "lr_spacing": 16, "bfs_bottom_up_divisor": 20,
+            "bfs_device_blocks_per_sm": 2, "bfs_persistent_blocks_per_sm": 1}
 # the strategy whose time decides each knob
-KNOB_STRATEGY = {"round_blocks_per_sm": "cc_euler", "lr_spacing": "cc_euler", "bfs_bottom_up_divisor": "bfs"}
+KNOB_STRATEGY = {"round_blocks_per_sm": "cc_euler", "lr_spacing": "cc_euler", "bfs_bottom_up_divisor": "bfs",
+                 "bfs_device_blocks_per_sm": "bfs_device", "bfs_persistent_blocks_per_sm": "bfs_persistent"}
 
 # size buckets by log2 n (half-open), with the log2 n of the graph tuned on
 BUCKETS = [(0, 14, 12), (14, 18, 16), (18, 22, 20), (22, 31, 24)]

@@ -362,6 +362,8 @@ struct __align__(16) FEntry {
 
 enum { BD_TD = 0, BD_BU = 1, BD_SEEK = 2, BD_DONE = 3 };
 
+// Fields that many blocks update or poll at once sit on their own 128-byte
+// lines, apart from the step description every block reads.
 struct BfsDevCtl {
   int L;     // level of the frontier being expanded
   int mode;  // BD_*
@@ -371,16 +373,16 @@ struct BfsDevCtl {
   unsigned long long max_iters;  // bound on loop iterations
   unsigned long long nf;         // frontier entries (short rows)
   unsigned long long nbig;       // frontier entries (long rows)
-  unsigned long long nn;         // next frontier, short rows (append counter)
-  unsigned long long nbn;        // next frontier, long rows (append counter)
   unsigned long long cursor;     // every vertex below it is visited
   unsigned long long window;     // seek window length
-  unsigned long long seek_min;   // smallest unvisited vertex found by a seek
   unsigned long long iters;      // loop iterations so far
   unsigned long long levels;     // levels expanded over all searches
-  unsigned int done;             // blocks of the current launch that finished
-  unsigned int arrive;           // persistent variant: blocks at the level barrier
-  unsigned int gen;              // persistent variant: barrier generation
+  alignas(128) unsigned long long nn;  // next frontier, short rows (append counter)
+  alignas(128) unsigned long long nbn;       // next frontier, long rows (append counter)
+  unsigned long long seek_min;               // smallest unvisited vertex found by a seek
+  alignas(128) unsigned int done;            // blocks of the current launch that finished
+  alignas(128) unsigned int arrive;          // persistent variant: blocks at the level barrier
+  alignas(128) unsigned int gen;             // persistent variant: barrier generation
 };
 
 // The fields one launch reads (a register copy of the control block).
@@ -445,6 +447,84 @@ __device__ __forceinline__ void bfsd_visit(const BfsDevArgs<OffT>& a, int32_t L,
       a.big[nxt][b] = e;
     } else {
       raise_error(a.status, DERR_CAPACITY);
+    }
+  }
+}
+
+// Up to kTdBatch arcs u -> col[j0 + k], k < cnt (cnt may be <= 0: no arcs):
+// the column loads, then the level claims, then the discovered vertices' row
+// bounds are issued together, and the warp reserves its queue slots once.
+// Warp-collective.
+constexpr int kTdBatch = 4;
+template <class OffT>
+__device__ __forceinline__ void bfsd_visit_batch(const BfsDevArgs<OffT>& a, int32_t L, int nxt, int32_t u,
+                                                 int64_t j0, int cnt) {
+  int32_t v[kTdBatch];
+  int32_t old[kTdBatch];
+#pragma unroll
+  for (int k = 0; k < kTdBatch; ++k) v[k] = k < cnt ? a.col[j0 + k] : -1;
+#pragma unroll
+  for (int k = 0; k < kTdBatch; ++k) {
+    old[k] = 0;
+    if (k < cnt) {
+      if (v[k] < 0 || (int64_t)v[k] >= a.n) {
+        raise_error(a.status, DERR_INDEX);
+        v[k] = -1;
+      } else {
+        old[k] = atomicCAS(&a.level[v[k]], -1, L + 1);
+      }
+    }
+  }
+  unsigned fresh = 0;
+#pragma unroll
+  for (int k = 0; k < kTdBatch; ++k)
+    if (k < cnt && v[k] >= 0) {
+      if (old[k] == -1 || old[k] == L + 1) atomicMin(&a.parent[v[k]], u);
+      if (old[k] == -1) fresh |= 1u << k;
+    }
+  int64_t vs[kTdBatch];
+  int64_t ve[kTdBatch];
+#pragma unroll
+  for (int k = 0; k < kTdBatch; ++k) {
+    vs[k] = 0;
+    ve[k] = 0;
+    if ((fresh >> k) & 1u) {
+      vs[k] = (int64_t)a.off[v[k]];
+      ve[k] = (int64_t)a.off[v[k] + 1];
+    }
+  }
+  unsigned norm = 0;
+#pragma unroll
+  for (int k = 0; k < kTdBatch; ++k)
+    if (((fresh >> k) & 1u) && ve[k] - vs[k] <= (int64_t)kBigDeg) norm |= 1u << k;
+  // one reservation per warp for every lane's short rows
+  const unsigned mine = (unsigned)__popc(norm);
+  const int lane = threadIdx.x & 31;
+  unsigned x = mine;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  const unsigned total = __shfl_sync(0xffffffffu, x, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(&a.ctl->nn, (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, 31) + (x - mine);
+#pragma unroll
+  for (int k = 0; k < kTdBatch; ++k) {
+    if (!((fresh >> k) & 1u)) continue;
+    FEntry e;
+    e.v = v[k];
+    e.deg = (uint32_t)(ve[k] - vs[k]);
+    e.start = vs[k];
+    if ((norm >> k) & 1u) {
+      a.q[nxt][base++] = e;
+    } else {
+      const unsigned long long b = atomicAdd(&a.ctl->nbn, 1ull);
+      if ((int64_t)b < a.bigcap)
+        a.big[nxt][b] = e;
+      else
+        raise_error(a.status, DERR_CAPACITY);
     }
   }
 }
@@ -541,17 +621,15 @@ __device__ __forceinline__ void bfsd_top_down(const BfsDevArgs<OffT>& a, const B
         bfsd_visit(a, L, nxt, valid, valid ? a.col[k] : 0, wu);
       }
     }
-    // thread tier: at most 32 arcs each
+    // thread tier: at most 32 arcs each, kTdBatch at a time with all their
+    // loads and atomics in flight together
     const int rem = (int)(hi - j);
     int mx = rem;
     for (int d = 16; d > 0; d >>= 1) {
       const int o = __shfl_xor_sync(0xffffffffu, mx, d);
       mx = o > mx ? o : mx;
     }
-    for (int t = 0; t < mx; ++t) {
-      const bool valid = t < rem;
-      bfsd_visit(a, L, nxt, valid, valid ? a.col[j + t] : 0, u);
-    }
+    for (int t0 = 0; t0 < mx; t0 += kTdBatch) bfsd_visit_batch(a, L, nxt, u, j + t0, rem - t0);
   }
 }
 

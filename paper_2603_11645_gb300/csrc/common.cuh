@@ -82,7 +82,7 @@ struct Tuning {
   int round_bps = 8;    // contraction-round kernels: resident blocks per SM in the grid (1..16)
   int bfs_bu_div = 20;  // BFS steps bottom-up while the frontier exceeds n / bfs_bu_div
   int bfsd_bps = 2;     // device-driven BFS: 256-thread blocks per SM in its grid (1..8)
-  int bfsp_bps = 8;     // persistent BFS: at most this many resident blocks per SM (1..8)
+  int bfsp_bps = 1;     // persistent BFS: at most this many resident blocks per SM (1..8)
 };
 Tuning& tuning();
 

@@ -33,7 +33,9 @@ def test_option_defaults_roundtrip_and_rejects(rst_lib):
     assert rst.get_option("lr_spacing") == 128
     for key, bad in [("lr_spacing", 8), ("lr_spacing", 48), ("lr_spacing", 1024),
                      ("round_blocks_per_sm", 0), ("round_blocks_per_sm", 17),
-                     ("bfs_bottom_up_divisor", 0), ("no_such_knob", 1)]:
+                     ("bfs_bottom_up_divisor", 0), ("bfs_device_blocks_per_sm", 0),
+                     ("bfs_device_blocks_per_sm", 9), ("bfs_persistent_blocks_per_sm", 0),
+                     ("no_such_knob", 1)]:
         with pytest.raises(rst.RstError):
             rst.set_option(key, bad)
     assert rst.get_option("lr_spacing") == 128  # a rejected value changes nothing
@@ -103,7 +105,9 @@ def _cases():
 
 KNOB_VALUES = [("lr_spacing", 32), ("lr_spacing", 512), ("round_blocks_per_sm", 1),
                ("round_blocks_per_sm", 16), ("bfs_bottom_up_divisor", 1),
-               ("bfs_bottom_up_divisor", 100000)]
+               ("bfs_bottom_up_divisor", 100000), ("bfs_device_blocks_per_sm", 1),
+               ("bfs_device_blocks_per_sm", 8), ("bfs_persistent_blocks_per_sm", 1),
+               ("bfs_persistent_blocks_per_sm", 8)]
 
 
 @pytest.mark.gpu
@@ -113,8 +117,9 @@ def test_knob_leaves_results_unchanged(rst_lib, knob, value):
     rst.set_option(knob, value)
     for g in _cases():
         off, col = _dev(g)
-        if knob == "bfs_bottom_up_divisor":
-            par = rst.build(off, col, g.root, "bfs").cpu().numpy()
+        strategy = AT.KNOB_STRATEGY[knob]
+        if strategy.startswith("bfs"):
+            par = rst.build(off, col, g.root, strategy).cpu().numpy()
             _, want = oracle.bfs(g.n, g.offsets, g.cols, g.root)
         else:
             par = rst.build(off, col, g.root, "cc_euler").cpu().numpy()
