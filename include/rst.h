@@ -291,19 +291,28 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  * picks the smallest, falling back to CC+Euler when the predicted advantage of
  * another strategy is below a margin.
  *
- * rst_selector_features: writes the 12 features (host float[12]) of a graph:
- *   log2 n, log2 m, mean degree, degree CV, degree skewness, log2(1+max deg),
- *   fraction of degree <= 2, log2(1+vertices reached by an 8-level BFS probe
- *   from root), log2 frontier growth between probe levels 3 and 7, log2 of an
- *   eccentricity estimate, log2(round-1 hook components / n), fraction of
- *   vertices the probe reached.
+ * rst_selector_features: writes the 12 features (host float[12]) of a graph,
+ *   computed on the device: log2 n, log2 m, mean degree, degree CV, degree
+ *   skewness, log2(1+max deg), fraction of degree <= 2, log2(1+vertices
+ *   reached by an 8-level BFS probe from root), log2 frontier growth between
+ *   probe levels 3 and 7, log2 of an eccentricity estimate, log2(round-1 hook
+ *   components / n), and the fraction of the m edges that survive one hook
+ *   pass (edges u < v whose ends lie in different round-1 components of the
+ *   min-key hooking of Section III-B).
  * rst_selector_load: installs network parameters (host float[5187]: W1[64][12],
  *   b1[64], W2[64][64], b2[64], W3[3][64], b3[3]), normalisation (host
  *   float[30]: feature means[12], feature stds[12], target means[3], target
  *   stds[3]) and the fallback margin (in log-time units).
- * rst_select: features + prediction; choice_out (host) and pred_log_time_out
- *   (host float[3], may be NULL).  Without loaded parameters it chooses
- *   RST_CC_EULER.  rst_build with RST_AUTO uses the same choice.
+ * rst_select: features, prediction and choice, all on the device; choice_out
+ *   (host) and pred_log_time_out (host float[3], may be NULL).  Without loaded
+ *   parameters it chooses RST_CC_EULER.  rst_build with RST_AUTO uses the
+ *   same choice.
+ * rst_selector_predict: the loaded network applied on the device to `batch`
+ *   feature rows (device float[batch][12], raw as rst_selector_features
+ *   writes them): pred_out (device float[batch][3] or NULL) receives the
+ *   predicted natural-log times (BFS, CC+Euler, PR-RST), choice_out (device
+ *   int32[batch] or NULL) the rst_strategy rst_select would pick.
+ *   RST_ERR_UNSUPPORTED when no parameters are loaded.
  * rst_mlp_forward / rst_mlp_loss_grad / rst_mlp_adam / rst_mlp_train: the
  *   network's FP32 forward pass, mean-squared-error loss and gradient, Adam
  *   step (Kingma & Ba) and a full-batch training loop, all on device arrays
@@ -339,6 +348,8 @@ rst_status rst_selector_load(const float *params, const float *norm, float margi
 rst_status rst_select(const void *csr_offsets, int offsets_bits, const int32_t *csr_cols, int64_t n,
                       int64_t m, int32_t root, rst_strategy *choice_out, float *pred_log_time_out,
                       rst_stream_t stream);
+rst_status rst_selector_predict(const float *features, int batch, float *pred_out, int32_t *choice_out,
+                                rst_stream_t stream);
 rst_status rst_mlp_forward(const float *params, const float *X, int batch, float *Y,
                            rst_stream_t stream);
 rst_status rst_mlp_loss_grad(const float *params, const float *X, const float *T, int batch,

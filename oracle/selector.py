@@ -2,13 +2,21 @@
 
 * ``features``: the 12 selector features from exact integer statistics of the
   CSR (degree moments, an 8-level BFS probe from the root, round-1 hook
-  components), following the definitions stated in include/rst.h.
+  components and the edges that survive that hook pass), following the
+  definitions stated in include/rst.h.
 * ``forward`` / ``loss_grad`` / ``adam_step``: the 12-64-64-3 ReLU network,
   its mean-squared-error loss and gradient (ReLU'(0) = 0), and one Adam step
   (Kingma & Ba 2015), all in float64.
+* ``predict`` / ``choose`` / ``regret``: the loaded model's float64 inference
+  (standardise, forward, un-standardise), the strategy choice with the
+  fallback margin, and the mean regret over graphs -- the checkers of the
+  library's on-device inference and of the selector's evaluation.
 
 Pins (tests/test_selector.py): central finite differences of ``loss_grad``,
-the closed form of a first Adam step, hand-computed features of small graphs.
+the closed form of a first Adam step, hand-computed features of small graphs
+(round-1 components and surviving edges of a hand-derived case), round-1
+components against a plain union-find, the choice rule on hand-built
+predictions.
 """
 from __future__ import annotations
 
@@ -106,6 +114,29 @@ def _probe(n, off, col, root, max_levels=8):
     return sizes, finished
 
 
+def first_neighbours(n, off, col):
+    """first[u] = the first entry of u's sorted row other than u (-1: none)."""
+    off = np.asarray(off, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    d = np.diff(off)
+    src = np.repeat(np.arange(n, dtype=np.int64), d)
+    idx = np.flatnonzero(col != src)
+    first = np.full(n, -1, dtype=np.int64)
+    rows, at = np.unique(src[idx], return_index=True)
+    first[rows] = col[idx[at]]
+    return first
+
+
+def round1_components(n, first):
+    """Component of every vertex in the graph of the round-1 hooks {u, first[u]}
+    (connected components of that graph; isolated vertices alone)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    u = np.flatnonzero(first >= 0)
+    a = coo_matrix((np.ones(len(u)), (u, first[u])), shape=(n, n))
+    return connected_components(a, directed=False)[1]
+
+
 def features(n, offsets, cols, root):
     off = np.asarray(offsets, dtype=np.int64)
     col = np.asarray(cols, dtype=np.int64)
@@ -147,22 +178,55 @@ def features(n, offsets, cols, root):
         fr = float(sizes[-1] if sizes[-1] > 0 else 1)
         ecc = levels + (rest / fr if rest > 0 else 0.0)
     f[9] = np.log2(1.0 + ecc)
-    # round-1 components with edges: u whose first neighbour v0 (self-loops
-    # skipped) has u as its own first neighbour, with u < v0
-    first = np.full(n, -1, dtype=np.int64)
-    for u in range(n) if n <= 4096 else []:
-        row = col[off[u]:off[u + 1]]
-        row = row[row != u]
-        if len(row):
-            first[u] = row[0]
-    if n > 4096:
-        has = d > 0
-        first[has] = col[off[:-1][has]]   # inputs of this size have no self-loops
+    # round 1 of the min-key hooking: every vertex hooks along its first
+    # neighbour other than itself (the smallest key, rows being sorted)
+    first = first_neighbours(n, off, col)
     u = np.arange(n)
     ok = first >= 0
     mutual = np.zeros(n, bool)
     mutual[ok] = first[first[ok]] == u[ok]
-    c1 = int((mutual & ok & (u < first)).sum())
+    c1 = int((mutual & ok & (u < first)).sum())   # components with edges: one mutual pair each
     f[10] = np.log2(max(c1, 1) / N)
-    f[11] = reached / N
+    comp = round1_components(n, first)
+    src = np.repeat(np.arange(n, dtype=np.int64), d)
+    keep = src < col
+    f[11] = float((comp[src[keep]] != comp[col[keep]]).sum()) / m if m > 0 else 0.0
     return f
+
+
+# ------------------------------------------------------------------ inference and evaluation
+
+def predict(params, norm, X):
+    """Predicted natural-log times of the model (params, norm = feature means,
+    feature stds, target means, target stds) for raw feature rows X."""
+    norm = np.asarray(norm, dtype=np.float64)
+    xm, xs, ym, ys = norm[:F], norm[F:2 * F], norm[2 * F:2 * F + O], norm[2 * F + O:]
+    xs = np.where(xs > 0, xs, 1.0)
+    ys = np.where(ys > 0, ys, 1.0)
+    y, _ = forward(params, (np.asarray(X, dtype=np.float64) - xm) / xs)
+    return y * ys + ym
+
+
+def choose(pred, margin):
+    """Index of the chosen strategy per row (0 BFS, 1 CC+Euler, 2 PR-RST): the
+    smallest prediction (the first on ties), replaced by CC+Euler when it
+    beats CC+Euler's prediction by less than the margin."""
+    pred = np.asarray(pred, dtype=np.float64)
+    out = np.empty(len(pred), dtype=np.int64)
+    for i, p in enumerate(pred):
+        best = 1
+        for k in range(O):
+            if p[k] < p[best]:
+                best = k
+        if best != 1 and p[1] - p[best] < margin:
+            best = 1
+        out[i] = best
+    return out
+
+
+def regret(times, choice):
+    """Mean over graphs of (t_chosen - t_best) / t_best."""
+    times = np.asarray(times, dtype=np.float64)
+    tb = times.min(1)
+    tc = times[np.arange(len(times)), np.asarray(choice)]
+    return float(np.mean((tc - tb) / tb))

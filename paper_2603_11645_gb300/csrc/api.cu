@@ -242,6 +242,7 @@ rst_status rst_shutdown(void) {
   CallGuard g;
   destroy_round_graphs();
   destroy_bfs_graphs();
+  release_selector();
   DeviceState& st = state();
   if (st.ws) cudaFree(st.ws);
   if (st.status) cudaFree(st.status);

@@ -7,13 +7,14 @@
 // depth-oblivious CC+Euler when the predicted margin is small.  No part of the
 // paper prescribes this network; it is a deployment addition.
 //
-// Features (float, in this order):
+// Features (float, in this order), all computed on the device:
 //   0 log2 n                       6 fraction of vertices with degree <= 2
 //   1 log2 m (undirected edges)    7 log2 (1 + vertices reached in an 8-level BFS probe)
 //   2 mean degree                  8 log2 ((1 + frontier at level 7) / (1 + frontier at level 3))
 //   3 degree coefficient of var.   9 log2 eccentricity estimate from the probe
 //   4 degree skewness             10 log2 (round-1 components / n) of the min-key hooking
-//   5 log2 (1 + max degree)       11 fraction of vertices the probe reached
+//   5 log2 (1 + max degree)       11 fraction of the edges that survive one hook pass (their
+//                                    ends lie in different round-1 components)
 #include <cmath>
 
 #include "pipeline.cuh"
@@ -82,84 +83,139 @@ __global__ void k_sel_r1roots(const OffT* __restrict__ off, const int32_t* __res
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
-struct FeatureRaw {
+// Counts of the input that determine the features (device memory): degree
+// moments, round-1 roots with edges, surviving edges, and the BFS probe's
+// frontier sizes (filled in by the host loop that drives the probe).
+struct SelRaw {
   double s1, s2, s3, le2;
-  unsigned long long maxdeg, r1roots;
+  unsigned long long maxdeg, r1roots, survive;
+  long long probe_levels, probe_finished, probe_reached, probe_last;
+  long long frontier[8];
 };
 
-static void assemble_features(int64_t n, int64_t A, const FeatureRaw& r, const BfsProbe& p, float* f) {
+// Edges u < v whose ends lie in different round-1 components (R = round-1 root).
+template <class OffT>
+__global__ void k_sel_survive(const OffT* __restrict__ off, const int32_t* __restrict__ col, int64_t n,
+                              const int32_t* __restrict__ R, unsigned long long* __restrict__ count) {
+  unsigned long long c = 0;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t ru = R[u];
+    const int64_t hi = (int64_t)off[u + 1];
+    for (int64_t j = (int64_t)off[u]; j < hi; ++j) {
+      const int32_t v = col[j];
+      if (v > (int32_t)u && (int64_t)v < n && R[v] != ru) ++c;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// The twelve features from the raw counts (one thread).
+__global__ void k_sel_assemble(int64_t n, int64_t A, const SelRaw* __restrict__ r, float* __restrict__ f) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
   const double N = (double)(n > 0 ? n : 1);
-  const double mu = r.s1 / N;
-  const double var = r.s2 / N - mu * mu;
-  const double sd = var > 0 ? std::sqrt(var) : 0.0;
-  const double m3 = r.s3 / N - 3.0 * mu * (r.s2 / N) + 2.0 * mu * mu * mu;
+  const double mu = r->s1 / N;
+  const double var = r->s2 / N - mu * mu;
+  const double sd = var > 0 ? sqrt(var) : 0.0;
+  const double m3 = r->s3 / N - 3.0 * mu * (r->s2 / N) + 2.0 * mu * mu * mu;
   const double m = (double)(A / 2);
-  f[0] = (float)std::log2(N);
-  f[1] = (float)std::log2(m > 1 ? m : 1.0);
+  f[0] = (float)log2(N);
+  f[1] = (float)log2(m > 1 ? m : 1.0);
   f[2] = (float)mu;
   f[3] = (float)(mu > 0 ? sd / mu : 0.0);
   f[4] = (float)(sd > 0 ? m3 / (sd * sd * sd) : 0.0);
-  f[5] = (float)std::log2(1.0 + (double)r.maxdeg);
-  f[6] = (float)(r.le2 / N);
-  const double reached = p.levels > 0 ? (double)p.reached : 1.0;
-  f[7] = (float)std::log2(1.0 + reached);
-  const double f3 = p.levels > 3 ? (double)p.frontier[3] : 0.0;
-  const double f7 = p.levels > 7 ? (double)p.frontier[7] : 0.0;
-  f[8] = (float)std::log2((1.0 + f7) / (1.0 + f3));
+  f[5] = (float)log2(1.0 + (double)r->maxdeg);
+  f[6] = (float)(r->le2 / N);
+  const long long levels = r->probe_levels;
+  const double reached = levels > 0 ? (double)r->probe_reached : 1.0;
+  f[7] = (float)log2(1.0 + reached);
+  const double f3 = levels > 3 ? (double)r->frontier[3] : 0.0;
+  const double f7 = levels > 7 ? (double)r->frontier[7] : 0.0;
+  f[8] = (float)log2((1.0 + f7) / (1.0 + f3));
   double ecc;
-  if (p.levels == 0 || p.finished) {
-    ecc = (double)(p.levels > 0 ? p.levels : 1);
+  if (levels == 0 || r->probe_finished) {
+    ecc = (double)(levels > 0 ? levels : 1);
   } else {
     const double rest = N - reached;
-    const double fr = (double)(p.last_frontier > 0 ? p.last_frontier : 1);
-    ecc = (double)p.levels + (rest > 0 ? rest / fr : 0.0);
+    const double fr = (double)(r->probe_last > 0 ? r->probe_last : 1);
+    ecc = (double)levels + (rest > 0 ? rest / fr : 0.0);
   }
-  f[9] = (float)std::log2(1.0 + ecc);
-  const double c1 = (double)(r.r1roots > 0 ? r.r1roots : 1);
-  f[10] = (float)std::log2(c1 / N);
-  f[11] = (float)(reached / N);
+  f[9] = (float)log2(1.0 + ecc);
+  const double c1 = (double)(r->r1roots > 0 ? r->r1roots : 1);
+  f[10] = (float)log2(c1 / N);
+  f[11] = (float)(m > 0 ? (double)r->survive / m : 0.0);
 }
 
+struct FeatBufs {
+  int32_t* parent;  // probe scratch
+  int32_t* P;       // round-1 roots
+  uint32_t* J;
+  uint4* pairs;
+  uint32_t* bits;
+  SelRaw* raw;
+  unsigned long long* cnt;  // round-1 tree-edge counter
+  float* feat;              // 12 features
+};
+
+static FeatBufs feat_layout(Arena& ar, int64_t n, int64_t A) {
+  FeatBufs b;
+  b.parent = ar.take<int32_t>(n + 1);
+  b.P = ar.take<int32_t>(n + 1);
+  b.J = ar.take<uint32_t>(n + 1);
+  b.pairs = ar.take<uint4>(n + 1);
+  b.bits = ar.take<uint32_t>(A / 32 + 2);
+  b.raw = ar.take<SelRaw>(1);
+  b.cnt = ar.take<unsigned long long>(4);
+  b.feat = ar.take<float>(16);
+  return b;
+}
+
+static size_t feat_workspace_bytes(int64_t n, int64_t A) {
+  Arena a;
+  a.counting = true;
+  feat_layout(a, n, A);
+  return a.used + bfs_workspace_bytes(n) + 1024;
+}
+
+// Features of one graph into device memory (*feat_dev, 12 floats in the
+// workspace); the BFS probe is the only host-driven part (it reads its
+// frontier sizes back, 8 levels at most).
 template <class OffT>
 static rst_status features_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root,
-                                float* feat_host, cudaStream_t s) {
-  const size_t ws = bfs_workspace_bytes(n) + (((size_t)n * 4 + 255) / 256 * 256 + 256) + 1024;
-  RST_TRY(ensure_workspace(ws));
-  RST_TRY(reset_device_error(s));
-  DeviceState& st = state();
-  Arena ar{st.ws, st.ws_cap, 0, false};
-  int32_t* scratch_parent = ar.take<int32_t>(n);
-  double* acc = ar.take<double>(4);
-  unsigned long long* ic = ar.take<unsigned long long>(2);
-  if (!acc || !ic) return RST_ERR_OOM;
-  RST_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
-  RST_CUDA(cudaMemsetAsync(ic, 0, 2 * sizeof(unsigned long long), s));
-  RST_LAUNCH(k_sel_degrees<OffT>, grid_for(n), kBlock, 0, s)(off, n, acc, ic);
-  RST_LAUNCH(k_sel_r1roots<OffT>, grid_for(n), kBlock, 0, s)(off, col, n, ic + 1);
+                                float** feat_dev, Arena& ar, cudaStream_t s) {
+  FeatBufs b = feat_layout(ar, n, A);
+  if (ar.used > ar.cap) return RST_ERR_OOM;
+  RST_CUDA(cudaMemsetAsync(b.raw, 0, sizeof(SelRaw), s));
+  RST_CUDA(cudaMemsetAsync(b.cnt, 0, 4 * sizeof(unsigned long long), s));
+  RST_CUDA(cudaMemsetAsync(b.bits, 0, (A / 32 + 2) * sizeof(uint32_t), s));
+  RST_LAUNCH(k_sel_degrees<OffT>, grid_for(n), kBlock, 0, s)(off, n, &b.raw->s1, &b.raw->maxdeg);
+  RST_LAUNCH(k_sel_r1roots<OffT>, grid_for(n), kBlock, 0, s)(off, col, n, &b.raw->r1roots);
+  RST_TRY(round1_forest<OffT>(off, col, n, b.P, b.J, b.pairs, b.bits, b.cnt, s));
+  RST_LAUNCH(k_sel_survive<OffT>, grid_for(n), kBlock, 0, s)(off, col, n, b.P, &b.raw->survive);
   RST_CUDA(cudaGetLastError());
-  FeatureRaw raw{};
-  char* hs = static_cast<char*>(host_scratch(64));
-  RST_CUDA(cudaMemcpyAsync(hs, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  RST_CUDA(cudaMemcpyAsync(hs + 32, ic, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  RST_CUDA(cudaStreamSynchronize(s));
-  std::memcpy(&raw.s1, hs, 8);
-  std::memcpy(&raw.s2, hs + 8, 8);
-  std::memcpy(&raw.s3, hs + 16, 8);
-  std::memcpy(&raw.le2, hs + 24, 8);
-  std::memcpy(&raw.maxdeg, hs + 32, 8);
-  std::memcpy(&raw.r1roots, hs + 40, 8);
   BfsProbe probe;
   probe.max_levels = 8;
   const int bits = sizeof(OffT) == 8 ? 64 : 32;
-  RST_TRY(bfs_probe_in(ar, off, bits, col, n, A, root, scratch_parent, &probe, s));
-  assemble_features(n, A, raw, probe, feat_host);
-  return read_device_error(s);
+  RST_TRY(bfs_probe_in(ar, off, bits, col, n, A, root, b.parent, &probe, s));
+  // the probe's counts join the device record (pinned staging; the copy is
+  // queued before any later read-back reuses the buffer)
+  long long* stage = reinterpret_cast<long long*>(state().hostbuf + 256);
+  stage[0] = probe.levels;
+  stage[1] = probe.finished ? 1 : 0;
+  stage[2] = probe.reached;
+  stage[3] = probe.last_frontier;
+  for (int i = 0; i < 8; ++i) stage[4 + i] = i < BfsProbe::kMax ? probe.frontier[i] : 0;
+  RST_CUDA(cudaMemcpyAsync(&b.raw->probe_levels, stage, 12 * sizeof(long long), cudaMemcpyHostToDevice, s));
+  RST_LAUNCH(k_sel_assemble, 1, 32, 0, s)(n, A, b.raw, b.feat);
+  RST_CUDA(cudaGetLastError());
+  *feat_dev = b.feat;
+  return RST_OK;
 }
 
 static rst_status features_any(const void* off, int bits, const int32_t* col, int64_t n, int64_t m, int32_t root,
-                               float* feat, cudaStream_t s) {
-  if (bits == 32) return features_impl<int32_t>((const int32_t*)off, col, n, m, root, feat, s);
-  return features_impl<int64_t>((const int64_t*)off, col, n, m, root, feat, s);
+                               float** feat_dev, Arena& ar, cudaStream_t s) {
+  if (bits == 32) return features_impl<int32_t>((const int32_t*)off, col, n, m, root, feat_dev, ar, s);
+  return features_impl<int64_t>((const int64_t*)off, col, n, m, root, feat_dev, ar, s);
 }
 
 // ------------------------------------------------------------------ MLP kernels
@@ -276,53 +332,123 @@ static void mlp_grad(const float* P, const float* X, const float* T, int B, MlpS
 
 // ------------------------------------------------------------------ selector state
 
-struct SelectorState {
-  bool loaded = false;
+// The loaded model: network parameters, feature and target normalisation and
+// the fallback margin.  The host keeps the master copy (rst_selector_load);
+// each device gets its own copy before its first prediction after a load.
+struct SelModel {
   float params[kParams];
   float xmean[kF], xstd[kF], ymean[kO], ystd[kO];
-  float margin = 0.f;
+  float margin;
+};
+struct SelectorState {
+  bool loaded = false;
+  int version = 0;
+  SelModel model;
 };
 static SelectorState g_sel;
+constexpr int kSelMaxDev = 64;
+static SelModel* g_sel_dev[kSelMaxDev] = {};
+static int g_sel_dev_version[kSelMaxDev] = {};
 
-// Host forward pass of the loaded network (12 features: inference is tiny and
-// host-side; the training kernels above run on the GPU).
-static void sel_predict(const float* f, float* pred) {
-  float x[kF], h1[kH], h2[kH];
-  for (int i = 0; i < kF; ++i) x[i] = (f[i] - g_sel.xmean[i]) / g_sel.xstd[i];
-  const float* P = g_sel.params;
-  for (int j = 0; j < kH; ++j) {
-    float a = P[kB1 + j];
-    for (int i = 0; i < kF; ++i) a += P[kW1 + j * kF + i] * x[i];
-    h1[j] = a > 0 ? a : 0;
-  }
-  for (int j = 0; j < kH; ++j) {
-    float a = P[kB2 + j];
-    for (int i = 0; i < kH; ++i) a += P[kW2 + j * kH + i] * h1[i];
-    h2[j] = a > 0 ? a : 0;
-  }
-  for (int k = 0; k < kO; ++k) {
-    float a = P[kB3 + k];
-    for (int i = 0; i < kH; ++i) a += P[kW3 + k * kH + i] * h2[i];
-    pred[k] = a * g_sel.ystd[k] + g_sel.ymean[k];
+// Inference of the loaded network on the device, one block per feature row:
+// standardise, 12-64-64-3 with ReLU, un-standardise to predicted natural-log
+// times (order BFS, CC+Euler, PR-RST), then pick the smallest and fall back to
+// CC+Euler when the predicted gain of another strategy is below the margin.
+__global__ void __launch_bounds__(kH) k_sel_infer(const SelModel* __restrict__ M, const float* __restrict__ feat,
+                                                  int B, float* __restrict__ pred, int32_t* __restrict__ choice) {
+  __shared__ float x[kF], h1[kH], h2[kH], y[kO];
+  const int t = threadIdx.x;
+  const float* P = M->params;
+  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    if (t < kF) x[t] = (feat[(int64_t)b * kF + t] - M->xmean[t]) / M->xstd[t];
+    __syncthreads();
+    float a = P[kB1 + t];
+    for (int i = 0; i < kF; ++i) a = fmaf(P[kW1 + t * kF + i], x[i], a);
+    h1[t] = fmaxf(a, 0.f);
+    __syncthreads();
+    a = P[kB2 + t];
+    for (int i = 0; i < kH; ++i) a = fmaf(P[kW2 + t * kH + i], h1[i], a);
+    h2[t] = fmaxf(a, 0.f);
+    __syncthreads();
+    if (t < kO) {
+      a = P[kB3 + t];
+      for (int i = 0; i < kH; ++i) a = fmaf(P[kW3 + t * kH + i], h2[i], a);
+      y[t] = a * M->ystd[t] + M->ymean[t];
+      if (pred) pred[(int64_t)b * kO + t] = y[t];
+    }
+    __syncthreads();
+    if (t == 0 && choice) {
+      int best = 1;
+      for (int k = 0; k < kO; ++k)
+        if (y[k] < y[best]) best = k;
+      if (best != 1 && y[1] - y[best] < M->margin) best = 1;  // small predicted gain: CC+Euler
+      choice[b] = best == 0 ? (int32_t)RST_BFS : (best == 1 ? (int32_t)RST_CC_EULER : (int32_t)RST_PR_RST);
+    }
+    __syncthreads();
   }
 }
 
-// Output order of the network: BFS, CC+Euler, PR-RST.
-static rst_strategy sel_choose(const float* pred) {
-  int best = 1;
-  for (int k = 0; k < kO; ++k)
-    if (pred[k] < pred[best]) best = k;
-  if (best != 1 && pred[1] - pred[best] < g_sel.margin) best = 1;  // small margin: CC+Euler
-  return best == 0 ? RST_BFS : (best == 1 ? RST_CC_EULER : RST_PR_RST);
+// The current device's copy of the loaded model (uploaded after each load).
+static rst_status model_on_device(const SelModel** out, cudaStream_t s) {
+  int dev = 0;
+  RST_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kSelMaxDev) return RST_ERR_UNSUPPORTED;
+  if (!g_sel_dev[dev]) RST_CUDA(cudaMalloc(&g_sel_dev[dev], sizeof(SelModel)));
+  if (g_sel_dev_version[dev] != g_sel.version) {
+    RST_CUDA(cudaMemcpyAsync(g_sel_dev[dev], &g_sel.model, sizeof(SelModel), cudaMemcpyHostToDevice, s));
+    RST_CUDA(cudaStreamSynchronize(s));
+    g_sel_dev_version[dev] = g_sel.version;
+  }
+  *out = g_sel_dev[dev];
+  return RST_OK;
+}
+
+void release_selector() {
+  for (int d = 0; d < kSelMaxDev; ++d)
+    if (g_sel_dev[d]) {
+      cudaFree(g_sel_dev[d]);
+      g_sel_dev[d] = nullptr;
+      g_sel_dev_version[d] = 0;
+    }
+}
+
+// Features, inference and the choice of one graph, all on the device; only
+// the choice and the three predictions come back to the host.
+static rst_status select_impl(const void* off, int bits, const int32_t* cols, int64_t n, int64_t m, int32_t root,
+                              rst_strategy* choice_out, float* pred_out, cudaStream_t s) {
+  RST_TRY(ensure_workspace(feat_workspace_bytes(n, m) + 1024));
+  RST_TRY(reset_device_error(s));
+  const SelModel* M = nullptr;
+  RST_TRY(model_on_device(&M, s));
+  DeviceState& st = state();
+  Arena ar{st.ws, st.ws_cap, 0, false};
+  float* fd = nullptr;
+  RST_TRY(features_any(off, bits, cols, n, m, root, &fd, ar, s));
+  float* pd = ar.take<float>(kO);
+  int32_t* cd = ar.take<int32_t>(1);
+  if (ar.used > ar.cap) return RST_ERR_OOM;
+  RST_LAUNCH(k_sel_infer, 1, kH, 0, s)(M, fd, 1, pd, cd);
+  RST_CUDA(cudaGetLastError());
+  unsigned long long* hb = st.hostbuf + 16;  // word 0 receives the status word
+  RST_CUDA(cudaMemcpyAsync(hb, pd, kO * sizeof(float), cudaMemcpyDeviceToHost, s));
+  RST_CUDA(cudaMemcpyAsync(hb + 2, cd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RST_TRY(read_device_error(s));
+  float pred[kO];
+  int32_t c = 0;
+  std::memcpy(pred, hb, sizeof(pred));
+  std::memcpy(&c, hb + 2, sizeof(c));
+  *choice_out = (rst_strategy)c;
+  if (pred_out)
+    for (int k = 0; k < kO; ++k) pred_out[k] = pred[k];
+  return RST_OK;
 }
 
 rst_strategy select_strategy_host(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                                   int32_t root, cudaStream_t s) {
   if (!g_sel.loaded) return RST_CC_EULER;
-  float f[kF], pred[kO];
-  if (features_any(off, offsets_bits, cols, n, m, root, f, s) != RST_OK) return RST_CC_EULER;
-  sel_predict(f, pred);
-  return sel_choose(pred);
+  rst_strategy c = RST_CC_EULER;
+  if (select_impl(off, offsets_bits, cols, n, m, root, &c, nullptr, s) != RST_OK) return RST_CC_EULER;
+  return c;
 }
 
 }  // namespace rst
@@ -335,26 +461,54 @@ rst_status rst_selector_features(const void* csr_offsets, int offsets_bits, cons
                                  int64_t m, int32_t root, float* features_out, rst_stream_t stream) {
   if (!features_out || (offsets_bits != 32 && offsets_bits != 64) || n <= 0 || root < 0 || root >= n)
     return RST_ERR_INVALID_ARG;
-  if (!csr_offsets || (m > 0 && !csr_cols)) return RST_ERR_INVALID_ARG;
+  if (!csr_offsets || (m > 0 && !csr_cols) || n >= ((int64_t)1 << 30) || m >= ((int64_t)1 << 32))
+    return RST_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(call_lock());
-  return features_any(csr_offsets, offsets_bits, csr_cols, n, m, root, features_out,
-                      reinterpret_cast<cudaStream_t>(stream));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RST_TRY(ensure_workspace(feat_workspace_bytes(n, m)));
+  RST_TRY(reset_device_error(s));
+  DeviceState& st = state();
+  Arena ar{st.ws, st.ws_cap, 0, false};
+  float* fd = nullptr;
+  RST_TRY(features_any(csr_offsets, offsets_bits, csr_cols, n, m, root, &fd, ar, s));
+  // features land after the word that read_device_error fills with the status
+  RST_CUDA(cudaMemcpyAsync(st.hostbuf + 16, fd, kF * sizeof(float), cudaMemcpyDeviceToHost, s));
+  RST_TRY(read_device_error(s));
+  std::memcpy(features_out, st.hostbuf + 16, kF * sizeof(float));
+  return RST_OK;
 }
 
 rst_status rst_selector_load(const float* params, const float* norm, float margin) {
   if (!params || !norm) return RST_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(call_lock());
-  std::memcpy(g_sel.params, params, sizeof(g_sel.params));
-  std::memcpy(g_sel.xmean, norm, sizeof(float) * kF);
-  std::memcpy(g_sel.xstd, norm + kF, sizeof(float) * kF);
-  std::memcpy(g_sel.ymean, norm + 2 * kF, sizeof(float) * kO);
-  std::memcpy(g_sel.ystd, norm + 2 * kF + kO, sizeof(float) * kO);
+  SelModel& M = g_sel.model;
+  std::memcpy(M.params, params, sizeof(M.params));
+  std::memcpy(M.xmean, norm, sizeof(float) * kF);
+  std::memcpy(M.xstd, norm + kF, sizeof(float) * kF);
+  std::memcpy(M.ymean, norm + 2 * kF, sizeof(float) * kO);
+  std::memcpy(M.ystd, norm + 2 * kF + kO, sizeof(float) * kO);
   for (int i = 0; i < kF; ++i)
-    if (!(g_sel.xstd[i] > 0)) g_sel.xstd[i] = 1.f;
+    if (!(M.xstd[i] > 0)) M.xstd[i] = 1.f;
   for (int k = 0; k < kO; ++k)
-    if (!(g_sel.ystd[k] > 0)) g_sel.ystd[k] = 1.f;
-  g_sel.margin = margin;
+    if (!(M.ystd[k] > 0)) M.ystd[k] = 1.f;
+  M.margin = margin;
   g_sel.loaded = true;
+  g_sel.version += 1;
+  return RST_OK;
+}
+
+rst_status rst_selector_predict(const float* features, int batch, float* pred_out, int32_t* choice_out,
+                                rst_stream_t stream) {
+  if (!features || batch <= 0 || (!pred_out && !choice_out)) return RST_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(call_lock());
+  if (!g_sel.loaded) return RST_ERR_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const SelModel* M = nullptr;
+  RST_TRY(model_on_device(&M, s));
+  const int grid = batch < device_info().sms * 16 ? batch : device_info().sms * 16;
+  RST_LAUNCH(k_sel_infer, grid, kH, 0, s)(M, features, batch, pred_out, choice_out);
+  RST_CUDA(cudaGetLastError());
+  RST_CUDA(cudaStreamSynchronize(s));
   return RST_OK;
 }
 
@@ -362,7 +516,8 @@ rst_status rst_select(const void* csr_offsets, int offsets_bits, const int32_t* 
                       int32_t root, rst_strategy* choice_out, float* pred_log_time_out, rst_stream_t stream) {
   if (!choice_out || (offsets_bits != 32 && offsets_bits != 64) || n <= 0 || root < 0 || root >= n)
     return RST_ERR_INVALID_ARG;
-  if (!csr_offsets || (m > 0 && !csr_cols)) return RST_ERR_INVALID_ARG;
+  if (!csr_offsets || (m > 0 && !csr_cols) || n >= ((int64_t)1 << 30) || m >= ((int64_t)1 << 32))
+    return RST_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(call_lock());
   if (!g_sel.loaded) {
     *choice_out = RST_CC_EULER;
@@ -370,13 +525,8 @@ rst_status rst_select(const void* csr_offsets, int offsets_bits, const int32_t* 
       for (int k = 0; k < kO; ++k) pred_log_time_out[k] = NAN;
     return RST_OK;
   }
-  float f[kF], pred[kO];
-  RST_TRY(features_any(csr_offsets, offsets_bits, csr_cols, n, m, root, f, reinterpret_cast<cudaStream_t>(stream)));
-  sel_predict(f, pred);
-  *choice_out = sel_choose(pred);
-  if (pred_log_time_out)
-    for (int k = 0; k < kO; ++k) pred_log_time_out[k] = pred[k];
-  return RST_OK;
+  return select_impl(csr_offsets, offsets_bits, csr_cols, n, m, root, choice_out, pred_log_time_out,
+                     reinterpret_cast<cudaStream_t>(stream));
 }
 
 rst_status rst_mlp_forward(const float* params, const float* X, int batch, float* Y, rst_stream_t stream) {

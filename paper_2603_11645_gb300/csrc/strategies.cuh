@@ -64,6 +64,9 @@ rst_status run_prrst_insert(int64_t n, int32_t* parent, const int32_t* uv, int64
 rst_status run_verify(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                       int32_t root, const int32_t* parent, int32_t* verdict_out, cudaStream_t s);
 
+// Release the device copies of the selector model (rst_shutdown).
+void release_selector();
+
 // Strategy for RST_AUTO.
 rst_strategy select_strategy_host(const void* off, int offsets_bits, const int32_t* cols, int64_t n,
                                   int64_t m, int32_t root, cudaStream_t s);

@@ -1,18 +1,21 @@
-"""Learned strategy selector: data generation, GPU training, evaluation.
+"""Learned strategy selector: data generation, GPU training, GPU inference.
 
 The library's own timings of BFS, CC+Euler and PR-RST on seeded graphs train a
 12-64-64-3 network (rst_mlp_train: forward, backward and Adam kernels on the
 GPU) that predicts each strategy's log-time from 12 cheap features
-(rst_selector_features).  rst_select / rst_build(RST_AUTO) pick the smallest
-prediction and fall back to CC+Euler when the predicted gain is below a margin.
+(rst_selector_features, computed on the GPU).  rst_select / rst_build(RST_AUTO)
+run the features, the network and the choice on the GPU: the smallest
+prediction wins, and CC+Euler is kept when another strategy's predicted gain
+is below a margin.  This module only moves data to and from those calls.
 
-Graph families (seeded; training seeds 5000+i, held-out seeds 9000+i):
-grids with aspect ratio log-uniform in [1, 4096], paths with uniformly random
-chords at density log-uniform in [1e-6, 1e-1], R-MAT graphs connected to
-vertex 0, and random 4-regular graphs; vertex counts log-uniform in
-[2^14, 2^20].  BFS runs are capped at BFS_LEVEL_CAP levels; a capped run is
-labelled with the time spent up to the cap (a lower bound that is never the
-fastest strategy, so regret stays exact).
+Graph families (seeded; training seeds 5000+i, held-out seeds 9000+i), in
+turn: grids with aspect ratio log-uniform in [1, 4096], paths with uniformly
+random chords at density log-uniform in [1e-6, 1e-1], R-MAT graphs of scale
+round(log2 n) in [16, 22] connected to vertex 0, and random 4-regular graphs;
+vertex counts log-uniform in [2^16, 2^22].  BFS runs are capped at
+BFS_LEVEL_CAP levels; a capped run is labelled with the time spent up to the
+cap (a lower bound far above the best strategy's time, so it is never the
+argmin and regret stays exact).
 """
 from __future__ import annotations
 
@@ -30,11 +33,13 @@ from . import graphs
 F, H, O = 12, 64, 3
 NPARAM = H * F + H + H * H + H + O * H + O
 STRATS = ("bfs", "cc_euler", "pr_rst")
-BFS_LEVEL_CAP = 4096
+CHOICE_INDEX = {1: 0, 2: 1, 3: 2}  # rst_strategy code -> position in STRATS
+BFS_LEVEL_CAP = 1024
+LOG2N_RANGE = (16, 22)
 WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.json")
 FEATURE_NAMES = ["log2_n", "log2_m", "mean_deg", "deg_cv", "deg_skew", "log2_maxdeg", "frac_deg_le2",
                  "log2_probe_reached", "log2_probe_growth", "log2_ecc_est", "log2_r1_comp_frac",
-                 "probe_reach_frac"]
+                 "surviving_edge_frac"]
 
 
 def _lib():
@@ -44,12 +49,13 @@ def _lib():
     L.rst_selector_features.argtypes = [P, I, P, I64, I64, I32, P, P]
     L.rst_selector_load.argtypes = [P, P, Fl]
     L.rst_select.argtypes = [P, I, P, I64, I64, I32, P, P, P]
+    L.rst_selector_predict.argtypes = [P, I, P, P, P]
     L.rst_mlp_forward.argtypes = [P, P, I, P, P]
     L.rst_mlp_loss_grad.argtypes = [P, P, P, I, P, P, P]
     L.rst_mlp_adam.argtypes = [P, P, P, P, I, I, Fl, Fl, Fl, Fl, P]
     L.rst_mlp_train.argtypes = [P, P, P, I, I, Fl, P, P, P, P]
     L.rst_set_option.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
-    for fn in ("rst_selector_features", "rst_selector_load", "rst_select", "rst_mlp_forward",
+    for fn in ("rst_selector_features", "rst_selector_load", "rst_select", "rst_selector_predict", "rst_mlp_forward",
                "rst_mlp_loss_grad", "rst_mlp_adam", "rst_mlp_train", "rst_set_option"):
         getattr(L, fn).restype = I
     return L
@@ -72,7 +78,8 @@ def family_graph(i: int, split: str = "train") -> graphs.Graph:
     seed = (5000 if split == "train" else 9000) + i
     r = graphs.uniform(4, 1 << 30, seed * 7919 + 11).astype(np.float64) / (1 << 30)
     fam = i % 4
-    n = int(round(math.exp(math.log(2 ** 14) + r[0] * (math.log(2 ** 20) - math.log(2 ** 14)))))
+    lo, hi = LOG2N_RANGE
+    n = int(round(math.exp(math.log(2 ** lo) + r[0] * (math.log(2 ** hi) - math.log(2 ** lo)))))
     if fam == 0:
         aspect = math.exp(r[1] * math.log(4096.0))
         Hh = max(1, int(round(math.sqrt(n / aspect))))
@@ -83,13 +90,50 @@ def family_graph(i: int, split: str = "train") -> graphs.Graph:
         g = graphs.chain_chords(n, d, seed=seed)
         g.root = int(graphs.uniform(1, n, seed + 3)[0])
     elif fam == 2:
-        scale = max(14, min(20, int(round(math.log2(n)))))
+        scale = max(lo, min(hi, int(round(math.log2(n)))))
         g = graphs.rmat(scale, 16, seed=seed, connect=True, offsets_bits=32)
     else:
         g = graphs.random_4regular(max(n, 5), seed=seed)
     g.meta["split"] = split
     g.meta["index"] = i
     return g
+
+
+def _family_graph_args(args):
+    return family_graph(*args)
+
+
+def _worker_init(threads: int):
+    os.environ["GG_THREADS"] = str(threads)  # the generator's own threads per worker
+
+
+def family_graphs(split: str, indices, workers: int | None = None):
+    """The split's graphs in index order, generated by a pool of spawned
+    worker processes (no CUDA in them) while the caller consumes earlier
+    ones; at most two graphs per worker are in flight or waiting."""
+    import collections
+    import multiprocessing as mp
+    indices = list(indices)
+    cores = os.cpu_count() or 2
+    workers = workers or max(1, min(12, cores - 2))
+    if workers <= 1 or len(indices) <= 1:
+        for i in indices:
+            yield family_graph(i, split)
+        return
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_worker_init, initargs=(max(2, cores // 2),)) as pool:
+        pending = collections.deque()
+        it = iter(indices)
+        for i in it:
+            pending.append(pool.apply_async(family_graph, (i, split)))
+            if len(pending) >= 2 * workers:
+                break
+        while pending:
+            g = pending.popleft().get()
+            nxt = next(it, None)
+            if nxt is not None:
+                pending.append(pool.apply_async(family_graph, (nxt, split)))
+            yield g
 
 
 # ------------------------------------------------------------------ GPU calls
@@ -105,7 +149,7 @@ def features(off, col, root: int) -> np.ndarray:
     return f
 
 
-def time_strategies(off, col, root: int, reps: int = 3):
+def time_strategies(off, col, root: int, reps: int = 2):
     """Median wall time (s, CUDA events) of each strategy; BFS capped."""
     import torch
     from . import build, RstError
@@ -136,18 +180,18 @@ def time_strategies(off, col, root: int, reps: int = 3):
     return times, censored
 
 
-def generate_dataset(split: str, count: int, path: str, reps: int = 3, log_every: int = 50):
+def generate_dataset(split: str, count: int, path: str, reps: int = 2, log_every: int = 100):
     """Features and timings of `count` graphs of the split, written as CSV."""
     import torch
     rows = []
     t0 = time.time()
-    for i in range(count):
-        g = family_graph(i, split)
+    for i, g in enumerate(family_graphs(split, range(count))):
         off = torch.from_numpy(g.offsets).cuda()
         col = torch.from_numpy(g.cols).cuda()
         f = features(off, col, g.root)
         ts, cens = time_strategies(off, col, g.root, reps)
         rows.append([split, i, g.meta.get("family", "?"), g.n, g.m] + [float(x) for x in f] + ts + [int(cens)])
+        del off, col
         if log_every and (i + 1) % log_every == 0:
             print(f"[{split}] {i + 1}/{count} graphs, {time.time() - t0:.0f} s", flush=True)
     header = ["split", "index", "family", "n", "m"] + FEATURE_NAMES + [f"t_{s}" for s in STRATS] + ["bfs_censored"]
@@ -207,47 +251,20 @@ def train(X: np.ndarray, times: np.ndarray, epochs: int = 4000, lr: float = 3e-3
             "loss_first": float(hist[0].item()), "loss_last": float(hist[-1].item())}
 
 
-def predict_host(model: dict, X: np.ndarray) -> np.ndarray:
-    """Predicted natural-log times (float64 host evaluation of the model)."""
-    p = np.asarray(model["params"], dtype=np.float64)
-    norm = np.asarray(model["norm"], dtype=np.float64)
-    xm, xs, ym, ys = norm[:F], norm[F:2 * F], norm[2 * F:2 * F + O], norm[2 * F + O:]
-    Xs = (X - xm) / xs
-    o = 0
-    w1 = p[o:o + H * F].reshape(H, F); o += H * F
-    b1 = p[o:o + H]; o += H
-    w2 = p[o:o + H * H].reshape(H, H); o += H * H
-    b2 = p[o:o + H]; o += H
-    w3 = p[o:o + O * H].reshape(O, H); o += O * H
-    b3 = p[o:o + O]
-    h1 = np.maximum(Xs @ w1.T + b1, 0)
-    h2 = np.maximum(h1 @ w2.T + b2, 0)
-    return (h2 @ w3.T + b3) * ys + ym
-
-
-def choose(pred: np.ndarray, margin: float) -> np.ndarray:
-    best = pred.argmin(1)
-    cc = 1
-    fallback = (best != cc) & (pred[:, cc] - pred[np.arange(len(pred)), best] < margin)
-    best[fallback] = cc
-    return best
-
-
-def regret(times: np.ndarray, choice: np.ndarray) -> float:
-    """Mean over graphs of (t_chosen - t_best) / t_best."""
-    tb = times.min(1)
-    tc = times[np.arange(len(times)), choice]
-    return float(np.mean((tc - tb) / tb))
-
-
-def fit_margin(model: dict, X: np.ndarray, times: np.ndarray) -> float:
-    pred = predict_host(model, X)
-    best_m, best_r = 0.0, None
-    for mg in [0.0, 0.05, 0.1, 0.2, 0.3, 0.5, 0.75, 1.0]:
-        r = regret(times, choose(pred, mg))
-        if best_r is None or r < best_r - 1e-12:
-            best_m, best_r = mg, r
-    return best_m
+def predict(X: np.ndarray):
+    """The loaded network on the GPU (rst_selector_predict) for raw feature
+    rows X: (predicted natural-log times [B][3], chosen STRATS index [B])."""
+    import torch
+    L = _lib()
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    B = Xd.shape[0]
+    pred = torch.empty((B, O), dtype=torch.float32, device="cuda")
+    choice = torch.empty(B, dtype=torch.int32, device="cuda")
+    _check("rst_selector_predict", L.rst_selector_predict(ctypes.c_void_p(Xd.data_ptr()), B,
+                                                          ctypes.c_void_p(pred.data_ptr()),
+                                                          ctypes.c_void_p(choice.data_ptr()), _stream()))
+    idx = np.array([CHOICE_INDEX[int(c)] for c in choice.cpu().numpy()], dtype=np.int64)
+    return pred.cpu().numpy(), idx
 
 
 def load_into_library(model: dict) -> None:
@@ -276,4 +293,4 @@ def select(off, col, root: int):
     code = L.rst_select(ctypes.c_void_p(off.data_ptr()), bits, ctypes.c_void_p(col.data_ptr()), off.numel() - 1,
                         col.numel(), int(root), ctypes.byref(choice), pred.ctypes.data, _stream())
     _check("rst_select", code)
-    return {1: "bfs", 2: "cc_euler", 3: "pr_rst"}[choice.value], pred
+    return STRATS[CHOICE_INDEX[choice.value]], pred

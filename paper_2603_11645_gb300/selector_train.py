@@ -1,10 +1,15 @@
-"""Collect selector timings on the GPU, train the network on the GPU, evaluate
-regret on held-out graphs and write the weights the library loads.
+"""Collect selector timings on the GPU, train the network on the GPU, fit the
+fallback margin and report held-out regret from the GPU's own choices, then
+write the weights the library loads.
 
     python -m paper_2603_11645_gb300.selector_train --train 2000 --heldout 200 \
         --data-dir paper_2603_11645_gb300/selector_data
 
-Resumes from existing CSVs in --data-dir (timings are not re-collected).
+Resumes from existing CSVs in --data-dir (timings are not re-collected).  The
+margin is fitted out of sample: a network trained on the first 80% of the
+training graphs chooses on the last 20% (rst_selector_predict, on the GPU)
+for every candidate margin; the final network is trained on all training
+graphs and keeps the margin with the lowest regret there.
 """
 from __future__ import annotations
 
@@ -16,6 +21,30 @@ import numpy as np
 
 from . import selector as S
 
+MARGINS = [0.0, 0.05, 0.1, 0.2, 0.3, 0.5, 0.75, 1.0]
+
+
+def _regret(times: np.ndarray, choice: np.ndarray) -> float:
+    """Mean over graphs of (t_chosen - t_best) / t_best."""
+    tb = times.min(1)
+    return float(np.mean((times[np.arange(len(times)), choice] - tb) / tb))
+
+
+def _choices(model: dict, X: np.ndarray, margin: float) -> np.ndarray:
+    m = dict(model, margin=margin)
+    S.load_into_library(m)
+    return S.predict(X)[1]
+
+
+def fit_margin(Xtr, Ttr, args):
+    k = int(len(Xtr) * 0.8)
+    model = S.train(Xtr[:k], Ttr[:k], args.epochs, args.lr, args.seed)
+    seen = {}
+    for mg in MARGINS:
+        seen[mg] = _regret(Ttr[k:], _choices(model, Xtr[k:], mg))
+    best = min(MARGINS, key=lambda mg: (seen[mg], mg))
+    return best, {str(mg): r for mg, r in seen.items()}
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -25,7 +54,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=4000)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--out", default=S.WEIGHTS_PATH)
     args = ap.parse_args()
     os.makedirs(args.data_dir, exist_ok=True)
@@ -37,21 +66,26 @@ def main():
         S.generate_dataset("heldout", args.heldout, ho, args.reps)
     Xtr, Ttr, _ = S.load_dataset(tr)
     Xho, Tho, fam = S.load_dataset(ho)
+    margin, margin_regrets = fit_margin(Xtr, Ttr, args)
     model = S.train(Xtr, Ttr, args.epochs, args.lr, args.seed)
-    model["margin"] = S.fit_margin(model, Xtr, Ttr)
-    pred = S.predict_host(model, Xho)
-    sel = S.choose(pred, model["margin"])
+    model["margin"] = margin
+    S.load_into_library(model)
+    pred, sel = S.predict(Xho)
     cc = np.ones(len(Tho), dtype=int)
     best = Tho.argmin(1)
+    fams = sorted(set(fam))
     report = {
         "heldout_graphs": int(len(Tho)),
-        "selector_regret": S.regret(Tho, sel),
-        "always_cc_euler_regret": S.regret(Tho, cc),
-        "always_bfs_regret": S.regret(Tho, np.zeros(len(Tho), dtype=int)),
+        "selector_regret": _regret(Tho, sel),
+        "always_cc_euler_regret": _regret(Tho, cc),
+        "always_bfs_regret": _regret(Tho, np.zeros(len(Tho), dtype=int)),
+        "always_pr_rst_regret": _regret(Tho, np.full(len(Tho), 2)),
         "oracle_choice_counts": {s: int((best == k).sum()) for k, s in enumerate(S.STRATS)},
         "selector_choice_counts": {s: int((sel == k).sum()) for k, s in enumerate(S.STRATS)},
         "selector_sum_ratio": float(Tho[np.arange(len(Tho)), sel].sum() / Tho.min(1).sum()),
-        "margin": model["margin"],
+        "per_family_regret": {f: _regret(Tho[[x == f for x in fam]], sel[[x == f for x in fam]]) for f in fams},
+        "margin": margin, "margin_validation_regret": margin_regrets,
+        "choices_by": "rst_selector_predict (GPU) on the GPU-computed features of each held-out graph",
         "train_loss_first": model["loss_first"], "train_loss_last": model["loss_last"],
     }
     model["heldout_report"] = report

@@ -61,9 +61,10 @@ def test_oracle_features_of_a_path():
     assert f[7] == pytest.approx(math.log2(9))
     assert f[8] == pytest.approx(0.0)
     assert f[9] == pytest.approx(math.log2(1 + 8 + 2 / 1))
-    # round 1: only 0 and 1 choose each other
+    # round 1: only 0 and 1 choose each other, and every vertex joins them
+    # (u hooks along u - 1), so no edge survives
     assert f[10] == pytest.approx(math.log2(1 / 10))
-    assert f[11] == pytest.approx(0.8)
+    assert f[11] == pytest.approx(0.0)
 
 
 def test_oracle_features_of_a_star():
@@ -73,9 +74,80 @@ def test_oracle_features_of_a_star():
     # levels: {3}, {0}, {1,2,4,...,8}; finished after 3 levels
     assert f[7] == pytest.approx(math.log2(10))
     assert f[9] == pytest.approx(math.log2(1 + 3))
-    assert f[11] == pytest.approx(1.0)
-    # every leaf's first neighbour is 0, 0's first neighbour is 1: one mutual pair
+    # every leaf's first neighbour is 0, 0's first neighbour is 1: one mutual
+    # pair, one round-1 component, no surviving edge
     assert f[10] == pytest.approx(math.log2(1 / 9))
+    assert f[11] == pytest.approx(0.0)
+
+
+def test_oracle_round1_of_a_hand_derived_case():
+    """Edges 0-2, 1-3, 2-3: rows 0:[2] 1:[3] 2:[0,3] 3:[1,2], so the first
+    neighbours are 0->2, 1->3, 2->0, 3->1: two mutual pairs, round-1
+    components {0,2} and {1,3}, and the edge 2-3 (one of three) survives."""
+    g = graphs.from_edges(4, [0, 1, 2], [2, 3, 3], root=0)
+    f = OS.features(4, g.offsets, g.cols, 0)
+    assert f[10] == pytest.approx(math.log2(2 / 4))
+    assert f[11] == pytest.approx(1 / 3)
+    first = OS.first_neighbours(4, g.offsets, g.cols)
+    assert list(first) == [2, 3, 0, 1]
+
+
+def _components_by_union_find(n, first):
+    par = list(range(n))
+
+    def find(x):
+        while par[x] != x:
+            par[x] = par[par[x]]
+            x = par[x]
+        return x
+    for u in range(n):
+        if first[u] >= 0:
+            a, b = find(u), find(int(first[u]))
+            if a != b:
+                par[max(a, b)] = min(a, b)
+    return [find(u) for u in range(n)]
+
+
+def test_oracle_round1_components_against_union_find():
+    """The first neighbour skips self-loops and the components of the hook
+    graph equal a plain union-find's, on multigraphs with loops and repeats."""
+    rng = np.random.default_rng(5)
+    for t in range(30):
+        n = int(rng.integers(1, 40))
+        k = int(rng.integers(0, 3 * n))
+        u = rng.integers(0, n, k)
+        v = np.where(rng.random(k) < 0.15, u, rng.integers(0, n, k))  # some self-loops
+        src = np.concatenate([u, v])
+        dst = np.concatenate([v, u])
+        order = np.lexsort((dst, src))
+        src, dst = src[order], dst[order]
+        off = np.zeros(n + 1, dtype=np.int64)
+        np.add.at(off, src + 1, 1)
+        off = np.cumsum(off)
+        first = OS.first_neighbours(n, off, dst)
+        for x in range(n):
+            row = [int(c) for c in dst[off[x]:off[x + 1]] if c != x]
+            assert first[x] == (row[0] if row else -1)
+        comp = OS.round1_components(n, first)
+        uf = _components_by_union_find(n, first)
+        for a in range(n):
+            for b in range(n):
+                assert (comp[a] == comp[b]) == (uf[a] == uf[b])
+
+
+def test_oracle_choice_rule():
+    """Smallest predicted log-time wins; CC+Euler (index 1) is kept when the
+    winner's predicted gain over it is below the margin."""
+    pred = np.array([[0.0, 1.0, 2.0],    # BFS by 1.0
+                     [3.0, 1.0, 0.95],   # PR-RST by 0.05
+                     [5.0, 1.0, 5.0],    # CC+Euler
+                     [1.0, 1.0, 2.0]])   # tie: CC+Euler (the first smallest from index 1 stays)
+    assert list(OS.choose(pred, 0.0)) == [0, 2, 1, 1]
+    assert list(OS.choose(pred, 0.1)) == [0, 1, 1, 1]
+    assert list(OS.choose(pred, 2.0)) == [1, 1, 1, 1]
+    t = np.array([[1.0, 2.0, 4.0], [2.0, 1.0, 1.0]])
+    assert OS.regret(t, [0, 1]) == pytest.approx(0.0)
+    assert OS.regret(t, [1, 2]) == pytest.approx(0.5)
 
 
 # ------------------------------------------------------------------ GPU kernels vs oracle
@@ -83,12 +155,31 @@ def test_oracle_features_of_a_star():
 torch = pytest.importorskip("torch")
 
 
+def _multigraph(n, k, seed):
+    """A CSR with self-loops and repeated arcs (rows sorted, symmetric)."""
+    rng = np.random.default_rng(seed)
+    u = rng.integers(0, n, k)
+    v = np.where(rng.random(k) < 0.1, u, rng.integers(0, n, k))
+    src = np.concatenate([u, v])
+    dst = np.concatenate([v, u])
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(off, src + 1, 1)
+    g = graphs.Graph(f"multi{n}", n, np.cumsum(off).astype(np.int32), dst.astype(np.int32),
+                     int(rng.integers(0, n)))
+    return g
+
+
 @pytest.mark.gpu
 def test_gpu_features_match_oracle():
     from paper_2603_11645_gb300 import selector as S
     cases = [graphs.grid(40, 30, seed=1, root="random"), graphs.chain_chords(5000, 0.001, seed=2),
              graphs.rmat(12, 16, seed=3, connect=True, offsets_bits=32), graphs.random_4regular(3000, seed=4),
-             graphs.erdos_renyi(2000, 1500, seed=5), graphs.from_edges(5, [0, 1], [1, 2], root=4)]
+             graphs.erdos_renyi(2000, 1500, seed=5), graphs.from_edges(5, [0, 1], [1, 2], root=4),
+             graphs.from_edges(4, [0, 1, 2], [2, 3, 3], root=1),
+             graphs.rmat(16, 16, seed=6, connect=True, offsets_bits=64),
+             _multigraph(6000, 15000, 7)]
     for g in cases:
         off = torch.from_numpy(g.offsets).cuda()
         col = torch.from_numpy(g.cols).cuda()
@@ -142,6 +233,32 @@ def test_gpu_training_fits_a_smooth_target():
     assert model["loss_last"] < 0.2 * model["loss_first"]
 
 
+@pytest.mark.gpu
+def test_gpu_inference_matches_oracle():
+    """rst_selector_predict (standardise, network, margin choice on the GPU)
+    against the oracle's float64 inference, for a random model and random
+    feature rows; choices are compared where no near-tie can flip them."""
+    from paper_2603_11645_gb300 import selector as S
+    rng = np.random.default_rng(21)
+    p = OS.he_init(3)
+    norm = np.concatenate([rng.normal(size=OS.F), rng.uniform(0.5, 2.0, OS.F), rng.normal(size=OS.O),
+                           rng.uniform(0.5, 2.0, OS.O)])
+    X = rng.normal(size=(300, OS.F)) * 2
+    for margin in (0.0, 0.3):
+        S.load_into_library({"params": p.tolist(), "norm": norm.tolist(), "margin": margin})
+        pred, idx = S.predict(X)
+        p32 = p.astype(np.float32).astype(np.float64)
+        n32 = norm.astype(np.float32).astype(np.float64)
+        want = OS.predict(p32, n32, X.astype(np.float32).astype(np.float64))
+        assert np.allclose(pred, want, rtol=1e-4, atol=1e-4)
+        wc = OS.choose(want, margin)
+        srt = np.sort(want, 1)
+        safe = (srt[:, 1] - srt[:, 0] > 1e-3) & (np.abs(want[:, 1] - want.min(1) - margin) > 1e-3)
+        assert safe.sum() > 250
+        assert np.array_equal(idx[safe], wc[safe])
+    S.load_default()
+
+
 # ------------------------------------------------------------------ regret of the trained selector
 
 def _trained():
@@ -157,16 +274,55 @@ def _trained():
     return S, model, os.path.join(data, ho[0])
 
 
-def test_selector_regret_beats_always_cc_euler():
-    """What the network gains over the method without it (always CC+Euler),
-    measured on held-out graphs from stored GPU timings."""
+def test_stored_model_regret_by_the_oracle():
+    """The committed network, evaluated by the oracle's float64 inference on
+    the stored held-out features, beats always-CC+Euler and stays within 10%
+    regret (a check of the stored weights and data, independent of the GPU)."""
     S, model, path = _trained()
     X, Tt, fam = S.load_dataset(path)
-    sel = S.choose(S.predict_host(model, X), model["margin"])
-    r_sel = S.regret(Tt, sel)
-    r_cc = S.regret(Tt, np.ones(len(Tt), dtype=int))
+    sel = OS.choose(OS.predict(model["params"], model["norm"], X), model["margin"])
+    r_sel = OS.regret(Tt, sel)
+    assert r_sel <= OS.regret(Tt, np.ones(len(Tt), dtype=int))
+    assert r_sel <= 0.10
+
+
+@pytest.mark.gpu
+def test_gpu_selector_regret_on_heldout_graphs():
+    """What the network gains over the method without it: the GPU's own
+    choices (rst_selector_predict on the held-out graphs' GPU features) score
+    at most 10% mean regret against the exhaustively timed strategies, and
+    less than always choosing CC+Euler."""
+    S, model, path = _trained()
+    X, Tt, fam = S.load_dataset(path)
+    S.load_into_library(model)
+    pred, sel = S.predict(X)
+    r_sel = OS.regret(Tt, sel)
+    r_cc = OS.regret(Tt, np.ones(len(Tt), dtype=int))
     assert r_sel <= r_cc
     assert r_sel <= 0.10
+
+
+@pytest.mark.gpu
+def test_rst_select_end_to_end_on_heldout_graphs():
+    """rst_select on regenerated held-out graphs: its features equal the stored
+    ones and its choice is the one the stored features give."""
+    S, model, path = _trained()
+    X, Tt, fam = S.load_dataset(path)
+    S.load_into_library(model)
+    _, stored_choice = S.predict(X)
+    import csv
+    with open(path) as fh:
+        rows = list(csv.DictReader(fh))
+    small = [i for i, r in enumerate(rows) if int(r["n"]) <= (1 << 18)][:8]
+    assert small
+    for i in small:
+        g = S.family_graph(i, "heldout")
+        off = torch.from_numpy(g.offsets).cuda()
+        col = torch.from_numpy(g.cols).cuda()
+        f = S.features(off, col, g.root)
+        assert np.allclose(f, X[i], rtol=1e-5, atol=1e-5), (i, f, X[i])
+        choice, pred = S.select(off, col, g.root)
+        assert choice == S.STRATS[stored_choice[i]]
 
 
 @pytest.mark.gpu
