@@ -253,7 +253,9 @@ def test_gpu_inference_matches_oracle():
         assert np.allclose(pred, want, rtol=1e-4, atol=1e-4)
         wc = OS.choose(want, margin)
         srt = np.sort(want, 1)
-        safe = (srt[:, 1] - srt[:, 0] > 1e-3) & (np.abs(want[:, 1] - want.min(1) - margin) > 1e-3)
+        gain = want[:, 1] - want.min(1)  # predicted gain of the best over CC+Euler
+        near_margin = (gain > 0) & (np.abs(gain - margin) <= 1e-3)
+        safe = (srt[:, 1] - srt[:, 0] > 1e-3) & ~near_margin
         assert safe.sum() > 250
         assert np.array_equal(idx[safe], wc[safe])
     S.load_default()
