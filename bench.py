@@ -413,7 +413,7 @@ def run_ours(args, rank, world, local_rank):
 
     # edge insertions: the forest of the graph with 45% of its edges held back,
     # then those edges inserted with PR-RST graft and reversal
-    ins_rep = run_insert(g, dev, stream, rst, graphs, torch, max(3, args.bfs_steps))
+    ins_rep = run_insert(g, dev, stream, rst, graphs, torch, max(3, args.bfs_steps), total_ms / args.steps)
 
     # tree shape (Fig. 2): heights of the trees each strategy returns
     heights = {}
@@ -548,10 +548,12 @@ def run_batch(args, dev, stream, rst, graphs, torch, rank=0, world=1, cpu_on=Fal
             "unit": "edges/s", "speedup": per_graph / batched}
 
 
-def run_insert(g, dev, stream, rst, graphs, torch, reps):
+def run_insert(g, dev, stream, rst, graphs, torch, reps, rebuild_ms):
     """Rooted spanning forest of g minus a seeded 45% of its edges (CC+Euler;
     below the square lattice's bond threshold, so a forest of many trees),
-    then the held-back edges inserted in one batch (rst_insert_edges)."""
+    then batches of the held-back edges inserted (rst_insert_edges): 1,000,
+    100,000 (seeded subsets) and all of them, each beside a full CC+Euler
+    rebuild of the graph."""
     import numpy as np
     src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets))
     col = g.cols.astype(np.int64)
@@ -559,28 +561,35 @@ def run_insert(g, dev, stream, rst, graphs, torch, reps):
     lo, hi = src[fwd], col[fwd]
     drop = ((lo * 0x9E3779B1 + hi * 0x85EBCA77 + 11) % 1000003) < 450000
     g0 = graphs.from_edges(g.n, lo[~drop], hi[~drop], root=g.root)
-    uv = torch.from_numpy(np.stack([lo[drop], hi[drop]], 1).astype(np.int32)).to(dev)
+    held = np.stack([lo[drop], hi[drop]], 1).astype(np.int32)
+    held = held[np.random.default_rng(12).permutation(len(held))]
     off0 = torch.from_numpy(g0.offsets).to(dev)
     col0 = torch.from_numpy(g0.cols).to(dev)
     base = rst.build(off0, col0, g.root, "cc_euler")
     work = torch.empty_like(base)
-    ts = []
-    for i in range(reps + 1):
-        work.copy_(base)
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rst.insert_edges(work, uv, g.root)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if i:
-            ts.append(e0.elapsed_time(e1))
-    ms = statistics.median(ts)
+    batches = {}
+    for k in (1000, 100000, len(held)):
+        uv = torch.from_numpy(np.ascontiguousarray(held[:k])).to(dev)
+        ts = []
+        for i in range(reps + 1):
+            work.copy_(base)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rst.insert_edges(work, uv, g.root)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if i:
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        batches[str(k)] = {"ms": ms, "rebuild_ms": rebuild_ms, "speedup_over_rebuild": rebuild_ms / ms}
     return {"workload": f"4096x4096 grid forest with {int(drop.sum())} edges (45%) held back, "
-                        f"then inserted in one batch", "inserted": int(drop.sum()), "ms": ms,
+                        f"then batches of them inserted (seeded order)", "inserted_max": int(drop.sum()),
+            "batches": batches,
             "trees_before": int((base.cpu() == torch.arange(g.n, dtype=torch.int32)).sum()),
-            "note": "PR-RST rounds from the existing forest over the inserted edges only"}
+            "note": "PR-RST rounds from the existing forest over the inserted edges only; batches of at most "
+                    "n/64 edges run them sparsely (work proportional to the batch)"}
 
 
 def _time(fn, reps, torch, dev, stream, flush=None):
@@ -684,9 +693,14 @@ def run_grid256(args, dev, stream, rst, graphs, torch, cpu_on):
     return out
 
 
-def run_selector_report(off, col, root, torch):
-    """Held-out regret of the trained selector (GPU timings stored with the
-    weights) and the cost of one rst_select call on the headline graph."""
+def run_selector_report(off, col, root, torch, count=24):
+    """The learned selector measured in this run: the first `count` held-out
+    graphs of the selector workload (seeds 9000+i, the four families in turn,
+    n log-uniform in [2^16, 2^22]) are generated, all three strategies are
+    timed on each (BFS capped as in training), and rst_select's choice (GPU
+    features, GPU network) is scored: regret = mean (t_chosen - t_best) /
+    t_best, beside always choosing CC+Euler.  Also the cost of one rst_select
+    call on the headline graph and the stored 200-graph report."""
     from paper_2603_11645_gb300 import selector as S
     model = S.load_default()
     if model is None:
@@ -695,12 +709,35 @@ def run_selector_report(off, col, root, torch):
     for _ in range(5):
         choice, pred = S.select(off, col, root)
     sel_ms = (time.perf_counter() - t0) / 5 * 1e3
+    rows = []
+    for g in S.family_graphs("heldout", range(count)):
+        o = torch.from_numpy(g.offsets).cuda()
+        c = torch.from_numpy(g.cols).cuda()
+        ts, cens = S.time_strategies(o, c, g.root)
+        ch, _ = S.select(o, c, g.root)
+        rows.append((g.meta.get("family", "?"), g.n, ts, S.STRATS.index(ch), cens))
+        del o, c
+    T = [r[2] for r in rows]
+    best = [min(range(3), key=lambda k: t[k]) for t in T]
+
+    def reg(ch):
+        return sum((t[k] - t[b]) / t[b] for t, k, b in zip(T, ch, best)) / len(T)
+
+    chosen = [r[3] for r in rows]
     rep = model.get("heldout_report", {})
-    return {"heldout_regret": rep.get("selector_regret"),
-            "always_cc_euler_regret": rep.get("always_cc_euler_regret"),
-            "heldout_graphs": rep.get("heldout_graphs"), "margin": model.get("margin"),
+    return {"heldout_regret": reg(chosen), "always_cc_euler_regret": reg([1] * len(T)),
+            "always_bfs_regret": reg([0] * len(T)),
+            "heldout_graphs": len(T), "margin": model.get("margin"),
+            "choice_counts": {s: chosen.count(k) for k, s in enumerate(S.STRATS)},
+            "best_counts": {s: best.count(k) for k, s in enumerate(S.STRATS)},
+            "bfs_censored": sum(r[4] for r in rows),
+            "workload": f"held-out graphs 0..{count - 1} of the selector workload (grid / chain+chords / "
+                        f"R-MAT / random 4-regular in turn, n log-uniform 2^16..2^22), timed live; choices by "
+                        f"rst_select (features and network on the GPU)",
             "choice_on_headline": choice, "select_ms": sel_ms,
-            "source": "paper_2603_11645_gb300/selector_weights.json (timings collected on GB300)"}
+            "stored_report": {k: rep.get(k) for k in ("heldout_graphs", "selector_regret",
+                                                      "always_cc_euler_regret", "selector_choice_counts",
+                                                      "oracle_choice_counts")}}
 
 
 def run_profile_case(args):

@@ -337,7 +337,14 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *     "bfs_device_blocks_per_sm"     grid of RST_BFS_DEVICE's level kernel in
  *                             256-thread blocks per SM, [1, 8] (default 2);
  *     "bfs_persistent_blocks_per_sm" grid of RST_BFS_PERSISTENT, at most this
- *                             many resident blocks per SM, [1, 8] (default 1).
+ *                             many resident blocks per SM, [1, 8] (default 1);
+ *     "insert_walk_limit"     rst_insert_edges runs its rounds sparsely (work
+ *                             proportional to the batch: walks from the new
+ *                             edges' ends to their roots, per-tree path
+ *                             reversal) while batches have at most n/64 edges
+ *                             and every walk stays within this many steps,
+ *                             otherwise over all vertices; [0, 2^30], 0 =
+ *                             never sparse (default 16384).
  *   Out-of-range values and unknown keys return RST_ERR_INVALID_ARG and change
  *   nothing.  Options are process-wide: set them between calls, not during.
  * rst_get_option: reads the current value of any key above into *value (host). */

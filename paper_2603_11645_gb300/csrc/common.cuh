@@ -83,6 +83,7 @@ struct Tuning {
   int bfs_bu_div = 20;  // BFS steps bottom-up while the frontier exceeds n / bfs_bu_div
   int bfsd_bps = 2;     // device-driven BFS: 256-thread blocks per SM in its grid (1..8)
   int bfsp_bps = 1;     // persistent BFS: at most this many resident blocks per SM (1..8)
+  long long insert_walk_limit = 1 << 14;  // edge insertion: sparse rounds while walks to roots stay this short (0: never)
 };
 Tuning& tuning();
 

@@ -179,6 +179,99 @@ __global__ void k_pr_fill_i32(int64_t n, int32_t* __restrict__ p, int32_t v) {
     p[i] = v;
 }
 
+// ---- sparse rounds (small insertion batches) ------------------------------
+// The same rounds with work proportional to the batch instead of n: each end
+// of an inserted edge finds its tree's root by walking up (at most `limit`
+// steps), hooks go to per-root slots, and each hooking tree reverses its own
+// path u -> root in place (paths of different trees are disjoint, so the
+// result equals the data-parallel reversal).  A walk longer than `limit` sets
+// *fallback and the round changes nothing: the caller continues with the
+// dense rounds from the same forest and round index.
+
+// Slot e of the batch's ends (uv[e]): its root, and the root's hook slot and
+// claim word reset.
+__global__ void k_sp_roots(int64_t ends, const int32_t* __restrict__ uv, int64_t n, const int32_t* __restrict__ P,
+                           int32_t* __restrict__ rep_e, unsigned long long* __restrict__ best,
+                           int32_t* __restrict__ claim, int64_t limit, int32_t* fallback, uint32_t* status) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ends; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = uv[e];
+    if (x < 0 || (int64_t)x >= n) {
+      raise_error(status, DERR_INDEX);
+      rep_e[e] = -1;
+      continue;
+    }
+    int32_t r = x;
+    int64_t steps = 0;
+    bool ok = true;
+    while (true) {
+      const int32_t p = P[r];
+      if (p == r) break;
+      if (p < 0 || (int64_t)p >= n) {
+        raise_error(status, DERR_INDEX);
+        ok = false;
+        break;
+      }
+      if (++steps > limit) {
+        *fallback = 1;
+        ok = false;
+        break;
+      }
+      r = p;
+    }
+    rep_e[e] = ok ? r : -1;
+    if (ok) {
+      best[r] = ~0ull;
+      claim[r] = 0;
+    }
+  }
+}
+
+// Proposals of the inserted edges (both orientations), as k_pr_hook_edges.
+__global__ void k_sp_hook(int64_t k, const int32_t* __restrict__ uv, const int32_t* __restrict__ rep_e, int max_rule,
+                          unsigned long long* __restrict__ best, const int32_t* __restrict__ fallback) {
+  if (*fallback) return;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = uv[2 * j], b = uv[2 * j + 1];
+    const int32_t ra = rep_e[2 * j], rb = rep_e[2 * j + 1];
+    if (ra < 0 || rb < 0 || ra == rb) continue;
+    if (max_rule ? rb > ra : rb < ra)
+      atomicMin(&best[ra], ((unsigned long long)(uint32_t)a << 32) | (uint32_t)b);
+    else
+      atomicMin(&best[rb], ((unsigned long long)(uint32_t)b << 32) | (uint32_t)a);
+  }
+}
+
+// The end that is its tree's chosen bottom vertex u (claimed once, ends may
+// repeat) reverses the path u -> root and grafts u under v: one thread per
+// hooking tree.  The path was walked by k_sp_roots within the step limit.
+__global__ void k_sp_reverse(int64_t ends, const int32_t* __restrict__ uv, const int32_t* __restrict__ rep_e,
+                             int32_t* __restrict__ P, const unsigned long long* __restrict__ best,
+                             int32_t* __restrict__ claim, int64_t limit, const int32_t* __restrict__ fallback,
+                             unsigned long long* hooks, uint32_t* status) {
+  if (*fallback) return;
+  unsigned long long cnt = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ends; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rep_e[e];
+    if (r < 0) continue;
+    const unsigned long long bk = best[r];
+    if (bk == ~0ull) continue;
+    const int32_t u = (int32_t)(bk >> 32), v = (int32_t)(bk & 0xffffffffull);
+    if (uv[e] != u || atomicExch(&claim[r], 1) != 0) continue;
+    int32_t cur = u, np = v;
+    for (int64_t steps = 0; steps <= limit; ++steps) {
+      const int32_t old = P[cur];
+      P[cur] = np;
+      if (old == cur) break;
+      np = cur;
+      cur = old;
+    }
+    ++cnt;
+  }
+  (void)status;
+  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(hooks, cnt);
+}
+
 struct PrBufs {
   int32_t* anc[kPrMaxLevels];  // anc[0] is P
   int32_t* Q;
@@ -230,7 +323,8 @@ rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A,
   while (((int64_t)1 << (levels - 2)) < n + 1 && levels < kPrMaxLevels) ++levels;
   const int64_t tiles = (A + kArcTile - 1) / kArcTile;
   auto al = [](size_t x) { return (x + 255) / 256 * 256 + 256; };
-  const size_t ws = al(n * 4) * (levels + 1) + al(n * 8) + al(n) + al(n * 4) * 2 + al((tiles + 2) * 4) + 256;
+  const size_t ws = al(n * 4) * (levels + 1) + al(n * 8) + al(n) + al(n * 4) * 2 + al((tiles + 2) * 4) + 256 +
+                    (uv ? al(2 * (size_t)k * 4) + al(4) : 0);
   RST_TRY(ensure_workspace(ws));
   RST_TRY(reset_device_error(s));
   DeviceState& st = state();
@@ -258,7 +352,36 @@ rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A,
   if (!uv && A > 0)
     RST_LAUNCH(k_arc_tile_rows<OffT>, grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
   int round = 0;
-  for (;; ++round) {
+  bool rounds_done = false;
+  const int64_t walk_limit = tuning().insert_walk_limit;
+  if (uv && k > 0 && walk_limit > 0 && k * 64 <= n) {
+    // sparse rounds while every end's walk to its root stays short
+    int32_t* rep_e = ar.take<int32_t>(2 * k);
+    int32_t* fb = ar.take<int32_t>(1);
+    if (ar.used > ar.cap) return RST_ERR_OOM;
+    RST_CUDA(cudaMemsetAsync(fb, 0, sizeof(int32_t), s));
+    const int ge = grid_for(2 * k);
+    for (;; ++round) {
+      if (round >= kPrMaxRounds) return RST_ERR_NOT_CONVERGED;
+      RST_CUDA(cudaMemsetAsync(hooks, 0, sizeof(unsigned long long), s));
+      RST_LAUNCH(k_sp_roots, ge, kBlock, 0, s)(2 * k, uv, n, b.anc[0], rep_e, b.best, b.mn, walk_limit, fb, status);
+      RST_LAUNCH(k_sp_hook, grid_for(k), kBlock, 0, s)(k, uv, rep_e, round & 1, b.best, fb);
+      RST_LAUNCH(k_sp_reverse, ge, kBlock, 0, s)(2 * k, uv, rep_e, b.anc[0], b.best, b.mn, walk_limit, fb, hooks,
+                                                status);
+      RST_CUDA(cudaGetLastError());
+      unsigned long long hf[2] = {0, 0};
+      RST_CUDA(cudaMemcpyAsync(host_scratch(16), hooks, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      RST_CUDA(cudaMemcpyAsync((char*)host_scratch(16) + 8, fb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      RST_CUDA(cudaStreamSynchronize(s));
+      std::memcpy(hf, host_scratch(16), 12);
+      if ((int32_t)hf[1] != 0) break;  // a long walk: the dense rounds take over at this round
+      if (hf[0] == 0) {
+        rounds_done = true;
+        break;
+      }
+    }
+  }
+  for (; !rounds_done; ++round) {
     if (round >= kPrMaxRounds) return RST_ERR_NOT_CONVERGED;
     int K = 0;
     RST_TRY(pr_history(b, n, s, &K));

@@ -627,6 +627,11 @@ rst_status rst_set_option(const char* key, long long value) {
     tuning().bfsp_bps = (int)value;
     return RST_OK;
   }
+  if (std::strcmp(key, "insert_walk_limit") == 0) {
+    if (value < 0 || value > (1LL << 30)) return RST_ERR_INVALID_ARG;
+    t.insert_walk_limit = value;
+    return RST_OK;
+  }
   if (std::strcmp(key, "bfs_bottom_up_divisor") == 0) {
     if (value < 1 || value > 1000000) return RST_ERR_INVALID_ARG;
     t.bfs_bu_div = (int)value;
@@ -644,6 +649,7 @@ rst_status rst_get_option(const char* key, long long* value) {
   else if (std::strcmp(key, "bfs_bottom_up_divisor") == 0) *value = t.bfs_bu_div;
   else if (std::strcmp(key, "bfs_device_blocks_per_sm") == 0) *value = t.bfsd_bps;
   else if (std::strcmp(key, "bfs_persistent_blocks_per_sm") == 0) *value = t.bfsp_bps;
+  else if (std::strcmp(key, "insert_walk_limit") == 0) *value = t.insert_walk_limit;
   else return RST_ERR_INVALID_ARG;
   return RST_OK;
 }

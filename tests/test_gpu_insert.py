@@ -92,3 +92,32 @@ def test_insert_rejects_bad_ids_and_cycles():
     ok = torch.tensor([0, 0, 2], dtype=torch.int32, device="cuda")
     rst.insert_edges(ok, torch.tensor([[1, 2]], dtype=torch.int32, device="cuda"), 0)
     assert ok.cpu().tolist() == [0, 0, 1]
+
+
+@pytest.mark.parametrize("which", ["grid", "rmat", "chain", "er"])
+@pytest.mark.parametrize("k", [1, 10, 100, 1000])
+def test_insert_small_batches_sparse_and_dense(which, k):
+    """Small batches take the sparse rounds (walks to the roots, per-tree path
+    reversal); a walk limit of 2 hands over to the dense rounds part-way, a
+    limit of 0 uses the dense rounds only: all three give the oracle's forest."""
+    import paper_2603_11645_gb300 as rst
+    g = {"er": lambda: graphs.erdos_renyi(80000, 90000, seed=71),
+         "grid": lambda: graphs.grid(400, 300, seed=72, permute=True, root="random"),
+         "rmat": lambda: graphs.rmat(16, 8, seed=73, connect=False, offsets_bits=32),
+         "chain": lambda: graphs.chain_chords(100000, 0.001, seed=74)}[which]()
+    g0, new = _dropped(g, 0.3, seed=7)
+    new = new[:k]
+    init = oracle.rst(g0.n, g0.offsets, g0.cols, g0.root)
+    src0 = np.repeat(np.arange(g0.n), np.diff(g0.offsets)).astype(np.int64)
+    keep = src0 < g0.cols
+    gk = graphs.from_edges(g.n, np.concatenate([src0[keep], new[:, 0]]),
+                           np.concatenate([g0.cols[keep].astype(np.int64), new[:, 1]]), root=g.root)
+    root = int(g.root)
+    want, _ = oracle.prrst(gk.n, gk.offsets, gk.cols, root, init=init)
+    try:
+        for limit in (1 << 14, 2, 0):
+            rst.set_option("insert_walk_limit", limit)
+            got = _gpu_insert(init, new, root)
+            assert np.array_equal(got, want), limit
+    finally:
+        rst.set_option("insert_walk_limit", 1 << 14)
