@@ -710,7 +710,7 @@ def run_selector_report(off, col, root, torch, count=24):
         choice, pred = S.select(off, col, root)
     sel_ms = (time.perf_counter() - t0) / 5 * 1e3
     rows = []
-    for g in S.family_graphs("heldout", range(count)):
+    for g in S.family_graphs("heldout", range(count)):  # the pool is idle while a chunk is timed
         o = torch.from_numpy(g.offsets).cuda()
         c = torch.from_numpy(g.cols).cuda()
         ts, cens = S.time_strategies(o, c, g.root)
@@ -740,23 +740,80 @@ def run_selector_report(off, col, root, torch, count=24):
                                                       "oracle_choice_counts")}}
 
 
+PROFILE_STRATEGIES = ("cc_euler", "bfs", "bfs_device", "bfs_persistent", "pr_rst", "cc_fast", "bcc", "verify",
+                      "depth", "euler_root", "select", "mlp", "insert")
+
+
 def run_profile_case(args):
-    """The CC+Euler step alone on a SIDE x SIDE permuted grid (seed 2), for
-    profiler captures: no timing, no oracle, no other strategies."""
+    """One path alone, W warm-up + K calls and no timing, on a SIDE x SIDE
+    permuted grid (seed 2): the command the ncu captures run.  The strategy
+    is --profile-strategy (default cc_euler); "euler_root" roots the grid's
+    spanning forest from its edge list (radix sort + tour), "select" runs the
+    selector's features and network, "mlp" the training kernels on a batch of
+    SIDE feature rows, "insert" inserts 1,000 edges into the forest of the
+    grid with 45% of its edges held back."""
+    import numpy as np
     import torch
 
     import paper_2603_11645_gb300 as rst
     from paper_2603_11645_gb300 import graphs
     side = args.profile_case
-    g = graphs.grid(side, side, seed=2, permute=True, root="random")
+    strat = args.profile_strategy
+    calls = args.warmup + args.steps
+    if args.profile_graph == "rmat":  # R-MAT of about SIDE^2 vertices, connected, int64 offsets
+        import math
+        g = graphs.rmat(int(round(math.log2(side * side))), 16, seed=3, connect=True, offsets_bits=64)
+    else:
+        g = graphs.grid(side, side, seed=2, permute=True, root="random")
     off = torch.from_numpy(g.offsets).cuda()
     col = torch.from_numpy(g.cols).cuda()
     par = torch.empty(g.n, dtype=torch.int32, device="cuda")
-    for _ in range(args.warmup + args.steps):
+    if strat in ("cc_euler", "bfs", "bfs_device", "bfs_persistent", "pr_rst", "cc_fast"):
+        for _ in range(calls):
+            rst.build(off, col, g.root, strat, out=par)
+    elif strat == "bcc":
+        for _ in range(calls):
+            rst.bcc(off, col)
+    elif strat == "verify":
         rst.build(off, col, g.root, "cc_euler", out=par)
+        for _ in range(calls):
+            rst.verify(off, col, g.root, par)
+    elif strat == "depth":
+        rst.build(off, col, g.root, "cc_euler", out=par)
+        for _ in range(calls):
+            rst.tree_depth(par)
+    elif strat == "euler_root":
+        labels, uv, T = rst.cc(off, col)
+        uv = uv.clone()
+        for _ in range(calls):
+            rst.euler_root(g.n, uv, g.root, with_rank=True)
+    elif strat == "select":
+        from paper_2603_11645_gb300 import selector as S
+        S.load_default()
+        for _ in range(calls):
+            S.select(off, col, g.root)
+    elif strat == "mlp":
+        from paper_2603_11645_gb300 import selector as S
+        rng = np.random.default_rng(3)
+        X = rng.normal(size=(side, S.F))
+        Tt = np.exp(rng.normal(size=(side, S.O)))
+        for _ in range(calls):
+            S.train(X, Tt, epochs=5, lr=1e-3, seed=1)
+    elif strat == "insert":
+        src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets))
+        c64 = g.cols.astype(np.int64)
+        fwd = src < c64
+        lo, hi = src[fwd], c64[fwd]
+        drop = ((lo * 0x9E3779B1 + hi * 0x85EBCA77 + 11) % 1000003) < 450000
+        g0 = graphs.from_edges(g.n, lo[~drop], hi[~drop], root=g.root)
+        uv = torch.from_numpy(np.stack([lo[drop], hi[drop]], 1)[:1000].astype(np.int32)).cuda()
+        base = rst.build(torch.from_numpy(g0.offsets).cuda(), torch.from_numpy(g0.cols).cuda(), g.root)
+        work = torch.empty_like(base)
+        for _ in range(calls):
+            work.copy_(base)
+            rst.insert_edges(work, uv, g.root)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": f"grid {side}x{side}", "n": g.n, "A": g.A,
-                      "launches": args.warmup + args.steps}))
+    print(json.dumps({"profile_case": g.name, "strategy": strat, "n": g.n, "A": g.A, "calls": calls}))
 
 
 # ----------------------------------------------------------------- reference arm (the oracle)
@@ -819,8 +876,13 @@ def main():
     ap.add_argument("--batch-hi", type=int, default=4096,
                     help="largest vertex count of the batch's graphs (262144: the literal 1K-256K size law)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="SIDE",
-                    help="only run the CC+Euler step (W warm-up + K steps, no timing) on a SIDE x SIDE "
-                         "grid of the headline family; the command the ncu captures use")
+                    help="only run one path (W warm-up + K calls, no timing) on a SIDE x SIDE grid of the "
+                         "headline family; the command the ncu captures use")
+    ap.add_argument("--profile-strategy", default="cc_euler", choices=PROFILE_STRATEGIES,
+                    help="the path --profile-case runs")
+    ap.add_argument("--profile-graph", default="grid", choices=["grid", "rmat"],
+                    help="the graph --profile-case runs on: the permuted SIDE x SIDE grid, or R-MAT of "
+                         "scale round(log2 SIDE^2) connected to vertex 0")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

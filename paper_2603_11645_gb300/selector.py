@@ -108,32 +108,25 @@ def _worker_init(threads: int):
 
 
 def family_graphs(split: str, indices, workers: int | None = None):
-    """The split's graphs in index order, generated by a pool of spawned
-    worker processes (no CUDA in them) while the caller consumes earlier
-    ones; at most two graphs per worker are in flight or waiting."""
-    import collections
+    """The split's graphs in index order.  They are generated a chunk at a time
+    by a pool of spawned worker processes (no CUDA in them); the pool is idle
+    while the caller consumes a chunk, so timings taken meanwhile see no
+    competing host load (the host-stepped strategies are sensitive to it)."""
     import multiprocessing as mp
     indices = list(indices)
     cores = os.cpu_count() or 2
-    workers = workers or max(1, min(12, cores - 2))
+    workers = workers or max(1, min(8, cores // 2))
     if workers <= 1 or len(indices) <= 1:
         for i in indices:
             yield family_graph(i, split)
         return
     ctx = mp.get_context("spawn")
-    with ctx.Pool(workers, initializer=_worker_init, initargs=(max(2, cores // 2),)) as pool:
-        pending = collections.deque()
-        it = iter(indices)
-        for i in it:
-            pending.append(pool.apply_async(family_graph, (i, split)))
-            if len(pending) >= 2 * workers:
-                break
-        while pending:
-            g = pending.popleft().get()
-            nxt = next(it, None)
-            if nxt is not None:
-                pending.append(pool.apply_async(family_graph, (nxt, split)))
-            yield g
+    chunk = 4 * workers
+    with ctx.Pool(workers, initializer=_worker_init, initargs=(max(1, cores // workers),)) as pool:
+        for c0 in range(0, len(indices), chunk):
+            part = [(i, split) for i in indices[c0:c0 + chunk]]
+            for g in pool.map(_family_graph_args, part, chunksize=1):
+                yield g
 
 
 # ------------------------------------------------------------------ GPU calls
@@ -149,7 +142,7 @@ def features(off, col, root: int) -> np.ndarray:
     return f
 
 
-def time_strategies(off, col, root: int, reps: int = 2):
+def time_strategies(off, col, root: int, reps: int = 3):
     """Median wall time (s, CUDA events) of each strategy; BFS capped."""
     import torch
     from . import build, RstError
@@ -180,7 +173,7 @@ def time_strategies(off, col, root: int, reps: int = 2):
     return times, censored
 
 
-def generate_dataset(split: str, count: int, path: str, reps: int = 2, log_every: int = 100):
+def generate_dataset(split: str, count: int, path: str, reps: int = 3, log_every: int = 100):
     """Features and timings of `count` graphs of the split, written as CSV."""
     import torch
     rows = []

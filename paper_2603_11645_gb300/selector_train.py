@@ -51,10 +51,10 @@ def main():
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--heldout", type=int, default=200)
     ap.add_argument("--data-dir", default=os.path.join(os.path.dirname(__file__), "selector_data"))
-    ap.add_argument("--epochs", type=int, default=4000)
+    ap.add_argument("--epochs", type=int, default=8000)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--out", default=S.WEIGHTS_PATH)
     args = ap.parse_args()
     os.makedirs(args.data_dir, exist_ok=True)
