@@ -344,7 +344,11 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *                             reversal) while batches have at most n/64 edges
  *                             and every walk stays within this many steps,
  *                             otherwise over all vertices; [0, 2^30], 0 =
- *                             never sparse (default 16384).
+ *                             never sparse (default 16384);
+ *     "euler_block"           threads per block of the Euler stage's
+ *                             grid-stride kernels (run boundaries, successors,
+ *                             parents from ranks): 128, 256 or 512 (default
+ *                             256).
  *   Out-of-range values and unknown keys return RST_ERR_INVALID_ARG and change
  *   nothing.  Options are process-wide: set them between calls, not during.
  * rst_get_option: reads the current value of any key above into *value (host). */

@@ -11,7 +11,9 @@ launches and samples, never a result:
   than n / divisor vertices;
 * ``bfs_device_blocks_per_sm`` / ``bfs_persistent_blocks_per_sm``: the grid of
   the device-driven BFS variants (a small grid keeps the per-level cost of
-  deep, narrow searches low; a large one feeds the wide bottom-up levels).
+  deep, narrow searches low; a large one feeds the wide bottom-up levels);
+* ``euler_block``: the block size (128/256/512) of the tour's grid-stride
+  kernels.
 
 They stand where Section III-C fixes its own launch granularity empirically
 (five pointer jumps per global synchronisation for PR-RST).  ``tune`` times
@@ -36,12 +38,14 @@ KNOBS = {
     "bfs_bottom_up_divisor": [5, 10, 20, 40, 80],
     "bfs_device_blocks_per_sm": [1, 2, 4, 8],
     "bfs_persistent_blocks_per_sm": [1, 2, 4],
+    "euler_block": [128, 256, 512],
 }
 DEFAULTS = {"round_blocks_per_sm": 8, "lr_spacing": 16, "bfs_bottom_up_divisor": 20,
-            "bfs_device_blocks_per_sm": 2, "bfs_persistent_blocks_per_sm": 1}
+            "bfs_device_blocks_per_sm": 2, "bfs_persistent_blocks_per_sm": 1, "euler_block": 256}
 # the strategy whose time decides each knob
 KNOB_STRATEGY = {"round_blocks_per_sm": "cc_euler", "lr_spacing": "cc_euler", "bfs_bottom_up_divisor": "bfs",
-                 "bfs_device_blocks_per_sm": "bfs_device", "bfs_persistent_blocks_per_sm": "bfs_persistent"}
+                 "bfs_device_blocks_per_sm": "bfs_device", "bfs_persistent_blocks_per_sm": "bfs_persistent",
+                 "euler_block": "cc_euler"}
 
 # size buckets by log2 n (half-open), with the log2 n of the graph tuned on
 BUCKETS = [(0, 14, 12), (14, 18, 16), (18, 22, 20), (22, 31, 24)]

@@ -215,7 +215,9 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   const bool prune = rank_out == nullptr && T > 0;
   uint8_t* leaf = prune ? ar.take<uint8_t>(n) : nullptr;
   if (prune && !leaf) return RST_ERR_OOM;
-  RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, rk, is_root, toff, parent_out,
+  // the plain grid-stride kernels of the tour take the tuned block size
+  const int eb = tuning().euler_block;
+  RST_LAUNCH(k_toff<OffT>, grid_for(n + 1, eb, 2048 / eb), eb, 0, s)(off, n, rk, is_root, toff, parent_out,
                                                           leaf);
   prof_mark(s, "k_toff");
   int64_t N = 2 * T;
@@ -223,7 +225,7 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
     RST_LAUNCH(k_prune_leaves, grid_for((T + kEuPer - 1) / kEuPer, kBlock, kEuBlocksPerSm), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
     prof_mark(s, "k_prune_leaves");
     RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
-    RST_LAUNCH(k_toff<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, rk, is_root, toff, nullptr,
+    RST_LAUNCH(k_toff<OffT>, grid_for(n + 1, eb, 2048 / eb), eb, 0, s)(off, n, rk, is_root, toff, nullptr,
                                                             nullptr);
     unsigned long long left = 0;
     RST_CUDA(cudaMemcpyAsync(host_scratch(8), &rk[W].y, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -242,8 +244,8 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   int32_t* succ = ar.take<int32_t>(N);
   uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
   if (!succ || !R) return RST_ERR_OOM;
-  const int gT = grid_for(T);
-  RST_LAUNCH(k_pairs_succ, gT, kBlock, 0, s)(T, cc->pairs, rk, toff, is_root, succ);
+  const int gT = grid_for(T, eb, 2048 / eb);
+  RST_LAUNCH(k_pairs_succ, gT, eb, 0, s)(T, cc->pairs, rk, toff, is_root, succ);
   prof_mark(s, "k_pairs_succ");
   RST_CUDA(cudaGetLastError());
   if (succ_view) *succ_view = succ;  // stays valid while the arena is not reset
@@ -252,11 +254,11 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   LrFirstLevel lv;
   RST_TRY(list_rank(ar, N, succ, nullptr, heads, cc->nroots, R, s, rank_out ? nullptr : &lv));
   if (lv.valid) {
-    RST_LAUNCH(k_parent_from_owner, gT, kBlock, 0, s)(T, cc->pairs, lv.ol, lv.ol32, lv.fbits, lv.spos, lv.S,
+    RST_LAUNCH(k_parent_from_owner, gT, eb, 0, s)(T, cc->pairs, lv.ol, lv.ol32, lv.fbits, lv.spos, lv.S,
                                                       lv.visited, lv.N, parent_out, state().status);
     prof_mark(s, "k_parent_from_owner");
   } else {
-    RST_LAUNCH(k_parent_from_rank, gT, kBlock, 0, s)(T, cc->pairs, R, parent_out);
+    RST_LAUNCH(k_parent_from_rank, gT, eb, 0, s)(T, cc->pairs, R, parent_out);
     prof_mark(s, "k_parent_from_rank");
   }
   RST_CUDA(cudaGetLastError());

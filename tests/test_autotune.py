@@ -35,6 +35,7 @@ def test_option_defaults_roundtrip_and_rejects(rst_lib):
                      ("round_blocks_per_sm", 0), ("round_blocks_per_sm", 17),
                      ("bfs_bottom_up_divisor", 0), ("bfs_device_blocks_per_sm", 0),
                      ("bfs_device_blocks_per_sm", 9), ("bfs_persistent_blocks_per_sm", 0),
+                     ("euler_block", 64), ("euler_block", 384), ("insert_walk_limit", -1),
                      ("no_such_knob", 1)]:
         with pytest.raises(rst.RstError):
             rst.set_option(key, bad)
@@ -107,7 +108,7 @@ KNOB_VALUES = [("lr_spacing", 32), ("lr_spacing", 512), ("round_blocks_per_sm", 
                ("round_blocks_per_sm", 16), ("bfs_bottom_up_divisor", 1),
                ("bfs_bottom_up_divisor", 100000), ("bfs_device_blocks_per_sm", 1),
                ("bfs_device_blocks_per_sm", 8), ("bfs_persistent_blocks_per_sm", 1),
-               ("bfs_persistent_blocks_per_sm", 8)]
+               ("bfs_persistent_blocks_per_sm", 8), ("euler_block", 128), ("euler_block", 512)]
 
 
 @pytest.mark.gpu
