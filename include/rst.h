@@ -348,7 +348,10 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *     "euler_block"           threads per block of the Euler stage's
  *                             grid-stride kernels (run boundaries, successors,
  *                             parents from ranks): 128, 256 or 512 (default
- *                             256).
+ *                             256);
+ *     "pr_levels_per_launch"  PR-RST computes this many pointer-jumping
+ *                             levels per launch and host check, [1, 3]
+ *                             (default 1; each level is recomputed exactly).
  *   Out-of-range values and unknown keys return RST_ERR_INVALID_ARG and change
  *   nothing.  Options are process-wide: set them between calls, not during.
  * rst_get_option: reads the current value of any key above into *value (host). */

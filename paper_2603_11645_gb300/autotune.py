@@ -13,7 +13,10 @@ launches and samples, never a result:
   the device-driven BFS variants (a small grid keeps the per-level cost of
   deep, narrow searches low; a large one feeds the wide bottom-up levels);
 * ``euler_block``: the block size (128/256/512) of the tour's grid-stride
-  kernels.
+  kernels;
+* ``pr_levels_per_launch``: PR-RST's pointer-jumping levels per launch and
+  host check (1..3), the counterpart of Section III-C's several pointer jumps
+  per global synchronisation.
 
 They stand where Section III-C fixes its own launch granularity empirically
 (five pointer jumps per global synchronisation for PR-RST).  ``tune`` times
@@ -39,13 +42,15 @@ KNOBS = {
     "bfs_device_blocks_per_sm": [1, 2, 4, 8],
     "bfs_persistent_blocks_per_sm": [1, 2, 4],
     "euler_block": [128, 256, 512],
+    "pr_levels_per_launch": [1, 2, 3],
 }
 DEFAULTS = {"round_blocks_per_sm": 8, "lr_spacing": 16, "bfs_bottom_up_divisor": 20,
-            "bfs_device_blocks_per_sm": 2, "bfs_persistent_blocks_per_sm": 1, "euler_block": 256}
+            "bfs_device_blocks_per_sm": 2, "bfs_persistent_blocks_per_sm": 1, "euler_block": 256,
+            "pr_levels_per_launch": 1}
 # the strategy whose time decides each knob
 KNOB_STRATEGY = {"round_blocks_per_sm": "cc_euler", "lr_spacing": "cc_euler", "bfs_bottom_up_divisor": "bfs",
                  "bfs_device_blocks_per_sm": "bfs_device", "bfs_persistent_blocks_per_sm": "bfs_persistent",
-                 "euler_block": "cc_euler"}
+                 "euler_block": "cc_euler", "pr_levels_per_launch": "pr_rst"}
 
 # size buckets by log2 n (half-open), with the log2 n of the graph tuned on
 BUCKETS = [(0, 14, 12), (14, 18, 16), (18, 22, 20), (22, 31, 24)]

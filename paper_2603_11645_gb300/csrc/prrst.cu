@@ -46,6 +46,41 @@ __global__ void k_pr_jump(int64_t n, const int32_t* __restrict__ low, int32_t* _
   if (__any_sync(0xffffffffu, ch) && (threadIdx.x & 31) == 0) *changed = 1;
 }
 
+// Several doubling levels per launch (the paper's several pointer jumps per
+// global synchronisation): level k+i of x is computed from level k alone, by
+// recomputing the intermediate ancestors it needs (2^i dependent reads), so
+// every level written is exactly the 2^(k+i)-th ancestor.  changed[i-1] is
+// set when level k+i differs from level k+i-1 somewhere.
+constexpr int kPrMaxPerLaunch = 3;
+__global__ void k_pr_jump_multi(int64_t n, const int32_t* __restrict__ low, int32_t* __restrict__ up1,
+                                int32_t* __restrict__ up2, int32_t* __restrict__ up3, int levels,
+                                int32_t* changed);
+__global__ void k_pr_jump_multi(int64_t n, const int32_t* __restrict__ low, int32_t* __restrict__ up1,
+                                int32_t* __restrict__ up2, int32_t* __restrict__ up3, int levels,
+                                int32_t* changed) {
+  bool ch[kPrMaxPerLaunch] = {false, false, false};
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a0 = low[x];
+    const int32_t a1 = low[a0];
+    up1[x] = a1;
+    ch[0] = ch[0] || (a1 != a0);
+    if (levels >= 2) {
+      // level k+2 of x = level k+1 of a1 = two level-k steps from a1
+      const int32_t a2 = low[low[a1]];
+      up2[x] = a2;
+      ch[1] = ch[1] || (a2 != a1);
+      if (levels >= 3) {
+        // level k+3 of x = level k+2 of a2 = four level-k steps from a2
+        const int32_t a3 = low[low[low[low[a2]]]];
+        up3[x] = a3;
+        ch[2] = ch[2] || (a3 != a2);
+      }
+    }
+  }
+  for (int i = 0; i < kPrMaxPerLaunch; ++i)
+    if (__any_sync(0xffffffffu, ch[i]) && (threadIdx.x & 31) == 0) changed[i] = 1;
+}
+
 __global__ void k_pr_fill_u64(int64_t n, unsigned long long* __restrict__ p) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
     p[v] = ~0ull;
@@ -285,19 +320,33 @@ struct PrBufs {
 };
 
 // anc[1..K] by pointer jumping until nothing changes; returns K (rep = anc[K]).
+// tuning().pr_levels levels are computed per launch (and per host check).
 static rst_status pr_history(PrBufs& b, int64_t n, cudaStream_t s, int* K_out) {
   const int g = grid_for(n);
+  const int per = tuning().pr_levels;
   int k = 0;
   while (true) {
     if (k + 1 >= b.levels) return RST_ERR_NOT_CONVERGED;
-    RST_CUDA(cudaMemsetAsync(b.flag, 0, sizeof(int32_t), s));
-    RST_LAUNCH(k_pr_jump, g, kBlock, 0, s)(n, b.anc[k], b.anc[k + 1], b.flag);
-    ++k;
-    int32_t changed = 0;
-    RST_CUDA(cudaMemcpyAsync(host_scratch(4), b.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    int j = per;
+    if (k + j >= b.levels) j = b.levels - 1 - k;
+    RST_CUDA(cudaMemsetAsync(b.flag, 0, kPrMaxPerLaunch * sizeof(int32_t), s));
+    if (j == 1) {
+      RST_LAUNCH(k_pr_jump, g, kBlock, 0, s)(n, b.anc[k], b.anc[k + 1], b.flag);
+    } else {
+      RST_LAUNCH(k_pr_jump_multi, g, kBlock, 0, s)(n, b.anc[k], b.anc[k + 1], b.anc[k + 2],
+                                                   j >= 3 ? b.anc[k + 3] : nullptr, j, b.flag);
+    }
+    int32_t changed[kPrMaxPerLaunch] = {0, 0, 0};
+    RST_CUDA(cudaMemcpyAsync(host_scratch(16), b.flag, j * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RST_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(&changed, host_scratch(4), sizeof(int32_t));
-    if (!changed) break;
+    std::memcpy(changed, host_scratch(16), j * sizeof(int32_t));
+    int i = 0;
+    while (i < j && changed[i]) ++i;
+    if (i < j) {  // level k+i+1 equals level k+i: the fixed point
+      k += i + 1;
+      break;
+    }
+    k += j;
   }
   *K_out = k;
   return RST_OK;
@@ -338,7 +387,7 @@ rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A,
   b.graft = ar.take<int32_t>(n);
   b.mn = ar.take<int32_t>(n);
   b.tile_row = ar.take<int32_t>(tiles + 2);
-  b.flag = ar.take<int32_t>(1);
+  b.flag = ar.take<int32_t>(kPrMaxPerLaunch);
   if (!b.flag) return RST_ERR_OOM;
   unsigned long long* hooks = dev_counter(0);
   const int g = grid_for(n);

@@ -627,6 +627,11 @@ rst_status rst_set_option(const char* key, long long value) {
     tuning().bfsp_bps = (int)value;
     return RST_OK;
   }
+  if (std::strcmp(key, "pr_levels_per_launch") == 0) {
+    if (value < 1 || value > 3) return RST_ERR_INVALID_ARG;
+    t.pr_levels = (int)value;
+    return RST_OK;
+  }
   if (std::strcmp(key, "euler_block") == 0) {
     if (value != 128 && value != 256 && value != 512) return RST_ERR_INVALID_ARG;
     t.euler_block = (int)value;
@@ -656,6 +661,7 @@ rst_status rst_get_option(const char* key, long long* value) {
   else if (std::strcmp(key, "bfs_persistent_blocks_per_sm") == 0) *value = t.bfsp_bps;
   else if (std::strcmp(key, "insert_walk_limit") == 0) *value = t.insert_walk_limit;
   else if (std::strcmp(key, "euler_block") == 0) *value = t.euler_block;
+  else if (std::strcmp(key, "pr_levels_per_launch") == 0) *value = t.pr_levels;
   else return RST_ERR_INVALID_ARG;
   return RST_OK;
 }

@@ -36,6 +36,7 @@ def test_option_defaults_roundtrip_and_rejects(rst_lib):
                      ("bfs_bottom_up_divisor", 0), ("bfs_device_blocks_per_sm", 0),
                      ("bfs_device_blocks_per_sm", 9), ("bfs_persistent_blocks_per_sm", 0),
                      ("euler_block", 64), ("euler_block", 384), ("insert_walk_limit", -1),
+                     ("pr_levels_per_launch", 0), ("pr_levels_per_launch", 4),
                      ("no_such_knob", 1)]:
         with pytest.raises(rst.RstError):
             rst.set_option(key, bad)
@@ -108,7 +109,8 @@ KNOB_VALUES = [("lr_spacing", 32), ("lr_spacing", 512), ("round_blocks_per_sm", 
                ("round_blocks_per_sm", 16), ("bfs_bottom_up_divisor", 1),
                ("bfs_bottom_up_divisor", 100000), ("bfs_device_blocks_per_sm", 1),
                ("bfs_device_blocks_per_sm", 8), ("bfs_persistent_blocks_per_sm", 1),
-               ("bfs_persistent_blocks_per_sm", 8), ("euler_block", 128), ("euler_block", 512)]
+               ("bfs_persistent_blocks_per_sm", 8), ("euler_block", 128), ("euler_block", 512),
+               ("pr_levels_per_launch", 2), ("pr_levels_per_launch", 3)]
 
 
 @pytest.mark.gpu
@@ -122,6 +124,9 @@ def test_knob_leaves_results_unchanged(rst_lib, knob, value):
         if strategy.startswith("bfs"):
             par = rst.build(off, col, g.root, strategy).cpu().numpy()
             _, want = oracle.bfs(g.n, g.offsets, g.cols, g.root)
+        elif strategy == "pr_rst":
+            par = rst.build(off, col, g.root, "pr_rst").cpu().numpy()
+            want, _ = oracle.prrst(g.n, g.offsets, g.cols, g.root)
         else:
             par = rst.build(off, col, g.root, "cc_euler").cpu().numpy()
             want = oracle.rst(g.n, g.offsets, g.cols, g.root)
