@@ -549,47 +549,57 @@ def run_batch(args, dev, stream, rst, graphs, torch, rank=0, world=1, cpu_on=Fal
 
 
 def run_insert(g, dev, stream, rst, graphs, torch, reps, rebuild_ms):
-    """Rooted spanning forest of g minus a seeded 45% of its edges (CC+Euler;
-    below the square lattice's bond threshold, so a forest of many trees),
-    then batches of the held-back edges inserted (rst_insert_edges): 1,000,
-    100,000 (seeded subsets) and all of them, each beside a full CC+Euler
-    rebuild of the graph."""
+    """Edge insertions (rst_insert_edges with the canonical flag: the forests
+    come from rst_build).  Two forests of the headline grid: 45% of its edges
+    held back (55% kept, above the square lattice's bond-percolation
+    threshold of 50%: one giant, deep tree beside ~1M small ones) and 60% held
+    back (40% kept, below it: small trees only).  Batches of the held-back
+    edges in a seeded order (1,000, 100,000, and for the first forest all of
+    them), each beside a full CC+Euler rebuild of the graph."""
     import numpy as np
     src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.offsets))
     col = g.cols.astype(np.int64)
     fwd = src < col
     lo, hi = src[fwd], col[fwd]
-    drop = ((lo * 0x9E3779B1 + hi * 0x85EBCA77 + 11) % 1000003) < 450000
-    g0 = graphs.from_edges(g.n, lo[~drop], hi[~drop], root=g.root)
-    held = np.stack([lo[drop], hi[drop]], 1).astype(np.int32)
-    held = held[np.random.default_rng(12).permutation(len(held))]
-    off0 = torch.from_numpy(g0.offsets).to(dev)
-    col0 = torch.from_numpy(g0.cols).to(dev)
-    base = rst.build(off0, col0, g.root, "cc_euler")
-    work = torch.empty_like(base)
-    batches = {}
-    for k in (1000, 100000, len(held)):
-        uv = torch.from_numpy(np.ascontiguousarray(held[:k])).to(dev)
-        ts = []
-        for i in range(reps + 1):
-            work.copy_(base)
-            torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rst.insert_edges(work, uv, g.root)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            if i:
-                ts.append(e0.elapsed_time(e1))
-        ms = statistics.median(ts)
-        batches[str(k)] = {"ms": ms, "rebuild_ms": rebuild_ms, "speedup_over_rebuild": rebuild_ms / ms}
-    return {"workload": f"4096x4096 grid forest with {int(drop.sum())} edges (45%) held back, "
-                        f"then batches of them inserted (seeded order)", "inserted_max": int(drop.sum()),
-            "batches": batches,
-            "trees_before": int((base.cpu() == torch.arange(g.n, dtype=torch.int32)).sum()),
-            "note": "PR-RST rounds from the existing forest over the inserted edges only; batches of at most "
-                    "n/64 edges run them sparsely (work proportional to the batch)"}
+    h = (lo * 0x9E3779B1 + hi * 0x85EBCA77 + 11) % 1000003
+    out = {"note": "PR-RST rounds from the existing forest over the inserted edges only; batches of at most "
+                   "n/64 edges run them sparsely (walks to roots, per-tree path reversal) while every walk "
+                   "stays within insert_walk_limit steps, and the canonical flag re-roots only merged trees"}
+    for name, thr, sizes in (("held_back_45pct", 450000, (1000, 100000, None)),
+                             ("held_back_60pct", 600000, (1000, 100000))):
+        drop = h < thr
+        g0 = graphs.from_edges(g.n, lo[~drop], hi[~drop], root=g.root)
+        held = np.stack([lo[drop], hi[drop]], 1).astype(np.int32)
+        held = held[np.random.default_rng(12).permutation(len(held))]
+        off0 = torch.from_numpy(g0.offsets).to(dev)
+        col0 = torch.from_numpy(g0.cols).to(dev)
+        base = rst.build(off0, col0, g.root, "cc_euler")
+        _, height = rst.tree_depth(base, want_depths=False)
+        work = torch.empty_like(base)
+        batches = {}
+        for k in sizes:
+            k = len(held) if k is None else k
+            uv = torch.from_numpy(np.ascontiguousarray(held[:k])).to(dev)
+            ts = []
+            for i in range(reps + 1):
+                work.copy_(base)
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rst.insert_edges(work, uv, g.root, canonical=True)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                if i:
+                    ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            batches[str(k)] = {"ms": ms, "rebuild_ms": rebuild_ms, "speedup_over_rebuild": rebuild_ms / ms}
+        out[name] = {"workload": f"4096x4096 grid forest with {int(drop.sum())} edges held back, then batches "
+                                 f"of them inserted", "trees_before":
+                         int((base.cpu() == torch.arange(g.n, dtype=torch.int32)).sum()),
+                     "height_before": int(height), "batches": batches}
+        del off0, col0, base, work
+    return out
 
 
 def _time(fn, reps, torch, dev, stream, flush=None):

@@ -233,10 +233,23 @@ rst_status rst_bcc(const void *csr_offsets, int offsets_bits, const int32_t *csr
  * (minimum rule, then maximum, alternating; each tree takes its eligible
  * edge with the smallest (u, v) key), which gives the same result as PR-RST
  * rounds over all edges of the new graph started from that forest.
- * Returns RST_ERR_DEVICE for an id outside [0, n) and RST_ERR_NOT_CONVERGED
- * when `parent` holds a cycle. */
+ *   flags   0, or RST_INSERT_CANONICAL: the caller declares that the input
+ *           is already in this canonical form for `root` (the tree holding
+ *           root rooted at root, every other tree at its minimum vertex), as
+ *           rst_build and rst_insert_edges return it.  Then only the trees the
+ *           batch merges are re-rooted at the end (work proportional to the
+ *           batch when their paths are short); for any other input the
+ *           output is unspecified.  Without the flag every tree is re-rooted,
+ *           whatever the input.
+ * Batches of at most n/64 edges run their rounds sparsely: each end walks to
+ * its root (at most the "insert_walk_limit" option's steps; a longer walk
+ * hands the rounds to the dense version, over all vertices, at the same
+ * round, with the same result).
+ * Returns RST_ERR_DEVICE for an id outside [0, n), RST_ERR_INVALID_ARG for an
+ * unknown flag and RST_ERR_NOT_CONVERGED when `parent` holds a cycle. */
+enum { RST_INSERT_CANONICAL = 1 };
 rst_status rst_insert_edges(int64_t n, int32_t *parent, const int32_t *new_uv, int64_t k, int32_t root,
-                            rst_stream_t stream);
+                            unsigned int flags, rst_stream_t stream);
 
 /* rst_tree_depth -- depth of every vertex of a rooted forest, and its height
  * (Section IV-B, Fig. 2: the trees of connectivity-based strategies are

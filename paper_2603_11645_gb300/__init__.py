@@ -46,7 +46,7 @@ def lib():
         L.rst_build_batch.argtypes = [P, I, P, P, P, I32, P, I, P, P]
         L.rst_tree_depth.argtypes = [P, I64, P, P, P]
         L.rst_bcc.argtypes = [P, I, P, I64, I64, P, P, P, P]
-        L.rst_insert_edges.argtypes = [I64, P, P, I64, I32, P]
+        L.rst_insert_edges.argtypes = [I64, P, P, I64, I32, ctypes.c_uint, P]
         L.rst_set_option.argtypes = [ctypes.c_char_p, ctypes.c_longlong]
         L.rst_get_option.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong)]
         L.rst_status_string.argtypes = [I]
@@ -202,16 +202,19 @@ def bcc(offsets, cols, want_cut: bool = True, stream=None):
     return label, cut, int(nb.value)
 
 
-def insert_edges(parent, new_uv, root: int, stream=None):
+def insert_edges(parent, new_uv, root: int, canonical: bool = False, stream=None):
     """Updates the rooted spanning forest `parent` (int32 CUDA tensor, in
     place) after inserting the undirected edges of `new_uv` (int32 CUDA
-    tensor of shape (k, 2)); returns `parent`."""
+    tensor of shape (k, 2)); returns `parent`.  canonical=True declares that
+    `parent` is in the canonical form rst_build returns for `root`
+    (RST_INSERT_CANONICAL)."""
     import torch
     assert parent.is_cuda and parent.dtype == torch.int32 and parent.is_contiguous()
     uv = new_uv.contiguous()
     assert uv.is_cuda and uv.dtype == torch.int32 and (uv.numel() == 0 or uv.shape[-1] == 2)
     k = uv.numel() // 2
     code = lib().rst_insert_edges(parent.numel(), ctypes.c_void_p(parent.data_ptr()),
-                                  ctypes.c_void_p(uv.data_ptr()) if k else None, k, int(root), _stream(stream))
+                                  ctypes.c_void_p(uv.data_ptr()) if k else None, k, int(root),
+                                  1 if canonical else 0, _stream(stream))
     _check("rst_insert_edges", code)
     return parent

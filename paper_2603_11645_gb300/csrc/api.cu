@@ -215,12 +215,13 @@ rst_status rst_bcc(const void* csr_offsets, int offsets_bits, const int32_t* csr
 }
 
 rst_status rst_insert_edges(int64_t n, int32_t* parent, const int32_t* new_uv, int64_t k, int32_t root,
-                            rst_stream_t stream) {
+                            unsigned int flags, rst_stream_t stream) {
   if (n <= 0 || n >= ((int64_t)1 << 30) || k < 0) return RST_ERR_INVALID_ARG;
   if (!parent || (k > 0 && !new_uv) || root < 0 || root >= n) return RST_ERR_INVALID_ARG;
+  if (flags & ~(unsigned int)RST_INSERT_CANONICAL) return RST_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   CallGuard g;
-  return run_prrst_insert(n, parent, new_uv, k, root, s);
+  return run_prrst_insert(n, parent, new_uv, k, root, (flags & RST_INSERT_CANONICAL) != 0, s);
 }
 
 rst_status rst_tree_depth(const int32_t* parent, int64_t n, int32_t* depth_out, int64_t* max_out,

@@ -307,6 +307,94 @@ __global__ void k_sp_reverse(int64_t ends, const int32_t* __restrict__ uv, const
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(hooks, cnt);
 }
 
+// ---- sparse final re-rooting (the caller declares the input canonical) ----
+// Every tree of the input not holding `root` is rooted at its minimum vertex
+// and the one holding `root` at root, so only trees the batch merged need
+// re-rooting: a merged tree not holding root at the smallest original root
+// among its parts, the tree holding root at root.  Ends are the batch's 2k
+// ends plus `root` itself (slot 2k).
+
+__device__ __forceinline__ int32_t sp_end(const int32_t* __restrict__ uv, int64_t ends, int32_t root, int64_t e) {
+  return e < ends ? uv[e] : root;
+}
+
+// Current root of every end (bounded walk); the merged trees' slots reset.
+__global__ void k_sp_final_roots(int64_t ends, const int32_t* __restrict__ uv, int32_t root, int64_t n,
+                                 const int32_t* __restrict__ P, int32_t* __restrict__ cur_e,
+                                 int32_t* __restrict__ tmin, int32_t* __restrict__ claim, int64_t limit,
+                                 int32_t* fallback) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= ends; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = sp_end(uv, ends, root, e);
+    int32_t r = -1;
+    if (x >= 0 && (int64_t)x < n) {
+      r = x;
+      for (int64_t steps = 0;; ++steps) {
+        const int32_t p = P[r];
+        if (p == r) break;
+        if (steps >= limit || p < 0 || (int64_t)p >= n) {
+          *fallback = 1;
+          r = -1;
+          break;
+        }
+        r = p;
+      }
+    }
+    cur_e[e] = r;
+    if (r >= 0) {
+      tmin[r] = INT_MAX;
+      claim[r] = 0;
+    }
+  }
+}
+
+// The smallest original root among each merged tree's parts (-1 marks the
+// tree holding root: its target is root).
+__global__ void k_sp_final_min(int64_t ends, const int32_t* __restrict__ cur_e, const int32_t* __restrict__ orig_e,
+                               int32_t* __restrict__ tmin) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= ends; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = cur_e[e];
+    if (c < 0) continue;
+    atomicMin(&tmin[c], e == ends ? -1 : orig_e[e]);
+  }
+}
+
+// One thread per merged tree re-roots it at its target: the path target ->
+// current root is walked once read-only (within the limit, else the dense
+// re-rooting takes over and this tree is left alone), then reversed.
+__global__ void k_sp_final_reverse(int64_t ends, const int32_t* __restrict__ cur_e, const int32_t* __restrict__ tmin,
+                                   int32_t root, int32_t* __restrict__ P, int32_t* __restrict__ claim, int64_t limit,
+                                   int32_t* fallback) {
+  if (*fallback) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= ends; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = cur_e[e];
+    if (c < 0 || atomicExch(&claim[c], 1) != 0) continue;
+    const int32_t t = tmin[c] < 0 ? root : tmin[c];
+    if (t == c) continue;
+    int32_t x = t;
+    bool ok = false;
+    for (int64_t steps = 0; steps <= limit; ++steps) {
+      const int32_t p = P[x];
+      if (p == x) {
+        ok = (x == c);
+        break;
+      }
+      x = p;
+    }
+    if (!ok) {
+      *fallback = 1;
+      continue;
+    }
+    int32_t cur = t, np = t;
+    for (int64_t steps = 0; steps <= limit; ++steps) {
+      const int32_t old = P[cur];
+      P[cur] = np;
+      if (old == cur) break;
+      np = cur;
+      cur = old;
+    }
+  }
+}
+
 struct PrBufs {
   int32_t* anc[kPrMaxLevels];  // anc[0] is P
   int32_t* Q;
@@ -367,13 +455,14 @@ static rst_status pr_reverse(PrBufs& b, int64_t n, int K, cudaStream_t s) {
 // forest `init` when it is set.
 template <class OffT>
 rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A, int32_t root, int32_t* parent,
-                      cudaStream_t s, const int32_t* init = nullptr, const int32_t* uv = nullptr, int64_t k = 0) {
+                      cudaStream_t s, const int32_t* init = nullptr, const int32_t* uv = nullptr, int64_t k = 0,
+                      bool canonical = false) {
   int levels = 2;
   while (((int64_t)1 << (levels - 2)) < n + 1 && levels < kPrMaxLevels) ++levels;
   const int64_t tiles = (A + kArcTile - 1) / kArcTile;
   auto al = [](size_t x) { return (x + 255) / 256 * 256 + 256; };
   const size_t ws = al(n * 4) * (levels + 1) + al(n * 8) + al(n) + al(n * 4) * 2 + al((tiles + 2) * 4) + 256 +
-                    (uv ? al(2 * (size_t)k * 4) + al(4) : 0);
+                    (uv ? al(2 * (size_t)k * 4) + al(4) + 2 * al((2 * (size_t)k + 1) * 4) + al(4) + al(n * 4) : 0);
   RST_TRY(ensure_workspace(ws));
   RST_TRY(reset_device_error(s));
   DeviceState& st = state();
@@ -403,6 +492,25 @@ rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A,
   int round = 0;
   bool rounds_done = false;
   const int64_t walk_limit = tuning().insert_walk_limit;
+  // canonical input: the original root of every end (and of root), taken
+  // before any round changes the forest, for a sparse final re-rooting
+  int32_t* orig_e = nullptr;
+  int32_t* cur_e = nullptr;
+  int32_t* ffb = nullptr;
+  int32_t* fclaim = nullptr;  // claim words of the final step (n)
+  bool sparse_final = false;
+  if (uv && canonical && walk_limit > 0 && k * 64 <= n) {
+    orig_e = ar.take<int32_t>(2 * k + 1);
+    cur_e = ar.take<int32_t>(2 * k + 1);
+    ffb = ar.take<int32_t>(1);
+    fclaim = ar.take<int32_t>(n);
+    if (ar.used > ar.cap) return RST_ERR_OOM;
+    RST_CUDA(cudaMemsetAsync(ffb, 0, sizeof(int32_t), s));
+    // the slots it resets (mn, fclaim) are reset again before any use
+    RST_LAUNCH(k_sp_final_roots, grid_for(2 * k + 1), kBlock, 0, s)(2 * k, uv, root, n, b.anc[0], orig_e, b.mn,
+                                                                   fclaim, walk_limit, ffb);
+    sparse_final = true;
+  }
   if (uv && k > 0 && walk_limit > 0 && k * 64 <= n) {
     // sparse rounds while every end's walk to its root stays short
     int32_t* rep_e = ar.take<int32_t>(2 * k);
@@ -450,6 +558,24 @@ rst_status prrst_impl(const OffT* off, const int32_t* col, int64_t n, int64_t A,
     if (h == 0) break;
     RST_TRY(pr_reverse(b, n, K, s));
   }
+  if (sparse_final) {
+    const int ge = grid_for(2 * k + 1);
+    RST_LAUNCH(k_sp_final_roots, ge, kBlock, 0, s)(2 * k, uv, root, n, b.anc[0], cur_e, b.mn, fclaim, walk_limit,
+                                                   ffb);
+    RST_LAUNCH(k_sp_final_min, ge, kBlock, 0, s)(2 * k, cur_e, orig_e, b.mn);
+    RST_LAUNCH(k_sp_final_reverse, ge, kBlock, 0, s)(2 * k, cur_e, b.mn, root, b.anc[0], fclaim, walk_limit, ffb);
+    RST_CUDA(cudaGetLastError());
+    int32_t f = 0;
+    RST_CUDA(cudaMemcpyAsync(host_scratch(4), ffb, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RST_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(&f, host_scratch(4), sizeof(int32_t));
+    if (f == 0) {
+      RST_CUDA(cudaMemcpyAsync(parent, b.anc[0], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      set_stat(STAT_ROUNDS, round + 1);
+      return read_device_error(s);
+    }
+    // a long walk: every tree is re-rooted by the dense step below
+  }
   // final re-rooting
   int K = 0;
   RST_TRY(pr_history(b, n, s, &K));
@@ -475,10 +601,10 @@ rst_status run_prrst(const void* off, int offsets_bits, const int32_t* cols, int
 }
 
 rst_status run_prrst_insert(int64_t n, int32_t* parent, const int32_t* uv, int64_t k, int32_t root,
-                            cudaStream_t s) {
+                            bool canonical, cudaStream_t s) {
   // the rounds read the starting forest from `parent` and write the result
   // back to it at the end (the copy into the history buffers comes first)
-  return prrst_impl<int32_t>(nullptr, nullptr, n, 0, root, parent, s, parent, uv, k);
+  return prrst_impl<int32_t>(nullptr, nullptr, n, 0, root, parent, s, parent, uv, k, canonical);
 }
 
 }  // namespace rst

@@ -60,7 +60,7 @@ rst_status tree_depth(const int32_t* parent, int64_t n, int32_t* depth_out, int6
 // PR-RST rounds started from the rooted forest in `parent` over k inserted
 // edges (uv pairs); the result replaces `parent` (prrst.cu).
 rst_status run_prrst_insert(int64_t n, int32_t* parent, const int32_t* uv, int64_t k, int32_t root,
-                            cudaStream_t s);
+                            bool canonical, cudaStream_t s);
 rst_status run_verify(const void* off, int offsets_bits, const int32_t* cols, int64_t n, int64_t m,
                       int32_t root, const int32_t* parent, int32_t* verdict_out, cudaStream_t s);
 

@@ -14,11 +14,11 @@ def _graph(n, edges):
     return graphs.from_edges(n, [e[0] for e in edges], [e[1] for e in edges], root=0)
 
 
-def _gpu_insert(init, new, root):
+def _gpu_insert(init, new, root, canonical=False):
     import paper_2603_11645_gb300 as rst
     par = torch.from_numpy(np.asarray(init, dtype=np.int32)).cuda()
     uv = torch.from_numpy(np.asarray(new, dtype=np.int32).reshape(-1, 2)).cuda()
-    rst.insert_edges(par, uv, root)
+    rst.insert_edges(par, uv, root, canonical=canonical)
     return par.cpu().numpy()
 
 
@@ -99,7 +99,9 @@ def test_insert_rejects_bad_ids_and_cycles():
 def test_insert_small_batches_sparse_and_dense(which, k):
     """Small batches take the sparse rounds (walks to the roots, per-tree path
     reversal); a walk limit of 2 hands over to the dense rounds part-way, a
-    limit of 0 uses the dense rounds only: all three give the oracle's forest."""
+    limit of 0 uses the dense rounds only; with the canonical flag (the input
+    comes from rst_build's canonical form) the final re-rooting touches only
+    the merged trees.  Every combination gives the oracle's forest."""
     import paper_2603_11645_gb300 as rst
     g = {"er": lambda: graphs.erdos_renyi(80000, 90000, seed=71),
          "grid": lambda: graphs.grid(400, 300, seed=72, permute=True, root="random"),
@@ -117,7 +119,42 @@ def test_insert_small_batches_sparse_and_dense(which, k):
     try:
         for limit in (1 << 14, 2, 0):
             rst.set_option("insert_walk_limit", limit)
-            got = _gpu_insert(init, new, root)
-            assert np.array_equal(got, want), limit
+            for canonical in (False, True):
+                got = _gpu_insert(init, new, root, canonical)
+                assert np.array_equal(got, want), (limit, canonical)
     finally:
         rst.set_option("insert_walk_limit", 1 << 14)
+
+
+def test_insert_canonical_flag_matches_the_full_re_rooting():
+    """The canonical flag on forests rst_build returned, repeated batches in a
+    row (each output is canonical again), against the oracle step by step,
+    including a batch that merges the root's tree and one that leaves it alone."""
+    import paper_2603_11645_gb300 as rst
+    g = graphs.grid(500, 400, seed=81, permute=True, root="random")
+    g0, new = _dropped(g, 0.6, seed=9)   # below the bond threshold: many small trees
+    off0 = torch.from_numpy(g0.offsets).cuda()
+    col0 = torch.from_numpy(g0.cols).cuda()
+    par = rst.build(off0, col0, g.root, "cc_euler")
+    cur = par.cpu().numpy()
+    src0 = np.repeat(np.arange(g0.n), np.diff(g0.offsets)).astype(np.int64)
+    keep = src0 < g0.cols
+    eu, ev = list(src0[keep]), list(g0.cols[keep].astype(np.int64))
+    for lo, hi in ((0, 1), (1, 50), (50, 2000), (2000, 2100)):
+        batch = new[lo:hi]
+        eu += list(batch[:, 0])
+        ev += list(batch[:, 1])
+        gk = graphs.from_edges(g.n, eu, ev, root=g.root)
+        want, _ = oracle.prrst(gk.n, gk.offsets, gk.cols, g.root, init=cur)
+        rst.insert_edges(par, torch.from_numpy(batch.astype(np.int32)).cuda(), g.root, canonical=True)
+        got = par.cpu().numpy()
+        assert np.array_equal(got, want), (lo, hi)
+        cur = got
+
+
+def test_insert_rejects_unknown_flags():
+    import ctypes
+    import paper_2603_11645_gb300 as rst
+    par = torch.tensor([0, 0, 2], dtype=torch.int32, device="cuda")
+    code = rst.lib().rst_insert_edges(3, ctypes.c_void_p(par.data_ptr()), None, 0, 0, 6, None)
+    assert code == 1
