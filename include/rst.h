@@ -357,7 +357,7 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *                             reversal) while batches have at most n/64 edges
  *                             and every walk stays within this many steps,
  *                             otherwise over all vertices; [0, 2^30], 0 =
- *                             never sparse (default 16384);
+ *                             never sparse (default 2048);
  *     "euler_block"           threads per block of the Euler stage's
  *                             grid-stride kernels (run boundaries, successors,
  *                             parents from ranks): 128, 256 or 512 (default

@@ -261,21 +261,36 @@ __global__ void k_mlp_dinput(const float* __restrict__ W, const float* __restric
   }
 }
 
-// gW[j][i] = sum_s dY[s][j] X[s][i]; gb[j] = sum_s dY[s][j].  One thread per weight.
-__global__ void k_mlp_wgrad(const float* __restrict__ dY, const float* __restrict__ X, int B, int in, int out,
-                            float* __restrict__ gW, float* __restrict__ gb) {
+// gW[j][i] = sum_s dY[s][j] X[s][i]; gb[j] = sum_s dY[s][j].  One block per
+// weight (blockIdx = j * (in + 1) + i, i == in: the bias): the block's threads
+// stride over the batch and a fixed-order tree adds their partial sums, so the
+// result is the same on every run.
+constexpr int kWgradThreads = 128;
+__global__ void __launch_bounds__(kWgradThreads) k_mlp_wgrad(const float* __restrict__ dY,
+                                                             const float* __restrict__ X, int B, int in, int out,
+                                                             float* __restrict__ gW, float* __restrict__ gb) {
+  __shared__ float s_part[kWgradThreads / 32];
   const int64_t total = (int64_t)out * (in + 1);
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
     const int j = (int)(t / (in + 1)), i = (int)(t % (in + 1));
     float acc = 0.f;
     if (i < in) {
-      for (int s = 0; s < B; ++s) acc = fmaf(dY[(int64_t)s * out + j], X[(int64_t)s * in + i], acc);
-      gW[(int64_t)j * in + i] = acc;
+      for (int s = threadIdx.x; s < B; s += blockDim.x) acc = fmaf(dY[(int64_t)s * out + j], X[(int64_t)s * in + i], acc);
     } else {
-      for (int s = 0; s < B; ++s) acc += dY[(int64_t)s * out + j];
-      gb[j] = acc;
+      for (int s = threadIdx.x; s < B; s += blockDim.x) acc += dY[(int64_t)s * out + j];
     }
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float sum = 0.f;
+      for (int w = 0; w < kWgradThreads / 32; ++w) sum += s_part[w];
+      if (i < in)
+        gW[(int64_t)j * in + i] = sum;
+      else
+        gb[j] = sum;
+    }
+    __syncthreads();
   }
 }
 
@@ -323,11 +338,11 @@ static void mlp_grad(const float* P, const float* X, const float* T, int B, MlpS
                      cudaStream_t st) {
   mlp_forward(P, X, B, s, s.y, st);
   RST_LAUNCH(k_mlp_dout, grid_for((int64_t)B * kO), kBlock, 0, st)(s.y, T, B, s.dy, loss);
-  RST_LAUNCH(k_mlp_wgrad, grid_for((int64_t)kO * (kH + 1)), kBlock, 0, st)(s.dy, s.h2, B, kH, kO, G + kW3, G + kB3);
+  RST_LAUNCH(k_mlp_wgrad, kO * (kH + 1), kWgradThreads, 0, st)(s.dy, s.h2, B, kH, kO, G + kW3, G + kB3);
   RST_LAUNCH(k_mlp_dinput, grid_for((int64_t)B * kH), kBlock, 0, st)(P + kW3, s.dy, s.h2, B, kH, kO, s.dh2);
-  RST_LAUNCH(k_mlp_wgrad, grid_for((int64_t)kH * (kH + 1)), kBlock, 0, st)(s.dh2, s.h1, B, kH, kH, G + kW2, G + kB2);
+  RST_LAUNCH(k_mlp_wgrad, kH * (kH + 1), kWgradThreads, 0, st)(s.dh2, s.h1, B, kH, kH, G + kW2, G + kB2);
   RST_LAUNCH(k_mlp_dinput, grid_for((int64_t)B * kH), kBlock, 0, st)(P + kW2, s.dh2, s.h1, B, kH, kH, s.dh1);
-  RST_LAUNCH(k_mlp_wgrad, grid_for((int64_t)kH * (kF + 1)), kBlock, 0, st)(s.dh1, X, B, kF, kH, G + kW1, G + kB1);
+  RST_LAUNCH(k_mlp_wgrad, kH * (kF + 1), kWgradThreads, 0, st)(s.dh1, X, B, kF, kH, G + kW1, G + kB1);
 }
 
 // ------------------------------------------------------------------ selector state

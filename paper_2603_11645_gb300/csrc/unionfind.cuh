@@ -35,10 +35,14 @@ __device__ __forceinline__ int32_t uf_root(const int32_t* uf, int32_t x, int64_t
   return x;
 }
 
-// Merges the trees of u and v; true iff this call's CAS did the merge.
+// Merges the trees of u and v; true iff this call's CAS did the merge.  A
+// failed CAS resumes the finds from the roots just found (ancestors of u and
+// v), not from u and v again.
 __device__ __forceinline__ bool uf_link(int32_t* uf, int32_t u, int32_t v, int64_t n, uint32_t* status) {
+  int32_t ru = u, rv = v;
   for (int64_t it = 0; it <= n; ++it) {
-    const int32_t ru = uf_find(uf, u, n, status), rv = uf_find(uf, v, n, status);
+    ru = uf_find(uf, ru, n, status);
+    rv = uf_find(uf, rv, n, status);
     if (ru == rv) return false;
     const int32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
     if (atomicCAS(&uf[hi], hi, lo) == hi) return true;

@@ -117,13 +117,13 @@ def test_insert_small_batches_sparse_and_dense(which, k):
     root = int(g.root)
     want, _ = oracle.prrst(gk.n, gk.offsets, gk.cols, root, init=init)
     try:
-        for limit in (1 << 14, 2, 0):
+        for limit in (2048, 2, 0):
             rst.set_option("insert_walk_limit", limit)
             for canonical in (False, True):
                 got = _gpu_insert(init, new, root, canonical)
                 assert np.array_equal(got, want), (limit, canonical)
     finally:
-        rst.set_option("insert_walk_limit", 1 << 14)
+        rst.set_option("insert_walk_limit", 2048)
 
 
 def test_insert_canonical_flag_matches_the_full_re_rooting():
