@@ -90,9 +90,12 @@ __global__ void k_mark_roots(int64_t nroots, const int32_t* __restrict__ roots, 
     is_root[tree_root_for(roots[k], root_label, root, rootof)] = 1;
 }
 
-// Tree-arc runs: toff[v] = first tree position of v.  With parent set, roots
-// and singletons also take P[v] = v; with leaf set, leaf[v] marks vertices of
-// tree degree 1 that are not tree roots.
+// Tree-arc runs: toff[v] = first tree position of v, with bit kRootBit set
+// when v is a tree root (tree positions stay below 2^31), so the successor
+// pass reads a vertex's run and its root flag in one sector.  With parent
+// set, roots and singletons also take P[v] = v; with leaf set, leaf[v] marks
+// vertices of tree degree 1 that are not tree roots.
+constexpr uint32_t kRootBit = 0x80000000u;
 template <class OffT>
 __global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint2* __restrict__ rk,
                        const uint8_t* __restrict__ is_root,
@@ -100,11 +103,12 @@ __global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint2* __r
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t t0 = bit_rank2(rk, (uint64_t)off[v]);
-    toff[v] = t0;
+    const bool rt = v < n && is_root[v];
+    toff[v] = t0 | (rt ? kRootBit : 0u);
     if (v < n && (parent || leaf)) {
       const uint32_t t1 = bit_rank2(rk, (uint64_t)off[v + 1]);
-      if (parent && (t0 == t1 || is_root[v])) parent[v] = (int32_t)v;
-      if (leaf) leaf[v] = (t1 - t0 == 1u && !is_root[v]) ? 1 : 0;
+      if (parent && (t0 == t1 || rt)) parent[v] = (int32_t)v;
+      if (leaf) leaf[v] = (t1 - t0 == 1u && !rt) ? 1 : 0;
     }
   }
 }
@@ -151,7 +155,8 @@ __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = tree_root_for(roots[k], root_label, root, rootof);
-    heads[k] = toff[r + 1] > toff[r] ? (int32_t)toff[r] : -1;  // -1: nothing left to tour
+    const uint32_t t0 = toff[r] & ~kRootBit, t1 = toff[r + 1] & ~kRootBit;
+    heads[k] = t1 > t0 ? (int32_t)t0 : -1;  // -1: nothing left to tour
   }
 }
 
@@ -160,8 +165,7 @@ __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32
 // run (wrapping to first[b]), succ(k) follows i in a's run; the arc that
 // wraps into a tree root's first arc is cut (succ = -1).
 __global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint2* __restrict__ rk,
-                             const uint32_t* __restrict__ toff,
-                             const uint8_t* __restrict__ is_root, int32_t* __restrict__ succ) {
+                             const uint32_t* __restrict__ toff, int32_t* __restrict__ succ) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
     uint4 r = pairs[t];
@@ -172,10 +176,11 @@ __global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint2* 
     r.x = i;
     r.y = k;
     pairs[t] = r;
-    const uint32_t lastb = toff[b + 1] - 1u;
-    succ[i] = (k != lastb) ? (int32_t)(k + 1u) : (is_root[b] ? -1 : (int32_t)toff[b]);
-    const uint32_t lasta = toff[a + 1] - 1u;
-    succ[k] = (i != lasta) ? (int32_t)(i + 1u) : (is_root[a] ? -1 : (int32_t)toff[a]);
+    const uint32_t fb = toff[b], fb1 = toff[b + 1], fa = toff[a], fa1 = toff[a + 1];
+    const uint32_t lastb = (fb1 & ~kRootBit) - 1u;
+    succ[i] = (k != lastb) ? (int32_t)(k + 1u) : ((fb & kRootBit) ? -1 : (int32_t)(fb & ~kRootBit));
+    const uint32_t lasta = (fa1 & ~kRootBit) - 1u;
+    succ[k] = (i != lasta) ? (int32_t)(i + 1u) : ((fa & kRootBit) ? -1 : (int32_t)(fa & ~kRootBit));
   }
 }
 
@@ -245,7 +250,7 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
   if (!succ || !R) return RST_ERR_OOM;
   const int gT = grid_for(T, eb, 2048 / eb);
-  RST_LAUNCH(k_pairs_succ, gT, eb, 0, s)(T, cc->pairs, rk, toff, is_root, succ);
+  RST_LAUNCH(k_pairs_succ, gT, eb, 0, s)(T, cc->pairs, rk, toff, succ);
   prof_mark(s, "k_pairs_succ");
   RST_CUDA(cudaGetLastError());
   if (succ_view) *succ_view = succ;  // stays valid while the arena is not reset
