@@ -400,8 +400,11 @@ long long rst_launch_count(void);
 /* Sizes seen by the last call (host array): hooking rounds, components with
  * edges after round 1, inter-component edges after round 1, tree edges,
  * components with edges, BFS levels or list-ranking levels, tree arcs list-
- * ranked (after leaf pruning).  Returns the number of values written (at most
- * max). */
+ * ranked (after leaf pruning), and for CC+Euler the hooking rounds finished
+ * by one thread block once few components remain (0: none) and the times
+ * that block handed back to the grid-wide rounds because the remaining
+ * component pairs did not fit.  Returns the number of values written (at
+ * most max, at most 10). */
 int rst_last_stats(long long *out, int max);
 void rst_profile_enable(int on);
 int rst_profile_read(float *ms_out, const char **names_out, int max_stages);

@@ -45,10 +45,38 @@ struct RoundState {
 };
 struct CcCtl {
   RoundState st[kMaxRounds + 1];
+  // the tail (below): 0 not entered, 1 requested at round tail_round,
+  // 2 finished in one block, 3 handed back to the regular rounds
+  int tail;
+  int tail_round;
   int cur;             // current round
   int root_label;      // canonical label of the requested root (-1 until known)
   unsigned int done;   // blocks of the round's last kernel that have finished
+  int tail_rounds;              // rounds the tail ran
+  unsigned int tail_hooks;      // tree edges the tail recorded (positions in tp)
+  unsigned int tail_overflow;   // the deduplicated pairs did not fit
+  int tail_first_back;          // round of the first hand-back (0: none)
+  int tail_backs;               // hand-backs
 };
+
+// The tail: once at most kTailC components with edges remain, the list
+// (mostly parallel edges between few components by then) is deduplicated to
+// one entry per component pair, keeping the smallest key (the minimum-key
+// choice of every component depends only on each pair's smallest key), and
+// one block finishes all remaining rounds in shared memory.  A tail that does
+// not fit (more than kTailPairs distinct pairs) hands back to the regular
+// rounds, which continue from the same round and request the tail again one
+// round later.  The pair graph of contracted grids and meshes is planar, so
+// kTailPairs = 3 kTailC always holds them; contracted random graphs are
+// dense and may need one or two more rounds first.
+constexpr int kTailC = 3072;
+constexpr int kTailPairs = 3 * kTailC;  // a planar pair graph on C vertices has < 3C edges
+constexpr int kTailSlots = 16384;  // hash table of component pairs (power of two)
+constexpr int kTailProbe = 64;
+constexpr int kTailThreads = 1024;
+constexpr int kTailBits = 14;     // log2 kTailSlots
+constexpr int kTailMaxRounds = 64;
+constexpr size_t kTailSmem = (size_t)kTailPairs * 12 + (size_t)kTailC * 32;
 
 // Row record of a vertex, one aligned 32-byte sector: where its row starts,
 // its degree and the first kRecCols entries.  Round 1 reads the chosen
@@ -81,6 +109,9 @@ struct CcBuffers {
   int32_t* roots;    // n/2+1
   struct CcCtl* ctl; // device-resident round control
   int32_t* tile_row; // row of the first arc of every arc tile
+  unsigned long long* tkey;  // kTailSlots: component pair (lo << 32 | hi), ~0 = empty
+  uint32_t* tval;            // kTailSlots: smallest key of the pair
+  uint32_t* tp;              // kTailC: keys (CSR positions) of the tail's tree edges
   int64_t ecap;      // list capacity
   int64_t bcap;      // slots in each best[] buffer
 };
@@ -115,6 +146,9 @@ static CcBuffers cc_layout(Arena& ar, int64_t n, int64_t A) {
   b.roots = ar.take<int32_t>(half);
   b.ctl = ar.take<CcCtl>(1);
   b.tile_row = ar.take<int32_t>(A / kArcTile + 2);
+  b.tkey = ar.take<unsigned long long>(kTailSlots);
+  b.tval = ar.take<uint32_t>(kTailSlots);
+  b.tp = ar.take<uint32_t>(kTailC);
   return b;
 }
 
@@ -479,6 +513,9 @@ struct CcPtrs {
   CcCtl* ctl;
   unsigned long long* counters;
   uint32_t* status;
+  unsigned long long* tkey;
+  uint32_t* tval;
+  uint32_t* tp;
   int64_t ecap;
   int64_t bcap;  // slots in each best[] buffer
 };
@@ -488,6 +525,11 @@ __global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < (int64_t)C;
        c += (int64_t)gridDim.x * blockDim.x)
     b.best[0][c] = ~0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kTailSlots;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    b.tkey[i] = ~0ull;  // the tail's pair table starts empty
+    b.tval[i] = ~0u;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     CcCtl* t = b.ctl;
     t->st[0].C = C;
@@ -819,7 +861,7 @@ __global__ void k_round_settle(CcPtrs b) {
 // Component -> next id and minimum vertex per new component.  The last block
 // to finish advances the round and sets the loop condition (no separate
 // kernel; every block has read the round index before it counts itself done).
-__global__ void k_round_map(CcPtrs b, cudaGraphConditionalHandle h, int use_handle) {
+__global__ void k_round_map(CcPtrs b, cudaGraphConditionalHandle h, int use_handle, int allow_tail) {
   CcCtl* t = b.ctl;
   const int r = t->cur;
   const int64_t C = (int64_t)t->st[r].C;
@@ -867,6 +909,11 @@ __global__ void k_round_map(CcPtrs b, cudaGraphConditionalHandle h, int use_hand
       raise_error(b.status, DERR_ROUND_LIMIT);
       more = false;
     }
+    if (more && allow_tail && t->st[nr].C <= (unsigned long long)kTailC) {
+      t->tail = 1;  // the tail takes the remaining rounds
+      t->tail_round = nr;
+      more = false;
+    }
     t->cur = nr;
     if (use_handle) cudaGraphSetConditional(h, more ? 1u : 0u);
   }
@@ -888,6 +935,320 @@ __global__ void k_label_vertices(int64_t n, const int32_t* __restrict__ C1,
        v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = C1[v];
     labels[v] = c < 0 ? (int32_t)v : lab1[c];
+  }
+}
+
+// ------------------------------------------------------------------ the tail
+
+// One entry per component pair of the list entering round tail_round: the
+// pair's smallest key (Fibonacci hashing, linear probing in an L2-resident
+// table; a full probe sequence flags an overflow and the tail is not run).
+__global__ void k_tail_dedup(CcPtrs b) {
+  CcCtl* t = b.ctl;
+  if (t->tail != 1) return;
+  const int R = t->tail_round;
+  const int64_t E = (int64_t)t->st[R].E;
+  const int src = R & 1;
+  const int32_t* __restrict__ mp = b.nextpool + t->st[R - 1].pool_at;
+  const int32_t* __restrict__ Icu = b.Ecu[src];
+  const int32_t* __restrict__ Icv = b.Ecv[src];
+  const uint32_t* __restrict__ Ip = b.Ep[src];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    // once the table has overflowed the tail will not run: stop early
+    if (__ldcg(&t->tail_overflow) != 0u) break;
+    const int32_t cu = mp[Icu[e]], cv = mp[Icv[e]];
+    if (cu == cv || cu < 0 || cv < 0) continue;
+    const uint32_t p = Ip[e];
+    const unsigned long long key = cu < cv ? ((unsigned long long)(uint32_t)cu << 32) | (uint32_t)cv
+                                           : ((unsigned long long)(uint32_t)cv << 32) | (uint32_t)cu;
+    uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kTailBits));
+    bool placed = false;
+    for (int probe = 0; probe < kTailProbe; ++probe) {
+      unsigned long long old = __ldcg(&b.tkey[h]);
+      if (old == ~0ull) old = atomicCAS(&b.tkey[h], ~0ull, key);
+      if (old == ~0ull || old == key) {
+        if (__ldcg(&b.tval[h]) > p) atomicMin(&b.tval[h], p);
+        placed = true;
+        break;
+      }
+      h = (h + 1) & (kTailSlots - 1);
+    }
+    if (!placed) atomicExch(&t->tail_overflow, 1u);
+  }
+}
+
+// Exclusive prefix sum over the block (kTailThreads threads); *total = sum.
+__device__ __forceinline__ int tail_scan(int v, int* s_warp, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+    int ws = w;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, ws, d);
+      if (lane >= d) ws += y;
+    }
+    if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = ws - w;
+    if (lane == 31) s_warp[32] = ws;
+  }
+  __syncthreads();
+  const int r = x - v + s_warp[warp];
+  *total = s_warp[32];
+  __syncthreads();
+  return r;
+}
+
+// All remaining rounds in one block, on the deduplicated pairs: the same
+// hooking, mutual-pair rule, tree-edge choice, compression and minimum
+// vertices as the regular rounds.  Final components join the root list as
+// they appear; the final label of every component entering the tail is
+// written over its minimum vertex (the labels pass reads it as the last
+// round's labels); the tree edges' keys go to tp for k_tail_records.
+__global__ void __launch_bounds__(kTailThreads) k_tail(CcPtrs b, cudaGraphConditionalHandle h2, int use_handle) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* s_best = reinterpret_cast<unsigned long long*>(smem);  // kTailC
+  int32_t* s_par = reinterpret_cast<int32_t*>(s_best + kTailC);             // parent, then next id
+  int32_t* s_minv = s_par + kTailC;
+  int32_t* s_minv2 = s_minv + kTailC;
+  int32_t* s_nid = s_minv2 + kTailC;  // -1 final, -2 hooked, else the live root's next id
+  int32_t* s_cur = s_nid + kTailC;    // entering component x: its current component (-1: done)
+  int32_t* s_lab = s_cur + kTailC;    // entering component x: its final label
+  uint32_t* s_pu = reinterpret_cast<uint32_t*>(s_lab + kTailC);  // kTailPairs
+  uint32_t* s_pv = s_pu + kTailPairs;
+  uint32_t* s_pp = s_pv + kTailPairs;
+  __shared__ int s_warp[33];
+  __shared__ int s_np, s_bad, s_hooks, s_flag, s_rc;
+  CcCtl* t = b.ctl;
+  if (t->tail != 1) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int R = t->tail_round;
+  const int C0 = (int)t->st[R].C;
+  if (tid == 0) {
+    s_np = 0;
+    s_bad = (t->tail_overflow != 0u || C0 > kTailC) ? 1 : 0;
+    s_hooks = 0;
+    s_rc = t->st[R].rc;
+  }
+  __syncthreads();
+  if (!s_bad) {
+    for (int slot = tid; slot < kTailSlots; slot += nt) {
+      const unsigned long long key = b.tkey[slot];
+      if (key == ~0ull) continue;
+      const int i = atomicAdd(&s_np, 1);
+      if (i < kTailPairs) {
+        s_pu[i] = (uint32_t)(key >> 32);
+        s_pv[i] = (uint32_t)(key & 0xffffffffull);
+        s_pp[i] = b.tval[slot];
+      } else {
+        s_bad = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_bad) {  // does not fit: the regular rounds continue from round R
+    for (int slot = tid; slot < kTailSlots; slot += nt) {  // empty table for the next request
+      b.tkey[slot] = ~0ull;
+      b.tval[slot] = ~0u;
+    }
+    if (tid == 0) {
+      t->tail = 3;
+      t->tail_overflow = 0u;
+      if (t->tail_backs++ == 0) t->tail_first_back = R;
+      if (use_handle) cudaGraphSetConditional(h2, 1u);
+    }
+    return;
+  }
+  const int32_t* __restrict__ minv_in = b.minvpool + t->st[R].pool_at;
+  for (int c = tid; c < C0; c += nt) {
+    s_minv[c] = minv_in[c];
+    s_cur[c] = c;
+    s_lab[c] = -1;
+  }
+  int C = C0, np = s_np;
+  int rounds = 0;
+  bool converged = false;
+  for (; rounds < kTailMaxRounds; ++rounds) {
+    for (int c = tid; c < C; c += nt) s_best[c] = ~0ull;
+    __syncthreads();
+    for (int i = tid; i < np; i += nt) {
+      const unsigned long long key = (unsigned long long)s_pp[i] << 32;
+      atomicMin(&s_best[s_pu[i]], key | s_pv[i]);
+      atomicMin(&s_best[s_pv[i]], key | s_pu[i]);
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += nt) {  // resolve
+      const unsigned long long bc = s_best[c];
+      if (bc == ~0ull) {
+        s_par[c] = c;
+        s_nid[c] = -1;
+        continue;
+      }
+      const int c2 = (int)(bc & 0xffffffffull);
+      const uint32_t p = (uint32_t)(bc >> 32);
+      if ((uint32_t)(s_best[c2] >> 32) == p && c < c2) {
+        s_par[c] = c;
+        s_nid[c] = 0;
+      } else {
+        s_par[c] = c2;
+        s_nid[c] = -2;
+        b.tp[atomicAdd(&s_hooks, 1)] = p;  // fewer than C0 <= kTailC hooks in all
+      }
+    }
+    __syncthreads();
+    for (int it = 0; it < 32; ++it) {  // compress (pointer jumping in place)
+      if (tid == 0) s_flag = 0;
+      __syncthreads();
+      for (int c = tid; c < C; c += nt) {
+        const int x = s_par[c], y = s_par[x];
+        if (y != x) {
+          s_par[c] = y;
+          s_flag = 1;
+        }
+      }
+      __syncthreads();
+      const int f = s_flag;
+      __syncthreads();
+      if (!f) break;
+      if (it == 31 && tid == 0) raise_error(b.status, DERR_ROUND_LIMIT);
+    }
+    // next ids of live roots, in component order; final components leave
+    int base = 0;
+    for (int c0 = 0; c0 < C; c0 += nt) {
+      const int c = c0 + tid;
+      const int live = (c < C && s_nid[c] == 0) ? 1 : 0;
+      int tot = 0;
+      const int ex = tail_scan(live, s_warp, &tot);
+      if (live) s_nid[c] = base + ex;
+      base += tot;
+    }
+    for (int c = tid; c < C; c += nt) {
+      if (s_nid[c] == -1) {
+        const unsigned long long rid = atomicAdd(&b.counters[CNT_ROOTS], 1ull);
+        b.roots[rid] = s_minv[c];
+        if (c == s_rc) t->root_label = s_minv[c];
+      } else if (s_par[c] == c) {
+        s_minv2[s_nid[c]] = s_minv[c];
+      }
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += nt) {  // next id of every component (-1: final)
+      int nx = s_nid[c] == -1 ? -1 : s_nid[s_par[c]];
+      if (s_nid[c] == -2) {
+        if (nx >= 0 && nx < base) {
+          atomicMin(&s_minv2[nx], s_minv[c]);
+        } else {  // a hooked component whose root is not live: cannot happen
+          raise_error(b.status, DERR_INDEX);
+          nx = -1;
+        }
+      }
+      s_par[c] = nx;
+    }
+    __syncthreads();
+    if (tid == 0) s_rc = s_rc >= 0 ? s_par[s_rc] : -1;
+    for (int x = tid; x < C0; x += nt) {  // the entering components' labels
+      const int c = s_cur[x];
+      if (c < 0) continue;
+      if (s_nid[c] == -1) {
+        s_lab[x] = s_minv[c];
+        s_cur[x] = -1;
+      } else {
+        s_cur[x] = s_par[c];
+      }
+    }
+    // the pairs in next ids, without those inside one component
+    constexpr int kPer = kTailPairs / kTailThreads;
+    static_assert(kPer * kTailThreads == kTailPairs, "pairs must split evenly over the block");
+    uint32_t u[kPer], v[kPer], pp[kPer];
+    int keep = 0;
+    for (int k = 0; k < kPer; ++k) {
+      const int i = k * nt + tid;
+      u[k] = v[k] = pp[k] = 0;
+      if (i < np) {
+        u[k] = (uint32_t)s_par[s_pu[i]];
+        v[k] = (uint32_t)s_par[s_pv[i]];
+        pp[k] = s_pp[i];
+        if (u[k] != v[k]) {
+          if (u[k] < (uint32_t)base && v[k] < (uint32_t)base)
+            keep |= 1 << k;
+          else  // an endpoint left as final while the pair remains: cannot happen
+            raise_error(b.status, DERR_INDEX);
+        }
+      }
+    }
+    int tot = 0;
+    int at = tail_scan(__popc(keep), s_warp, &tot);  // all reads of the old pairs are done
+    for (int k = 0; k < kPer; ++k)
+      if ((keep >> k) & 1) {
+        s_pu[at] = u[k];
+        s_pv[at] = v[k];
+        s_pp[at] = pp[k];
+        ++at;
+      }
+    for (int c = tid; c < base; c += nt) s_minv[c] = s_minv2[c];
+    __syncthreads();
+    C = base;
+    np = tot;
+    if (C == 0) {
+      converged = true;
+      ++rounds;
+      break;
+    }
+  }
+  if (!converged && tid == 0) raise_error(b.status, DERR_ROUND_LIMIT);
+  int32_t* lab_out = b.minvpool + t->st[R].pool_at;
+  for (int x = tid; x < C0; x += nt) lab_out[x] = s_lab[x];
+  if (tid == 0) {
+    t->tail_rounds = rounds;
+    t->tail_hooks = (unsigned int)s_hooks;
+    t->tail = 2;
+  }
+}
+
+// The tail's tree edges as records {p, q, a, b} with both arcs marked, as
+// k_round_resolve writes them (the twin found from b's row record or row).
+template <class OffT>
+__global__ void __launch_bounds__(kBlock) k_tail_records(CcPtrs b, const OffT* __restrict__ off) {
+  CcCtl* t = b.ctl;
+  if (t->tail != 2) return;
+  const int64_t H = (int64_t)t->tail_hooks;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < H; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = base + threadIdx.x;
+    bool emit = false;
+    uint4 out = make_uint4(0, 0, 0, 0);
+    if (j < H) {
+      const uint32_t p = b.tp[j];
+      const int32_t bb = b.col[p];
+      int32_t a = 0;
+      int64_t q = 0;
+      bool found;
+      if (b.rec) {
+        const RowRec Rr = b.rec[bb];
+        found = Rr.deg <= (uint32_t)kRecCols ? twin_from_record(off, Rr, bb, (uint64_t)p, &a, &q)
+                                             : twin_of_position(off, b.col, bb, (uint64_t)p, &a, &q);
+      } else {
+        found = twin_of_position(off, b.col, bb, (uint64_t)p, &a, &q);
+      }
+      if (found) {
+        emit = true;
+        out = make_uint4(p, (uint32_t)q, (uint32_t)a, (uint32_t)bb);
+        atomicOr(&b.bits[out.x >> 5], 1u << (out.x & 31));
+        atomicOr(&b.bits[out.y >> 5], 1u << (out.y & 31));
+      } else {
+        raise_error(b.status, DERR_INDEX);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, emit);
+    const unsigned long long mine = block_reserve<kBlock>(&b.counters[CNT_PAIRS], lane == 0 ? (unsigned)__popc(bal) : 0u);
+    const unsigned long long w0 = __shfl_sync(0xffffffffu, mine, 0);
+    if (emit) b.pairs[w0 + __popc(bal & lt)] = out;
   }
 }
 
@@ -919,15 +1280,58 @@ void destroy_round_graphs() {
 
 template <class OffT>
 static void launch_round_body(const CcPtrs& p, const OffT* off, cudaGraphConditionalHandle h,
-                              int use_handle, cudaStream_t s) {
+                              int use_handle, int allow_tail, cudaStream_t s) {
   const int g = device_info().sms * tuning().round_bps;
   const int gh = device_info().sms * std::min(tuning().round_bps, kHookBlocksPerSm);
   RST_LAUNCH(k_round_hook, gh, kBlock, 0, s)(p);
   const int gr = device_info().sms * std::min(tuning().round_bps, kResolveBlocksPerSm);
   RST_LAUNCH(k_round_resolve<OffT>, gr, kBlock, 0, s)(p, off);
   RST_LAUNCH(k_round_settle, g, kBlock, 0, s)(p);
-  RST_LAUNCH(k_round_map, g, kBlock, 0, s)(p, h, use_handle);
+  RST_LAUNCH(k_round_map, g, kBlock, 0, s)(p, h, use_handle, allow_tail);
 }
+
+template <class OffT>
+static void launch_tail(const CcPtrs& p, const OffT* off, cudaGraphConditionalHandle h2, int use_handle,
+                        cudaStream_t s) {
+  RST_LAUNCH(k_tail_dedup, device_info().sms * 8, kBlock, 0, s)(p);
+  RST_LAUNCH(k_tail, 1, kTailThreads, kTailSmem, s)(p, h2, use_handle);
+  RST_LAUNCH(k_tail_records<OffT>, device_info().sms * 4, kBlock, 0, s)(p, off);
+}
+
+// A while node whose body is one contraction round (captured from the
+// round kernels), followed by the tail's kernels when with_tail is set,
+// after the given dependencies.
+template <class OffT>
+static rst_status add_round_loop(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
+                                 cudaGraphConditionalHandle h, const CcPtrs& p, const OffT* off, bool with_tail,
+                                 cudaStream_t cs, cudaGraphNode_t* node) {
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  RST_CUDA(cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  RST_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_round_body<OffT>(p, off, h, 1, 1, cs);
+  if (with_tail) launch_tail<OffT>(p, off, h, 1, cs);
+  cudaGraph_t captured = nullptr;
+  RST_CUDA(cudaStreamEndCapture(cs, &captured));
+  return RST_OK;
+}
+
+// Shared memory beyond the default for the tail's single block (once per device).
+static rst_status tail_smem_attr() {
+  static bool set[64] = {};
+  int dev = 0;
+  RST_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && set[dev]) return RST_OK;
+  RST_CUDA(cudaFuncSetAttribute((const void*)k_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kTailSmem));
+  if (dev >= 0 && dev < 64) set[dev] = true;
+  return RST_OK;
+}
+
 
 template <class OffT>
 static rst_status round_graph_for(const CcPtrs& p, const OffT* off, int64_t n, int64_t A,
@@ -944,23 +1348,43 @@ static rst_status round_graph_for(const CcPtrs& p, const OffT* off, int64_t n, i
   if (dev < 0 || dev >= 64) return RST_ERR_UNSUPPORTED;
   if (!g_capture_stream[dev])
     RST_CUDA(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
+  RST_TRY(tail_smem_attr());
   cudaStream_t cs = g_capture_stream[dev];
+  // regular rounds (a while loop) -> the tail's three kernels -> a second
+  // while loop of rounds each followed by the tail's kernels, entered only
+  // when the tail hands back
   cudaGraph_t graph = nullptr;
   RST_CUDA(cudaGraphCreate(&graph, 0));
-  cudaGraphConditionalHandle h;
-  RST_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t node;
-  RST_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  RST_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  launch_round_body<OffT>(p, off, h, 1, cs);
-  cudaGraph_t captured = nullptr;
-  RST_CUDA(cudaStreamEndCapture(cs, &captured));
+  cudaGraphConditionalHandle h1, h2;
+  RST_CUDA(cudaGraphConditionalHandleCreate(&h1, graph, 1, cudaGraphCondAssignDefault));
+  RST_CUDA(cudaGraphConditionalHandleCreate(&h2, graph, 0, cudaGraphCondAssignDefault));
+  cudaGraphNode_t loop1, dedup, tailn, recs, loop2;
+  RST_TRY(add_round_loop<OffT>(graph, nullptr, 0, h1, p, off, false, cs, &loop1));
+  CcPtrs pc = p;
+  int one = 1;
+  void* dedup_args[] = {&pc};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)k_tail_dedup;
+  kp.gridDim = dim3(device_info().sms * 8);
+  kp.blockDim = dim3(kBlock);
+  kp.kernelParams = dedup_args;
+  RST_CUDA(cudaGraphAddKernelNode(&dedup, graph, &loop1, 1, &kp));
+  void* tail_args[] = {&pc, &h2, &one};
+  kp.func = (void*)k_tail;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(kTailThreads);
+  kp.sharedMemBytes = (unsigned)kTailSmem;
+  kp.kernelParams = tail_args;
+  RST_CUDA(cudaGraphAddKernelNode(&tailn, graph, &dedup, 1, &kp));
+  const OffT* offp = off;
+  void* rec_args[] = {&pc, &offp};
+  kp.func = (void*)k_tail_records<OffT>;
+  kp.gridDim = dim3(device_info().sms * 4);
+  kp.blockDim = dim3(kBlock);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = rec_args;
+  RST_CUDA(cudaGraphAddKernelNode(&recs, graph, &tailn, 1, &kp));
+  RST_TRY(add_round_loop<OffT>(graph, &recs, 1, h2, p, off, true, cs, &loop2));
   cudaGraphExec_t exec = nullptr;
   RST_CUDA(cudaGraphInstantiate(&exec, graph, 0));
   RST_CUDA(cudaGraphDestroy(graph));
@@ -1036,6 +1460,9 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   p.ctl = b.ctl;
   p.counters = cnt;
   p.status = status;
+  p.tkey = b.tkey;
+  p.tval = b.tval;
+  p.tp = b.tp;
   p.ecap = b.ecap;
   p.bcap = b.bcap;
   RST_LAUNCH(k_round_init, grid_for(n / 2 + 1), kBlock, 0, s)(p, root, b.C1);
@@ -1063,12 +1490,22 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
     RST_TRY(round_graph_for<OffT>(p, off, n, A, &exec));
     RST_CUDA(cudaGraphLaunch(exec, s));
   } else {
+    RST_TRY(tail_smem_attr());
     for (int r = 0; r < kMaxRounds; ++r) {
-      launch_round_body<OffT>(p, off, cudaGraphConditionalHandle{}, 0, s);
+      launch_round_body<OffT>(p, off, cudaGraphConditionalHandle{}, 0, 1, s);
       RST_CUDA(cudaGetLastError());
       unsigned long long c = 0;
       RST_TRY(fetch_u64(&b.ctl->st[r + 1].C, 1, &c, s));
       if (c == 0) break;
+      if (c <= (unsigned long long)kTailC && r + 1 < kMaxRounds) {
+        // the device requested the tail (the same test as k_round_map's)
+        launch_tail<OffT>(p, off, cudaGraphConditionalHandle{}, 0, s);
+        RST_CUDA(cudaGetLastError());
+        unsigned long long w = 0;  // tail (low half), tail_round (high half)
+        RST_TRY(fetch_u64(reinterpret_cast<const unsigned long long*>(&b.ctl->tail), 1, &w, s));
+        if ((int)(w & 0xffffffffull) == 2) break;
+        // handed back: the regular rounds continue and request it again
+      }
     }
   }
   prof_mark(s, "cc_rounds");
@@ -1091,8 +1528,15 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   }
   unsigned long long h[8];
   for (int i = 0; i < 8; ++i) h[i] = hb[i];
-  const int rounds_done = hctl->cur;
-  if (!eager) count_launches(4LL * rounds_done);  // the round kernels the graph ran
+  // with the tail, the labels of the components entering round tail_round
+  // are final (the label pass starts one round later)
+  const bool tailed = hctl->tail == 2;
+  const int rounds_done = tailed ? hctl->tail_round + 1 : hctl->cur;
+  const int regular_rounds = tailed ? hctl->tail_round : hctl->cur;
+  if (!eager) {  // the kernels the graph ran (the second loop's rounds run the tail's three too)
+    const int first_loop = hctl->tail_backs ? hctl->tail_first_back : regular_rounds;
+    count_launches(4LL * first_loop + 3 + 7LL * (regular_rounds - first_loop));
+  }
   if (labels_out) {
     for (int r = rounds_done - 2; r >= 0; --r) {
       const int64_t Cr = (int64_t)hctl->st[r].C;
@@ -1113,12 +1557,14 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   out->bits = b.bits;
   out->nroots = (int64_t)h[CNT_ROOTS];
   out->roots = b.roots;
-  out->rounds = rounds_done + 1;
+  out->rounds = regular_rounds + (tailed ? hctl->tail_rounds : 0) + 1;
   out->root_label = root >= 0 ? hctl->root_label : -1;
   out->rk = pre_rk;
   out->rk_tmp = pre_tmp;
   out->is_root = pre_root;
   set_stat(STAT_ROUNDS, out->rounds);
+  set_stat(STAT_TAIL, tailed ? hctl->tail_rounds : 0);
+  set_stat(STAT_TAIL_BACKS, hctl->tail_backs);
   set_stat(STAT_T, out->T);
   set_stat(STAT_NROOTS, out->nroots);
   return RST_OK;

@@ -60,7 +60,9 @@ enum StatSlot : int {
   STAT_NROOTS = 4,   // components with edges
   STAT_LEVELS = 5,   // BFS levels (BFS) / list-ranking levels (CC+Euler)
   STAT_LR_N = 6,     // elements list-ranked (tree arcs left after leaf pruning)
-  STAT_COUNT = 8
+  STAT_TAIL = 7,     // CC+Euler: rounds the single-block tail ran (0: it did not finish the rounds)
+  STAT_TAIL_BACKS = 8,  // CC+Euler: times the tail's component pairs did not fit
+  STAT_COUNT = 10
 };
 void set_stat(int slot, long long v);
 
