@@ -123,9 +123,15 @@ def kernel_bytes(name, n, A, st, o):
         # read once, the minimum vertex of every round-1 component written
         "k_r1_label": 12 * n + n // 4 + 4 * c1,
         "k_build_list": (n + 1) * o + 4 * A + 4 * n + 2 * A + 12 * E2,
-        "k_toff": (n + 1) * (o + 8 + 4) + 2 * n,
+        # offsets, the ranked tree bitmap at both row ends, the root bit, the
+        # leaf flag written
+        "k_run_flags": (n + 1) * o + 8 * n + n // 8 + n,
+        # offsets read, the row-start bitmap written
+        "k_row_starts": (n + 1) * o + A // 8,
         "k_prune_leaves": 16 * T + 2 * T + 4 * (T - K),
-        "k_pairs_succ": 16 * T + K * (16 + 16 + 16 + 8),
+        # per toured edge: its record rewritten, both arcs' ranked words, the
+        # row-start words after both arcs and a root bit, two successors
+        "k_pairs_succ": 16 * T + K * (16 + 16 + 12 + 8),
         # successor read and packed 4-byte record written per element; per
         # splitter its start, next splitter and weight
         "k_lr_walk1": 8 * N + 12 * ((N + 15) // 16),

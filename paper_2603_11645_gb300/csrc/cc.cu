@@ -167,13 +167,16 @@ enum { CNT_PAIRS = 0, CNT_COMPS = 1, CNT_LIST = 2, CNT_ROOTS = 3, CNT_NEXT = 4, 
 
 // P[u] = first neighbour of u other than u itself (the endpoint of u's
 // minimum-key edge: rows are sorted), J[u] = its CSR position; isolated
-// vertices point at themselves with J = kNone.
+// vertices point at themselves with J = kNone.  With rs set it also builds
+// the row-start bitmap the Euler stage reads (row_start_bit).
 template <class OffT>
 __global__ void k_r1_choose(const OffT* __restrict__ off, const int32_t* __restrict__ col,
                             int64_t n, int32_t* __restrict__ P, uint32_t* __restrict__ J,
-                            RowRec* __restrict__ rec, uint32_t* status) {
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-       u += (int64_t)gridDim.x * blockDim.x) {
+                            RowRec* __restrict__ rec, uint32_t* __restrict__ rs, uint32_t* status) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base <= n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = base + threadIdx.x;
+    if (rs) row_start_bit(rs, off, n, u, u <= n ? (uint64_t)off[u] : 0, u < n ? (uint64_t)off[u + 1] : 0);
+    if (u >= n) continue;
     int64_t j = (int64_t)off[u], hi = (int64_t)off[u + 1];
     if (rec) {
       RowRec r;
@@ -1416,12 +1419,14 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   const int64_t W = A / 32 + 1;
   uint2* pre_rk = nullptr;
   unsigned long long* pre_tmp = nullptr;
-  uint8_t* pre_root = nullptr;
+  uint32_t* pre_root = nullptr;
+  uint32_t* pre_rs = nullptr;
   if (prefetch_euler && state().readback && !state_overridden()) {
     pre_rk = ar.take<uint2>(W + 1);
     pre_tmp = ar.take<unsigned long long>(scan_tmp_words(W));
-    pre_root = ar.take<uint8_t>(n);
-    if (!pre_rk || !pre_tmp || !pre_root) return RST_ERR_OOM;
+    pre_root = ar.take<uint32_t>(n / 32 + 1);
+    pre_rs = ar.take<uint32_t>(row_start_words(A));
+    if (!pre_rk || !pre_tmp || !pre_root || !pre_rs) return RST_ERR_OOM;
   }
   uint32_t* status = state().status;
   unsigned long long* cnt = dev_counter(0);
@@ -1429,10 +1434,11 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   RST_CUDA(cudaMemsetAsync(b.bits, 0, (A / 32 + 2) * sizeof(uint32_t), s));
   RST_CUDA(cudaMemsetAsync(b.ctl, 0, sizeof(CcCtl), s));
   RST_CUDA(cudaMemsetAsync(b.rbits, 0, (n / 32 + 2) * sizeof(uint32_t), s));
+  if (pre_rs) RST_CUDA(cudaMemsetAsync(pre_rs, 0, row_start_words(A) * sizeof(uint32_t), s));
 
   const int gN = grid_for(n);
   prof_mark(s, "cc_setup");
-  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, status);
+  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, pre_rs, status);
   prof_mark(s, "k_r1_choose");
   RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
       off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, b.rbits, cnt, status);
@@ -1521,7 +1527,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   if (pre_rk) {
     RST_CUDA(cudaEventRecord(state().readback, s));
     RST_TRY(scan_popcount_ranked(b.bits, pre_rk, W, pre_tmp, s));
-    RST_CUDA(cudaMemsetAsync(pre_root, 0, n, s));
+    RST_CUDA(cudaMemsetAsync(pre_root, 0, (n / 32 + 1) * sizeof(uint32_t), s));
     RST_CUDA(cudaEventSynchronize(state().readback));
   } else {
     RST_CUDA(cudaStreamSynchronize(s));
@@ -1561,7 +1567,8 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   out->root_label = root >= 0 ? hctl->root_label : -1;
   out->rk = pre_rk;
   out->rk_tmp = pre_tmp;
-  out->is_root = pre_root;
+  out->root_bits = pre_root;
+  out->rs = pre_rs;
   set_stat(STAT_ROUNDS, out->rounds);
   set_stat(STAT_TAIL, tailed ? hctl->tail_rounds : 0);
   set_stat(STAT_TAIL_BACKS, hctl->tail_backs);
@@ -1578,7 +1585,7 @@ rst_status round1_forest(const OffT* off, const int32_t* col, int64_t n, int32_t
                          uint4* pairs, uint32_t* bits, unsigned long long* counters, cudaStream_t s) {
   uint32_t* status = state().status;
   const int gN = grid_for(n);
-  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, nullptr, status);
+  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, nullptr, nullptr, status);
   RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
       off, col, n, P, J, nullptr, pairs, bits, nullptr, counters, status);
   RST_CUDA(cudaGetLastError());

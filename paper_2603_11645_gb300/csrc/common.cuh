@@ -86,7 +86,7 @@ struct Tuning {
   int bfsd_bps = 2;     // device-driven BFS: 256-thread blocks per SM in its grid (1..8)
   int bfsp_bps = 1;     // persistent BFS: at most this many resident blocks per SM (1..8)
   long long insert_walk_limit = 2048;  // edge insertion: sparse rounds while walks to roots stay this short (0: never)
-  int euler_block = 256;  // block size of the tour's grid-stride kernels (toff, successors, parents): 128/256/512
+  int euler_block = 256;  // block size of the tour's grid-stride kernels (run flags, successors, parents): 128/256/512
   int pr_levels = 1;      // PR-RST: pointer-jumping levels computed per launch and host check (1..3)
 };
 Tuning& tuning();

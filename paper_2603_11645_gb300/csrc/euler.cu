@@ -5,7 +5,8 @@
 // the CSR rows are already sorted, so the tree arcs in CSR order ARE the
 // lexicographically sorted arc array, and the tree position of CSR position j
 // is the number of marked bits before j (a popcount prefix over the bitmap).
-// first[v] = toff[v], last[v] = toff[v+1]-1 and next(e) = e+1 inside a run.
+// A vertex's tree arcs form one run of consecutive tree positions, and
+// next(e) = e+1 inside a run.
 //
 // succ(e) = next(rev(e)) if rev(e) is not the last arc of its run, otherwise
 // first(from(rev(e))).  For every tree root r the arc e with rev(e) = last[r]
@@ -84,32 +85,111 @@ __device__ __forceinline__ int32_t tree_root_for(int32_t L, int32_t root_label, 
 
 __global__ void k_mark_roots(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
                              int32_t root, const int32_t* __restrict__ rootof,
-                             uint8_t* __restrict__ is_root) {
+                             uint32_t* __restrict__ root_bits) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
-       k += (int64_t)gridDim.x * blockDim.x)
-    is_root[tree_root_for(roots[k], root_label, root, rootof)] = 1;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = tree_root_for(roots[k], root_label, root, rootof);
+    atomicOr(&root_bits[r >> 5], 1u << (r & 31));
+  }
 }
 
-// Tree-arc runs: toff[v] = first tree position of v, with bit kRootBit set
-// when v is a tree root (tree positions stay below 2^31), so the successor
-// pass reads a vertex's run and its root flag in one sector.  With parent
-// set, roots and singletons also take P[v] = v; with leaf set, leaf[v] marks
-// vertices of tree degree 1 that are not tree roots.
-constexpr uint32_t kRootBit = 0x80000000u;
+__device__ __forceinline__ bool is_tree_root(const uint32_t* __restrict__ root_bits, int64_t v) {
+  return (root_bits[v >> 5] >> (v & 31)) & 1u;
+}
+
+// ----------------------------------------------------------------- row starts
+
+int64_t row_start_words(int64_t A) { return A / 32 + 2; }
+
 template <class OffT>
-__global__ void k_toff(const OffT* __restrict__ off, int64_t n, const uint2* __restrict__ rk,
-                       const uint8_t* __restrict__ is_root,
-                       uint32_t* __restrict__ toff, int32_t* __restrict__ parent, uint8_t* __restrict__ leaf) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
+__global__ void k_row_starts(const OffT* __restrict__ off, int64_t n, uint32_t* __restrict__ rs) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base <= n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    row_start_bit(rs, off, n, v, v <= n ? (uint64_t)off[v] : 0, v < n ? (uint64_t)off[v + 1] : 0);
+  }
+}
+
+template <class OffT>
+rst_status row_starts(const OffT* off, int64_t n, int64_t A, uint32_t* rs, cudaStream_t s) {
+  RST_CUDA(cudaMemsetAsync(rs, 0, row_start_words(A) * sizeof(uint32_t), s));
+  RST_LAUNCH(k_row_starts<OffT>, grid_for(n + 1), kBlock, 0, s)(off, n, rs);
+  return RST_OK;
+}
+template rst_status row_starts<int32_t>(const int32_t*, int64_t, int64_t, uint32_t*, cudaStream_t);
+template rst_status row_starts<int64_t>(const int64_t*, int64_t, int64_t, uint32_t*, cudaStream_t);
+
+// Words a row-start or tree-bit scan reads before it falls back to the
+// vertex's offsets (rows of a few arcs end within one or two words).
+constexpr int kRunScanWords = 4;
+
+// For the tree arc at CSR position pos: true iff no tree arc follows it in
+// its row, i.e. the next tree bit comes at or after the next row start (a
+// position that is both is the next row's first arc).  *ok = false when the
+// scan gave up.  Bit A of rs is set, so the scan never passes word A/32.
+__device__ __forceinline__ bool last_in_run(const uint2* __restrict__ rk, const uint32_t* __restrict__ rs,
+                                            uint64_t pos, bool* ok) {
+  uint64_t w = (pos + 1) >> 5;
+  uint32_t m = ~0u << ((pos + 1) & 31);
+  for (int it = 0; it < kRunScanWords; ++it, ++w, m = ~0u) {
+    const uint32_t t = rk[w].x & m, r = rs[w] & m;
+    if (t | r) {
+      *ok = true;
+      if (!r) return false;
+      if (!t) return true;
+      return __ffs(r) <= __ffs(t);
+    }
+  }
+  *ok = false;
+  return false;
+}
+
+// Start of the row holding CSR position pos (the last row start at or
+// before it); *ok = false when the scan gave up.
+__device__ __forceinline__ uint64_t row_start_of(const uint32_t* __restrict__ rs, uint64_t pos, bool* ok) {
+  int64_t w = (int64_t)(pos >> 5);
+  uint32_t m = (2u << (pos & 31)) - 1u;  // bits 0..pos&31 (all ones for bit 31)
+  for (int it = 0; it < kRunScanWords && w >= 0; ++it, --w, m = ~0u) {
+    const uint32_t r = rs[w] & m;
+    if (r) {
+      *ok = true;
+      return ((uint64_t)w << 5) + 31u - (uint32_t)__clz(r);
+    }
+  }
+  *ok = false;
+  return 0;
+}
+
+// Euler successor of the arc that follows the tree arc at CSR position pos
+// (tree position tp) in the tour: the next tree arc of v's row, else the
+// first one of the row (the wrap), else -1 when v is a tree root (the cut).
+template <class OffT>
+__device__ __forceinline__ int32_t run_successor(const uint2* __restrict__ rk, const uint32_t* __restrict__ rs,
+                                                 const uint32_t* __restrict__ root_bits,
+                                                 const OffT* __restrict__ off, uint64_t pos, int32_t v,
+                                                 uint32_t tp) {
+  bool ok;
+  bool last = last_in_run(rk, rs, pos, &ok);
+  if (!ok) last = tp + 1u == bit_rank2(rk, (uint64_t)off[v + 1]);
+  if (!last) return (int32_t)(tp + 1u);
+  if (is_tree_root(root_bits, v)) return -1;
+  const uint64_t st = row_start_of(rs, pos, &ok);
+  return (int32_t)bit_rank2(rk, ok ? st : (uint64_t)off[v]);
+}
+
+// Per vertex, from its tree-arc run [rank(off[v]), rank(off[v+1])): with
+// parent set, roots and singletons take P[v] = v; with leaf set, leaf[v]
+// marks vertices of tree degree 1 that are not tree roots.
+template <class OffT>
+__global__ void k_run_flags(const OffT* __restrict__ off, int64_t n, const uint2* __restrict__ rk,
+                            const uint32_t* __restrict__ root_bits, int32_t* __restrict__ parent,
+                            uint8_t* __restrict__ leaf) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t t0 = bit_rank2(rk, (uint64_t)off[v]);
-    const bool rt = v < n && is_root[v];
-    toff[v] = t0 | (rt ? kRootBit : 0u);
-    if (v < n && (parent || leaf)) {
-      const uint32_t t1 = bit_rank2(rk, (uint64_t)off[v + 1]);
-      if (parent && (t0 == t1 || rt)) parent[v] = (int32_t)v;
-      if (leaf) leaf[v] = (t1 - t0 == 1u && !rt) ? 1 : 0;
-    }
+    const uint32_t t1 = bit_rank2(rk, (uint64_t)off[v + 1]);
+    const bool rt = is_tree_root(root_bits, v);
+    if (parent && (t0 == t1 || rt)) parent[v] = (int32_t)v;
+    if (leaf) leaf[v] = (t1 - t0 == 1u && !rt) ? 1 : 0;
   }
 }
 
@@ -149,13 +229,14 @@ __global__ void __launch_bounds__(kBlock, kEuBlocksPerSm) k_prune_leaves(int64_t
   }
 }
 
+template <class OffT>
 __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
-                        int32_t root, const int32_t* __restrict__ rootof,
-                        const uint32_t* __restrict__ toff, int32_t* __restrict__ heads) {
+                        int32_t root, const int32_t* __restrict__ rootof, const OffT* __restrict__ off,
+                        const uint2* __restrict__ rk, int32_t* __restrict__ heads) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = tree_root_for(roots[k], root_label, root, rootof);
-    const uint32_t t0 = toff[r] & ~kRootBit, t1 = toff[r + 1] & ~kRootBit;
+    const uint32_t t0 = bit_rank2(rk, (uint64_t)off[r]), t1 = bit_rank2(rk, (uint64_t)off[r + 1]);
     heads[k] = t1 > t0 ? (int32_t)t0 : -1;  // -1: nothing left to tour
   }
 }
@@ -163,32 +244,34 @@ __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32
 // {p, q, a, b} (CSR positions) -> {i, k, a, b} (tree positions), in place,
 // and the Euler successors of both arcs: succ(i) follows rev(i) = k in b's
 // run (wrapping to first[b]), succ(k) follows i in a's run; the arc that
-// wraps into a tree root's first arc is cut (succ = -1).
+// wraps into a tree root's first arc is cut (succ = -1).  Whether an arc is
+// the last of its run and where its row starts come from the tree-arc and
+// row-start bitmaps (L2-resident), not from the endpoints' offsets.
+template <class OffT>
 __global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint2* __restrict__ rk,
-                             const uint32_t* __restrict__ toff, int32_t* __restrict__ succ) {
+                             const uint32_t* __restrict__ rs, const uint32_t* __restrict__ root_bits,
+                             const OffT* __restrict__ off, int32_t* __restrict__ succ) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
     uint4 r = pairs[t];
     if (r.x == kNone) continue;  // pruned leaf edge
-    const uint32_t i = bit_rank2(rk, r.x);
-    const uint32_t k = bit_rank2(rk, r.y);
+    const uint32_t p = r.x, q = r.y;
+    const uint32_t i = bit_rank2(rk, p);
+    const uint32_t k = bit_rank2(rk, q);
     const int32_t a = (int32_t)r.z, b = (int32_t)r.w;
     r.x = i;
     r.y = k;
     pairs[t] = r;
-    const uint32_t fb = toff[b], fb1 = toff[b + 1], fa = toff[a], fa1 = toff[a + 1];
-    const uint32_t lastb = (fb1 & ~kRootBit) - 1u;
-    succ[i] = (k != lastb) ? (int32_t)(k + 1u) : ((fb & kRootBit) ? -1 : (int32_t)(fb & ~kRootBit));
-    const uint32_t lasta = (fa1 & ~kRootBit) - 1u;
-    succ[k] = (i != lasta) ? (int32_t)(i + 1u) : ((fa & kRootBit) ? -1 : (int32_t)(fa & ~kRootBit));
+    succ[i] = run_successor(rk, rs, root_bits, off, q, b, k);
+    succ[k] = run_successor(rk, rs, root_bits, off, p, a, i);
   }
 }
 
 size_t euler_cc_workspace_bytes(int64_t n, int64_t A, int64_t T, int64_t nroots) {
   const int64_t W = A / 32 + 1;
   auto al = [](size_t b) { return (b + 255) / 256 * 256 + 256; };
-  size_t b = 2 * al((W + 1) * 4) + al(scan_tmp_words(W) * 8) + 2 * al(n) + 2 * al((n + 1) * 4) +
-             al(nroots * 4 + 4) + 256;
+  size_t b = al((W + 1) * 8) + al(scan_tmp_words(W) * 8) + al((n / 32 + 1) * 4) +
+             al(row_start_words(A) * 4) + al(n) + al(nroots * 4 + 4) + 256;
   return b + euler_core_bytes(T);
 }
 
@@ -197,22 +280,23 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
                          int32_t* parent_out, uint32_t* rank_out, cudaStream_t s, const int32_t** succ_view) {
   const int64_t W = A / 32 + 1;
   // the ranked bitmap and the cleared root flags may already be queued by the
-  // connectivity pass (cc->rk, cc->is_root)
-  const bool pre = cc->rk != nullptr && cc->rk_tmp != nullptr && cc->is_root != nullptr;
+  // connectivity pass (cc->rk, cc->root_bits, cc->rs)
+  const bool pre = cc->rk != nullptr && cc->rk_tmp != nullptr && cc->root_bits != nullptr && cc->rs != nullptr;
   uint2* rk = pre ? cc->rk : ar.take<uint2>(W + 1);  // {tree-arc bitmap word, prefix}
   unsigned long long* tmp = pre ? cc->rk_tmp : ar.take<unsigned long long>(scan_tmp_words(W));
-  uint8_t* is_root = pre ? cc->is_root : ar.take<uint8_t>(n);
-  uint32_t* toff = ar.take<uint32_t>(n + 1);
+  uint32_t* root_bits = pre ? cc->root_bits : ar.take<uint32_t>(n / 32 + 1);
+  uint32_t* rs = pre ? cc->rs : ar.take<uint32_t>(row_start_words(A));
   int32_t* heads = ar.take<int32_t>(cc->nroots + 1);
-  if (!rk || !tmp || !is_root || !toff || !heads) return RST_ERR_OOM;
+  if (!rk || !tmp || !root_bits || !rs || !heads) return RST_ERR_OOM;
   if (!pre) {
     RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
     prof_mark(s, "eu_bitscan");
-    RST_CUDA(cudaMemsetAsync(is_root, 0, n, s));
+    RST_CUDA(cudaMemsetAsync(root_bits, 0, (n / 32 + 1) * sizeof(uint32_t), s));
+    RST_TRY(row_starts<OffT>(off, n, A, rs, s));
   }
   if (cc->nroots > 0)
     RST_LAUNCH(k_mark_roots, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label,
-                                                         root, cc->rootof, is_root);
+                                                         root, cc->rootof, root_bits);
   prof_mark(s, "eu_roots");
   const int64_t T = cc->T;
   // Without requested ranks the tour only has to order each edge's twins, so
@@ -222,35 +306,30 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   if (prune && !leaf) return RST_ERR_OOM;
   // the plain grid-stride kernels of the tour take the tuned block size
   const int eb = tuning().euler_block;
-  RST_LAUNCH(k_toff<OffT>, grid_for(n + 1, eb, 2048 / eb), eb, 0, s)(off, n, rk, is_root, toff, parent_out,
-                                                          leaf);
-  prof_mark(s, "k_toff");
+  RST_LAUNCH(k_run_flags<OffT>, grid_for(n, eb, 2048 / eb), eb, 0, s)(off, n, rk, root_bits, parent_out, leaf);
+  prof_mark(s, "k_run_flags");
   int64_t N = 2 * T;
   if (prune) {
     RST_LAUNCH(k_prune_leaves, grid_for((T + kEuPer - 1) / kEuPer, kBlock, kEuBlocksPerSm), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
     prof_mark(s, "k_prune_leaves");
     RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
-    RST_LAUNCH(k_toff<OffT>, grid_for(n + 1, eb, 2048 / eb), eb, 0, s)(off, n, rk, is_root, toff, nullptr,
-                                                            nullptr);
-    unsigned long long left = 0;
+    uint32_t left32 = 0;
     RST_CUDA(cudaMemcpyAsync(host_scratch(8), &rk[W].y, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     RST_CUDA(cudaStreamSynchronize(s));
-    uint32_t left32 = 0;
     std::memcpy(&left32, host_scratch(8), sizeof(uint32_t));
-    left = left32;
-    N = (int64_t)left;
+    N = (int64_t)left32;
     prof_mark(s, "eu_reduced");
   }
   if (cc->nroots > 0)
-    RST_LAUNCH(k_heads, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label, root,
-                                                    cc->rootof, toff, heads);
+    RST_LAUNCH(k_heads<OffT>, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label, root,
+                                                          cc->rootof, off, rk, heads);
   RST_CUDA(cudaGetLastError());
   if (T <= 0 || N <= 0) return RST_OK;
   int32_t* succ = ar.take<int32_t>(N);
   uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
   if (!succ || !R) return RST_ERR_OOM;
   const int gT = grid_for(T, eb, 2048 / eb);
-  RST_LAUNCH(k_pairs_succ, gT, eb, 0, s)(T, cc->pairs, rk, toff, succ);
+  RST_LAUNCH(k_pairs_succ<OffT>, gT, eb, 0, s)(T, cc->pairs, rk, rs, root_bits, off, succ);
   prof_mark(s, "k_pairs_succ");
   RST_CUDA(cudaGetLastError());
   if (succ_view) *succ_view = succ;  // stays valid while the arena is not reset

@@ -39,11 +39,46 @@ struct CcOut {
   const int32_t* rootof = nullptr;
   // Set when the connectivity pass already started the Euler stage's first
   // steps while the host read its counts back: the ranked tree-arc bitmap
-  // (A/32 + 2 {word, prefix} pairs, from bits) and a zeroed root-flag array.
+  // (A/32 + 2 {word, prefix} pairs, from bits), a zeroed root bitmap
+  // (n/32 + 1 words) and the row-start bitmap (row_starts below).
   uint2* rk = nullptr;
   unsigned long long* rk_tmp = nullptr;  // the scan's scratch (reused by later scans)
-  uint8_t* is_root = nullptr;
+  uint32_t* root_bits = nullptr;
+  uint32_t* rs = nullptr;
 };
+
+// Row-start bitmap over CSR positions (A/32 + 2 words): bit j is set when a
+// non-empty row starts at position j, and bit A closes the last row.  With
+// the tree-arc bitmap it tells, for a tree arc, whether another tree arc
+// follows it in its row and where its row starts, from two small
+// L2-resident bitmaps instead of the vertex's offsets.
+int64_t row_start_words(int64_t A);
+// The bit of vertex v (v <= n; o = off[v], o1 = off[v+1] for v < n), called
+// by every lane of a warp for consecutive v (lanes past n pass v > n).
+// Offsets are non-decreasing, so a warp's positions fall in a few
+// consecutive words: the bits of one word are OR-ed across the warp first (a
+// segmented suffix OR by shuffles) and its first lane sets them with one
+// atomic.  rs must start zeroed.
+template <class OffT>
+__device__ __forceinline__ void row_start_bit(uint32_t* __restrict__ rs, const OffT*, int64_t n, int64_t v,
+                                              uint64_t o, uint64_t o1) {
+  const int lane = threadIdx.x & 31;
+  int64_t word = -1;  // lanes past n belong to no word
+  uint32_t bit = 0;
+  if (v <= n) {
+    word = (int64_t)(o >> 5);
+    if (v == n || o1 > o) bit = 1u << (o & 31);  // v == n: the end of the last row
+  }
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t b2 = __shfl_down_sync(0xffffffffu, bit, d);
+    const int64_t w2 = __shfl_down_sync(0xffffffffu, word, d);
+    if (lane + d < 32 && w2 == word) bit |= b2;
+  }
+  const int64_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
+  if (word >= 0 && bit && (lane == 0 || wprev != word)) atomicOr(&rs[word], bit);
+}
+template <class OffT>
+rst_status row_starts(const OffT* off, int64_t n, int64_t A, uint32_t* rs, cudaStream_t s);
 
 struct CcPlan;  // workspace layout, defined in cc.cu
 
@@ -51,7 +86,8 @@ struct CcPlan;  // workspace layout, defined in cc.cu
 // canonical label of every vertex.  `root` (may be -1) selects the vertex whose
 // component label is returned in out->root_label.  With prefetch_euler the
 // Euler stage's bitmap scan and root-flag clear are queued behind the count
-// read-back, so the GPU runs them while the host waits (out->rk, out->is_root).
+// read-back, so the GPU runs them while the host waits (out->rk, out->root_bits,
+// out->rs).
 template <class OffT>
 rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int64_t A,
                   int32_t root, int32_t* labels_out, CcOut* out, cudaStream_t s,
@@ -74,15 +110,6 @@ template <class OffT>
 size_t ccfast_workspace_bytes(int64_t n, int64_t A);
 
 // ----------------------------------------------------------------- Euler
-struct EulerIn {
-  int64_t n = 0;
-  int64_t T = 0;
-  uint4* pairs = nullptr;      // T records {i, k, a, b} in tree-arc positions (see below)
-  const uint32_t* toff = nullptr;  // n+1: first tree position of each vertex's run
-  const int32_t* heads = nullptr;  // one tour head (tree position) per tree
-  int64_t nheads = 0;
-};
-
 
 // CSR-bitmap front end: converts CC output into tree positions, marks roots
 // (the requested root for its component, the minimum vertex otherwise), sets

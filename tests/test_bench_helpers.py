@@ -14,7 +14,7 @@ STATS = {"T": 16_777_215, "lr_n": 17_547_804, "c1": 2_097_526, "E2": 14_763_947}
 
 
 def test_byte_models_are_positive_and_match_their_formulas():
-    names = ["k_r1_choose", "k_r1_resolve", "k_r1_label", "k_build_list", "k_toff",
+    names = ["k_r1_choose", "k_r1_resolve", "k_r1_label", "k_build_list", "k_run_flags", "k_row_starts",
              "k_prune_leaves", "k_pairs_succ", "k_lr_walk1", "k_lr_final1",
              "k_parent_from_rank", "k_parent_from_owner"]
     for nm in names:
