@@ -177,27 +177,39 @@ __device__ __forceinline__ int32_t run_successor(const uint2* __restrict__ rk, c
 }
 
 // Per vertex, from its tree-arc run [rank(off[v]), rank(off[v+1])): with
-// parent set, roots and singletons take P[v] = v; with leaf set, leaf[v]
-// marks vertices of tree degree 1 that are not tree roots.
+// parent set, roots and singletons take P[v] = v; with leaf set, the leaf
+// bitmap (n/32 + 1 words) marks vertices of tree degree 1 that are not tree
+// roots, one word per warp (a ballot: the warp's 32 vertices are one word).
 template <class OffT>
 __global__ void k_run_flags(const OffT* __restrict__ off, int64_t n, const uint2* __restrict__ rk,
                             const uint32_t* __restrict__ root_bits, int32_t* __restrict__ parent,
-                            uint8_t* __restrict__ leaf) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t0 = bit_rank2(rk, (uint64_t)off[v]);
-    const uint32_t t1 = bit_rank2(rk, (uint64_t)off[v + 1]);
-    const bool rt = is_tree_root(root_bits, v);
-    if (parent && (t0 == t1 || rt)) parent[v] = (int32_t)v;
-    if (leaf) leaf[v] = (t1 - t0 == 1u && !rt) ? 1 : 0;
+                            uint32_t* __restrict__ leaf) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    bool lf = false;
+    if (v < n) {
+      const uint32_t t0 = bit_rank2(rk, (uint64_t)off[v]);
+      const uint32_t t1 = bit_rank2(rk, (uint64_t)off[v + 1]);
+      const bool rt = is_tree_root(root_bits, v);
+      if (parent && (t0 == t1 || rt)) parent[v] = (int32_t)v;
+      lf = t1 - t0 == 1u && !rt;
+    }
+    if (leaf) {
+      const uint32_t w = __ballot_sync(0xffffffffu, lf);
+      if ((threadIdx.x & 31) == 0 && v < n) leaf[v >> 5] = w;
+    }
   }
+}
+
+__device__ __forceinline__ bool is_leaf(const uint32_t* __restrict__ leaf, uint32_t v) {
+  return (__ldg(&leaf[v >> 5]) >> (v & 31)) & 1u;
 }
 
 // Leaf pruning (rake) before the tour: a non-root vertex of tree degree 1
 // has its single tree neighbour as parent.  Its edge leaves the tree that is
 // toured (both arcs' bits are cleared) and the pair is marked done.  Removing
 // leaves changes no ancestor relation among the remaining vertices.
-__global__ void __launch_bounds__(kBlock, kEuBlocksPerSm) k_prune_leaves(int64_t T, uint4* __restrict__ pairs, const uint8_t* __restrict__ leaf,
+__global__ void __launch_bounds__(kBlock, kEuBlocksPerSm) k_prune_leaves(int64_t T, uint4* __restrict__ pairs, const uint32_t* __restrict__ leaf,
                                uint32_t* __restrict__ bits, int32_t* __restrict__ parent) {
   const int64_t tile = (int64_t)blockDim.x * kEuPer;
   for (int64_t base = (int64_t)blockIdx.x * tile; base < T; base += (int64_t)gridDim.x * tile) {
@@ -211,8 +223,8 @@ __global__ void __launch_bounds__(kBlock, kEuBlocksPerSm) k_prune_leaves(int64_t
 #pragma unroll
     for (int j = 0; j < kEuPer; ++j) {
       const int64_t t = base + (int64_t)j * blockDim.x + threadIdx.x;
-      la[j] = t < T && leaf[r[j].z];
-      lb[j] = t < T && leaf[r[j].w];
+      la[j] = t < T && is_leaf(leaf, r[j].z);
+      lb[j] = t < T && is_leaf(leaf, r[j].w);
     }
 #pragma unroll
     for (int j = 0; j < kEuPer; ++j) {
@@ -302,7 +314,7 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   // Without requested ranks the tour only has to order each edge's twins, so
   // leaves are pruned first: their parent is their single tree neighbour.
   const bool prune = rank_out == nullptr && T > 0;
-  uint8_t* leaf = prune ? ar.take<uint8_t>(n) : nullptr;
+  uint32_t* leaf = prune ? ar.take<uint32_t>(n / 32 + 1) : nullptr;
   if (prune && !leaf) return RST_ERR_OOM;
   // the plain grid-stride kernels of the tour take the tuned block size
   const int eb = tuning().euler_block;
@@ -313,25 +325,39 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
     RST_LAUNCH(k_prune_leaves, grid_for((T + kEuPer - 1) / kEuPer, kBlock, kEuBlocksPerSm), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
     prof_mark(s, "k_prune_leaves");
     RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
-    uint32_t left32 = 0;
-    RST_CUDA(cudaMemcpyAsync(host_scratch(8), &rk[W].y, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    RST_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(&left32, host_scratch(8), sizeof(uint32_t));
-    N = (int64_t)left32;
     prof_mark(s, "eu_reduced");
   }
   if (cc->nroots > 0)
     RST_LAUNCH(k_heads<OffT>, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label, root,
                                                           cc->rootof, off, rk, heads);
   RST_CUDA(cudaGetLastError());
-  if (T <= 0 || N <= 0) return RST_OK;
+  if (T <= 0) return RST_OK;
+  // The successors need only T (the array holds at most 2T arcs), so they are
+  // queued behind the read-back of the pruned arc count: the GPU builds them
+  // while the host waits for the count that sizes the ranking levels.
   int32_t* succ = ar.take<int32_t>(N);
-  uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
-  if (!succ || !R) return RST_ERR_OOM;
+  if (!succ) return RST_ERR_OOM;
+  cudaEvent_t ev = state().readback;  // none in the fixed-scratch variant: it synchronises the stream
+  // pinned read-back word (a copy into pageable memory would block the host)
+  unsigned long long* hw = state().hostbuf + 2;
+  if (prune) RST_CUDA(cudaMemcpyAsync(hw, &rk[W].y, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (prune && ev) RST_CUDA(cudaEventRecord(ev, s));
   const int gT = grid_for(T, eb, 2048 / eb);
   RST_LAUNCH(k_pairs_succ<OffT>, gT, eb, 0, s)(T, cc->pairs, rk, rs, root_bits, off, succ);
   prof_mark(s, "k_pairs_succ");
   RST_CUDA(cudaGetLastError());
+  if (prune) {
+    if (ev)
+      RST_CUDA(cudaEventSynchronize(ev));
+    else
+      RST_CUDA(cudaStreamSynchronize(s));
+    uint32_t left32 = 0;
+    std::memcpy(&left32, hw, sizeof(uint32_t));
+    N = (int64_t)left32;
+  }
+  if (N <= 0) return RST_OK;
+  uint32_t* R = rank_out ? rank_out : ar.take<uint32_t>(N);
+  if (!R) return RST_ERR_OOM;
   if (succ_view) *succ_view = succ;  // stays valid while the arena is not reset
   // Without requested ranks the parents read their positions straight from the
   // first ranking level's records (no pass writing every position).
