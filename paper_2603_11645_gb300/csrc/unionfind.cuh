@@ -36,13 +36,12 @@ __device__ __forceinline__ int32_t uf_root(const int32_t* uf, int32_t x, int64_t
 }
 
 // Merges the trees of u and v; true iff this call's CAS did the merge.  A
-// failed CAS resumes the finds from the roots just found (ancestors of u and
-// v), not from u and v again.
+// failed CAS repeats both finds from u and v: the halving writes of every
+// retry shorten the paths other links walk (resuming from the roots found
+// instead made the biconnected-components link pass 2.5x slower).
 __device__ __forceinline__ bool uf_link(int32_t* uf, int32_t u, int32_t v, int64_t n, uint32_t* status) {
-  int32_t ru = u, rv = v;
   for (int64_t it = 0; it <= n; ++it) {
-    ru = uf_find(uf, ru, n, status);
-    rv = uf_find(uf, rv, n, status);
+    const int32_t ru = uf_find(uf, u, n, status), rv = uf_find(uf, v, n, status);
     if (ru == rv) return false;
     const int32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
     if (atomicCAS(&uf[hi], hi, lo) == hi) return true;
