@@ -77,6 +77,7 @@ constexpr int kTailThreads = 1024;
 constexpr int kTailBits = 14;     // log2 kTailSlots
 constexpr int kTailMaxRounds = 64;
 constexpr size_t kTailSmem = (size_t)kTailPairs * 12 + (size_t)kTailC * 32;
+static_assert(kTailSlots % kTailThreads == 0, "the table scan takes whole blocks of slots");
 
 // Row record of a vertex, one aligned 32-byte sector: where its row starts,
 // its degree and the first kRecCols entries.  Round 1 reads the chosen
@@ -1040,16 +1041,25 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(CcPtrs b, cudaGraphCondit
   }
   __syncthreads();
   if (!s_bad) {
-    for (int slot = tid; slot < kTailSlots; slot += nt) {
+    // the table's pairs into shared memory, one position reservation per
+    // warp and step (kTailSlots is a multiple of the block size)
+    for (int s0 = 0; s0 < kTailSlots; s0 += nt) {
+      const int slot = s0 + tid;
       const unsigned long long key = b.tkey[slot];
-      if (key == ~0ull) continue;
-      const int i = atomicAdd(&s_np, 1);
-      if (i < kTailPairs) {
-        s_pu[i] = (uint32_t)(key >> 32);
-        s_pv[i] = (uint32_t)(key & 0xffffffffull);
-        s_pp[i] = b.tval[slot];
-      } else {
-        s_bad = 1;
+      const bool has = key != ~0ull;
+      const unsigned bal = __ballot_sync(0xffffffffu, has);
+      int at = 0;
+      if ((tid & 31) == 0 && bal) at = atomicAdd(&s_np, __popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (has) {
+        const int i = at + __popc(bal & ((1u << (tid & 31)) - 1u));
+        if (i < kTailPairs) {
+          s_pu[i] = (uint32_t)(key >> 32);
+          s_pv[i] = (uint32_t)(key & 0xffffffffull);
+          s_pp[i] = b.tval[slot];
+        } else {
+          s_bad = 1;
+        }
       }
     }
   }
@@ -1080,28 +1090,42 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(CcPtrs b, cudaGraphCondit
     for (int c = tid; c < C; c += nt) s_best[c] = ~0ull;
     __syncthreads();
     for (int i = tid; i < np; i += nt) {
+      // read before the atomic: slot values only fall, so most atomics are skipped
       const unsigned long long key = (unsigned long long)s_pp[i] << 32;
-      atomicMin(&s_best[s_pu[i]], key | s_pv[i]);
-      atomicMin(&s_best[s_pv[i]], key | s_pu[i]);
+      const unsigned long long ku = key | s_pv[i], kv = key | s_pu[i];
+      if (s_best[s_pu[i]] > ku) atomicMin(&s_best[s_pu[i]], ku);
+      if (s_best[s_pv[i]] > kv) atomicMin(&s_best[s_pv[i]], kv);
     }
     __syncthreads();
-    for (int c = tid; c < C; c += nt) {  // resolve
-      const unsigned long long bc = s_best[c];
-      if (bc == ~0ull) {
-        s_par[c] = c;
-        s_nid[c] = -1;
-        continue;
+    for (int c0 = 0; c0 < C; c0 += nt) {  // resolve (every lane of a warp takes each step)
+      const int c = c0 + tid;
+      bool hook = false;
+      uint32_t p = 0;
+      if (c < C) {
+        const unsigned long long bc = s_best[c];
+        if (bc == ~0ull) {
+          s_par[c] = c;
+          s_nid[c] = -1;
+        } else {
+          const int c2 = (int)(bc & 0xffffffffull);
+          p = (uint32_t)(bc >> 32);
+          if ((uint32_t)(s_best[c2] >> 32) == p && c < c2) {
+            s_par[c] = c;
+            s_nid[c] = 0;
+          } else {
+            s_par[c] = c2;
+            s_nid[c] = -2;
+            hook = true;
+          }
+        }
       }
-      const int c2 = (int)(bc & 0xffffffffull);
-      const uint32_t p = (uint32_t)(bc >> 32);
-      if ((uint32_t)(s_best[c2] >> 32) == p && c < c2) {
-        s_par[c] = c;
-        s_nid[c] = 0;
-      } else {
-        s_par[c] = c2;
-        s_nid[c] = -2;
-        b.tp[atomicAdd(&s_hooks, 1)] = p;  // fewer than C0 <= kTailC hooks in all
-      }
+      // one slot reservation per warp (a single shared counter serialises
+      // per-thread atomics); fewer than C0 <= kTailC hooks in all
+      const unsigned bal = __ballot_sync(0xffffffffu, hook);
+      int at = 0;
+      if ((tid & 31) == 0 && bal) at = atomicAdd(&s_hooks, __popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (hook) b.tp[at + __popc(bal & ((1u << (tid & 31)) - 1u))] = p;
     }
     __syncthreads();
     for (int it = 0; it < 32; ++it) {  // compress (pointer jumping in place)
