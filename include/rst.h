@@ -407,6 +407,12 @@ long long rst_launch_count(void);
  * most max, at most 10). */
 int rst_last_stats(long long *out, int max);
 void rst_profile_enable(int on);
+/* Record only the stage marks named in `names` (comma-separated, as returned
+ * by rst_profile_read; NULL or "" records every mark).  A recorded mark is an
+ * event between two kernels, which also keeps the second from being
+ * scheduled while the first drains; timing a few stages this way leaves the
+ * rest of the call as it runs unprofiled. */
+void rst_profile_only(const char *names);
 int rst_profile_read(float *ms_out, const char **names_out, int max_stages);
 
 /* Release the internal workspace of every device the library touched. */

@@ -174,6 +174,7 @@ template <class OffT>
 __global__ void k_r1_choose(const OffT* __restrict__ off, const int32_t* __restrict__ col,
                             int64_t n, int32_t* __restrict__ P, uint32_t* __restrict__ J,
                             RowRec* __restrict__ rec, uint32_t* __restrict__ rs, uint32_t* status) {
+  pdl_wait();  // launched as a programmatic dependent
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base <= n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = base + threadIdx.x;
     if (rs) row_start_bit(rs, off, n, u, u <= n ? (uint64_t)off[u] : 0, u < n ? (uint64_t)off[u + 1] : 0);
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
                              const RowRec* __restrict__ rows, uint4* __restrict__ pairs,
                              uint32_t* __restrict__ bits, uint32_t* __restrict__ rbits,
                              unsigned long long* counters, uint32_t* status) {
+  pdl_wait();  // launched as a programmatic dependent
   const uint64_t once = l2_evict_first();  // J and the records stream; L2 keeps P and the row records
   const int64_t tile = (int64_t)blockDim.x * kR1Per;
   const int lane = threadIdx.x & 31;
@@ -371,6 +373,7 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
 __global__ void k_r1_label(int64_t n, const int32_t* __restrict__ P, const uint32_t* __restrict__ J,
                            const uint2* __restrict__ rrank, int32_t* __restrict__ C1,
                            int32_t* __restrict__ minv, unsigned long long* counters) {
+  pdl_wait();  // launched as a programmatic dependent
   if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_COMPS] = rrank[n / 32 + 1].y;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
@@ -402,6 +405,7 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
                                                             const int32_t* __restrict__ tile_row,
                                                             unsigned long long* __restrict__ best,
                                                             uint32_t* status) {
+  pdl_wait();  // launched as a programmatic dependent
   __shared__ __align__(16) int32_t s_row[kArcTile];
   const uint64_t once = l2_evict_first();  // the columns stream past; L2 keeps C1 and the hook slots
   for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
@@ -525,6 +529,7 @@ struct CcPtrs {
 };
 
 __global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__ C1) {
+  pdl_wait();  // launched as a programmatic dependent
   const unsigned long long C = b.counters[CNT_COMPS];
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < (int64_t)C;
        c += (int64_t)gridDim.x * blockDim.x)
@@ -1462,14 +1467,14 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
 
   const int gN = grid_for(n);
   prof_mark(s, "cc_setup");
-  RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, pre_rs, status);
+  RST_LAUNCH_PDL((k_r1_choose<OffT>), gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, pre_rs, status);
   prof_mark(s, "k_r1_choose");
-  RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
+  RST_LAUNCH_PDL((k_r1_resolve<OffT>), grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
       off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, b.rbits, cnt, status);
   prof_mark(s, "k_r1_resolve");
   RST_TRY(scan_popcount_ranked(b.rbits, b.rrank, n / 32 + 1, b.rtmp, s));
   prof_mark(s, "r1_rootscan");
-  RST_LAUNCH(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rrank, b.C1, b.minvpool, cnt);
+  RST_LAUNCH_PDL(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rrank, b.C1, b.minvpool, cnt);
   prof_mark(s, "k_r1_label");
   CcPtrs p;
   p.col = col;
@@ -1495,15 +1500,15 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   p.tp = b.tp;
   p.ecap = b.ecap;
   p.bcap = b.bcap;
-  RST_LAUNCH(k_round_init, grid_for(n / 2 + 1), kBlock, 0, s)(p, root, b.C1);
+  RST_LAUNCH_PDL(k_round_init, grid_for(n / 2 + 1), kBlock, 0, s)(p, root, b.C1);
   prof_mark(s, "k_round_init");
   if (A > 0) {
     // one tile per block: the row searches of many resident blocks overlap;
     // entries go to list buffer 1 (round 1 reads it) and are counted in st[1].E
     const int64_t tiles = (A + kArcTile - 1) / kArcTile;
     const unsigned g = (unsigned)tiles;
-    RST_LAUNCH(k_arc_tile_rows<OffT>, grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
-    RST_LAUNCH(k_build_list<OffT>, g, kArcThreads, 0, s)(off, col, n, A, b.C1, b.Ecu[1], b.Ecv[1],
+    RST_LAUNCH_PDL((k_arc_tile_rows<OffT>), grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
+    RST_LAUNCH_PDL((k_build_list<OffT>), g, kArcThreads, 0, s)(off, col, n, A, b.C1, b.Ecu[1], b.Ecv[1],
                                                          b.Ep[1], &b.ctl->st[1].E, b.ecap, b.tile_row,
                                                          b.best[0], status);
   }

@@ -1,5 +1,6 @@
 // Shared device/host utilities of the RST library (not part of the C ABI).
 #pragma once
+#include <utility>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -48,6 +49,43 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
 void count_launch();
 void count_launches(long long k);  // kernels executed inside a graph launch
 #define RST_LAUNCH(k, ...) ::rst::count_launch(), k<<<__VA_ARGS__>>>
+
+// Programmatic dependent launch: the kernel may be scheduled while the
+// previous kernel on the stream drains (its launch latency and first blocks
+// overlap that kernel's tail).  Every kernel launched this way calls
+// pdl_wait() before it touches memory, which waits until the previous grid
+// has completed and its writes are visible; in a kernel launched plainly
+// pdl_wait() returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <class... P>
+struct PdlLaunch {
+  void (*f)(P...);
+  dim3 grid, block;
+  size_t smem;
+  cudaStream_t stream;
+  template <class... A>
+  void operator()(A&&... a) const {
+    count_launch();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, f, std::forward<A>(a)...);  // errors surface through cudaGetLastError
+  }
+};
+template <class... P>
+inline PdlLaunch<P...> pdl_launch(void (*f)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
+  return PdlLaunch<P...>{f, grid, block, smem, s};
+}
+// RST_LAUNCH_PDL(kernel, grid, block, smem, stream)(args...); a templated
+// kernel name goes in parentheses.
+#define RST_LAUNCH_PDL(...) ::rst::pdl_launch(__VA_ARGS__)
 // Stage marks: when profiling is on, records a CUDA event on `s` that ends the
 // stage `name` (a string literal); rst_profile_read returns the durations.
 void prof_mark(cudaStream_t s, const char* name);

@@ -117,6 +117,7 @@ __device__ __forceinline__ int64_t row_of_arc(const OffT* __restrict__ off, int6
 template <class OffT>
 __global__ void k_arc_tile_rows(const OffT* __restrict__ off, int64_t n, int64_t A, int64_t tiles,
                                 int32_t* __restrict__ tile_row) {
+  pdl_wait();  // launched as a programmatic dependent
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tiles;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = t * kArcTile < A ? t * kArcTile : A - 1;

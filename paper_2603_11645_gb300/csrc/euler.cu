@@ -27,6 +27,7 @@ constexpr int kEuBlocksPerSm = 6;  // resident blocks at its 40 registers
 
 __global__ void k_parent_from_rank(int64_t T, const uint4* __restrict__ pairs,
                                    const uint32_t* __restrict__ R, int32_t* __restrict__ parent) {
+  pdl_wait();  // launched as a programmatic dependent
   const uint64_t once = l2_evict_first();  // the records: read once, keep L2 for R and parent
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -48,6 +49,7 @@ __global__ void k_parent_from_owner(int64_t T, const uint4* __restrict__ pairs, 
                                     const uint32_t* __restrict__ spos, int64_t S,
                                     const unsigned long long* visited, int64_t N,
                                     int32_t* __restrict__ parent, uint32_t* status) {
+  pdl_wait();  // launched as a programmatic dependent
   if (visited && blockIdx.x == 0 && threadIdx.x == 0 && *visited != (unsigned long long)N)
     raise_error(status, DERR_NOT_FOREST);
   const uint64_t once = l2_evict_first();
@@ -86,6 +88,7 @@ __device__ __forceinline__ int32_t tree_root_for(int32_t L, int32_t root_label, 
 __global__ void k_mark_roots(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
                              int32_t root, const int32_t* __restrict__ rootof,
                              uint32_t* __restrict__ root_bits) {
+  pdl_wait();  // launched as a programmatic dependent
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = tree_root_for(roots[k], root_label, root, rootof);
@@ -184,6 +187,7 @@ template <class OffT>
 __global__ void k_run_flags(const OffT* __restrict__ off, int64_t n, const uint2* __restrict__ rk,
                             const uint32_t* __restrict__ root_bits, int32_t* __restrict__ parent,
                             uint32_t* __restrict__ leaf) {
+  pdl_wait();  // launched as a programmatic dependent
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
     bool lf = false;
@@ -211,6 +215,7 @@ __device__ __forceinline__ bool is_leaf(const uint32_t* __restrict__ leaf, uint3
 // leaves changes no ancestor relation among the remaining vertices.
 __global__ void __launch_bounds__(kBlock, kEuBlocksPerSm) k_prune_leaves(int64_t T, uint4* __restrict__ pairs, const uint32_t* __restrict__ leaf,
                                uint32_t* __restrict__ bits, int32_t* __restrict__ parent) {
+  pdl_wait();  // launched as a programmatic dependent
   const int64_t tile = (int64_t)blockDim.x * kEuPer;
   for (int64_t base = (int64_t)blockIdx.x * tile; base < T; base += (int64_t)gridDim.x * tile) {
     uint4 r[kEuPer];
@@ -245,6 +250,7 @@ template <class OffT>
 __global__ void k_heads(int64_t nroots, const int32_t* __restrict__ roots, int32_t root_label,
                         int32_t root, const int32_t* __restrict__ rootof, const OffT* __restrict__ off,
                         const uint2* __restrict__ rk, int32_t* __restrict__ heads) {
+  pdl_wait();  // launched as a programmatic dependent
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nroots;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = tree_root_for(roots[k], root_label, root, rootof);
@@ -263,6 +269,7 @@ template <class OffT>
 __global__ void k_pairs_succ(int64_t T, uint4* __restrict__ pairs, const uint2* __restrict__ rk,
                              const uint32_t* __restrict__ rs, const uint32_t* __restrict__ root_bits,
                              const OffT* __restrict__ off, int32_t* __restrict__ succ) {
+  pdl_wait();  // launched as a programmatic dependent
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
        t += (int64_t)gridDim.x * blockDim.x) {
     uint4 r = pairs[t];
@@ -307,7 +314,7 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
     RST_TRY(row_starts<OffT>(off, n, A, rs, s));
   }
   if (cc->nroots > 0)
-    RST_LAUNCH(k_mark_roots, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label,
+    RST_LAUNCH_PDL(k_mark_roots, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label,
                                                          root, cc->rootof, root_bits);
   prof_mark(s, "eu_roots");
   const int64_t T = cc->T;
@@ -318,17 +325,17 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   if (prune && !leaf) return RST_ERR_OOM;
   // the plain grid-stride kernels of the tour take the tuned block size
   const int eb = tuning().euler_block;
-  RST_LAUNCH(k_run_flags<OffT>, grid_for(n, eb, 2048 / eb), eb, 0, s)(off, n, rk, root_bits, parent_out, leaf);
+  RST_LAUNCH_PDL((k_run_flags<OffT>), grid_for(n, eb, 2048 / eb), eb, 0, s)(off, n, rk, root_bits, parent_out, leaf);
   prof_mark(s, "k_run_flags");
   int64_t N = 2 * T;
   if (prune) {
-    RST_LAUNCH(k_prune_leaves, grid_for((T + kEuPer - 1) / kEuPer, kBlock, kEuBlocksPerSm), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
+    RST_LAUNCH_PDL(k_prune_leaves, grid_for((T + kEuPer - 1) / kEuPer, kBlock, kEuBlocksPerSm), kBlock, 0, s)(T, cc->pairs, leaf, cc->bits, parent_out);
     prof_mark(s, "k_prune_leaves");
     RST_TRY(scan_popcount_ranked(cc->bits, rk, W, tmp, s));
     prof_mark(s, "eu_reduced");
   }
   if (cc->nroots > 0)
-    RST_LAUNCH(k_heads<OffT>, grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label, root,
+    RST_LAUNCH_PDL((k_heads<OffT>), grid_for(cc->nroots), kBlock, 0, s)(cc->nroots, cc->roots, cc->root_label, root,
                                                           cc->rootof, off, rk, heads);
   RST_CUDA(cudaGetLastError());
   if (T <= 0) return RST_OK;
@@ -343,7 +350,7 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   if (prune) RST_CUDA(cudaMemcpyAsync(hw, &rk[W].y, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   if (prune && ev) RST_CUDA(cudaEventRecord(ev, s));
   const int gT = grid_for(T, eb, 2048 / eb);
-  RST_LAUNCH(k_pairs_succ<OffT>, gT, eb, 0, s)(T, cc->pairs, rk, rs, root_bits, off, succ);
+  RST_LAUNCH_PDL((k_pairs_succ<OffT>), gT, eb, 0, s)(T, cc->pairs, rk, rs, root_bits, off, succ);
   prof_mark(s, "k_pairs_succ");
   RST_CUDA(cudaGetLastError());
   if (prune) {
@@ -364,11 +371,11 @@ rst_status euler_root_cc(Arena& ar, const OffT* off, int64_t n, int64_t A, int32
   LrFirstLevel lv;
   RST_TRY(list_rank(ar, N, succ, nullptr, heads, cc->nroots, R, s, rank_out ? nullptr : &lv));
   if (lv.valid) {
-    RST_LAUNCH(k_parent_from_owner, gT, eb, 0, s)(T, cc->pairs, lv.ol, lv.ol32, lv.fbits, lv.spos, lv.S,
+    RST_LAUNCH_PDL(k_parent_from_owner, gT, eb, 0, s)(T, cc->pairs, lv.ol, lv.ol32, lv.fbits, lv.spos, lv.S,
                                                       lv.visited, lv.N, parent_out, state().status);
     prof_mark(s, "k_parent_from_owner");
   } else {
-    RST_LAUNCH(k_parent_from_rank, gT, eb, 0, s)(T, cc->pairs, R, parent_out);
+    RST_LAUNCH_PDL(k_parent_from_rank, gT, eb, 0, s)(T, cc->pairs, R, parent_out);
     prof_mark(s, "k_parent_from_rank");
   }
   RST_CUDA(cudaGetLastError());

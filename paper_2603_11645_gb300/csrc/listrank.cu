@@ -117,6 +117,7 @@ __device__ __forceinline__ uint32_t wget(const uint32_t* w, int64_t x) { return 
 
 __global__ void k_lr_heads(int64_t N, int64_t S0, int sh, const int32_t* __restrict__ heads, int64_t h,
                            int32_t* __restrict__ sstart, int32_t* __restrict__ shead) {
+  pdl_wait();  // launched as a programmatic dependent
   const int32_t mask = (1 << sh) - 1;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < h;
        j += (int64_t)gridDim.x * blockDim.x) {
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(kLrWalkThreads) k_lr_walk(int64_t N, int64_t S
                                                             uint32_t* __restrict__ w_next,
                                                             unsigned long long* visited,
                                                             uint32_t* status) {
+  pdl_wait();  // launched as a programmatic dependent
   unsigned long long seen = 0;
   const int32_t mask = (1 << sh) - 1;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
@@ -205,6 +207,7 @@ __global__ void k_lr_final(int64_t N, int64_t S, const int2* __restrict__ ol,
                            const uint32_t* __restrict__ ol32, int fbits,
                            const uint32_t* __restrict__ spos, uint32_t* __restrict__ pos,
                            const unsigned long long* visited, uint32_t* status) {
+  pdl_wait();  // launched as a programmatic dependent
   if (visited && blockIdx.x == 0 && threadIdx.x == 0 && *visited != (unsigned long long)N)
     raise_error(status, DERR_NOT_FOREST);
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
@@ -217,6 +220,7 @@ __global__ void k_lr_final(int64_t N, int64_t S, const int2* __restrict__ ol,
 __global__ void __launch_bounds__(kLrBaseThreads) k_lr_base(int64_t N, const int32_t* __restrict__ nxt,
                                                             const uint32_t* __restrict__ w,
                                                             uint32_t* __restrict__ pos) {
+  pdl_wait();  // launched as a programmatic dependent
   __shared__ int32_t pj[kLrBase];
   __shared__ uint32_t val[kLrBase];
   const int n = (int)N;
@@ -320,14 +324,14 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     const int64_t S0 = (f.N + (1LL << shl) - 1) >> shl;
     const int64_t S = S0 + nheads;
     if (l == 0) RST_CUDA(cudaMemsetAsync(visited, 0, sizeof(unsigned long long), s));
-    RST_LAUNCH(k_lr_heads, grid_for(nheads), kBlock, 0, s)(f.N, S0, shl, f.heads, nheads, b.sstart, b.shead);
+    RST_LAUNCH_PDL(k_lr_heads, grid_for(nheads), kBlock, 0, s)(f.N, S0, shl, f.heads, nheads, b.sstart, b.shead);
     prof_mark(s, l == 0 ? "lr_prep1" : "lr_prep");
     int obits = 1;
     while (((int64_t)1 << obits) < S) ++obits;
     const int fbits = 32 - obits;
     if (fbits < 8) b.ol32 = nullptr;  // too many splitters to pack: full records
     lfbits[l] = fbits;
-    RST_LAUNCH(k_lr_walk, (unsigned)((S + kLrWalkThreads - 1) / kLrWalkThreads), kLrWalkThreads, 0, s)(
+    RST_LAUNCH_PDL(k_lr_walk, (unsigned)((S + kLrWalkThreads - 1) / kLrWalkThreads), kLrWalkThreads, 0, s)(
         f.N, S0, S, shl, f.nxt, f.w, b.sstart, b.ol, b.ol32, fbits, b.snext, b.w_next,
         l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_walk1" : "k_lr_walk");
@@ -336,7 +340,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
     f = Frame{S, b.snext, b.w_next, b.shead, b.spos};
   }
   if (f.N <= kLrBase) {
-    RST_LAUNCH(k_lr_base, 1, kLrBaseThreads, 0, s)(f.N, f.nxt, f.w, f.pos);
+    RST_LAUNCH_PDL(k_lr_base, 1, kLrBaseThreads, 0, s)(f.N, f.nxt, f.w, f.pos);
   } else {
     RST_CUDA(cudaMemsetAsync(wpj, 0xff, f.N * sizeof(int32_t), s));
     RST_CUDA(cudaMemsetAsync(wval, 0, f.N * sizeof(uint32_t), s));
@@ -378,7 +382,7 @@ rst_status list_rank(Arena& ar, int64_t N, const int32_t* nxt, const uint32_t* w
       break;
     }
 
-    RST_LAUNCH(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.ol32, lfbits[l], b.spos, fr.pos,
+    RST_LAUNCH_PDL(k_lr_final, grid_for(fr.N), kBlock, 0, s)(fr.N, S, b.ol, b.ol32, lfbits[l], b.spos, fr.pos,
                                                          l == 0 ? visited : nullptr, status);
     prof_mark(s, l == 0 ? "k_lr_final1" : "k_lr_final");
   }

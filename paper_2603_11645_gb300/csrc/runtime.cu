@@ -3,6 +3,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include <string>
 
 namespace rst {
 
@@ -33,11 +34,15 @@ struct Profiler {
   bool on = false;
   std::vector<std::pair<const char*, cudaEvent_t>> marks;
   std::vector<cudaEvent_t> pool;
+  std::vector<std::string> only;  // record only these marks (empty: all)
 };
 static Profiler g_prof;
 
 void prof_mark(cudaStream_t s, const char* name) {
   if (!g_prof.on || g_state_override) return;  // event creation may allocate
+  if (!g_prof.only.empty() &&
+      std::find(g_prof.only.begin(), g_prof.only.end(), name) == g_prof.only.end())
+    return;
   cudaEvent_t e;
   if (g_prof.pool.empty()) {
     if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -207,6 +212,7 @@ struct LoadPopc {
 template <class Load>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load load, int64_t count,
                                                                 unsigned long long* partial) {
+  pdl_wait();  // launched as a programmatic dependent
   __shared__ unsigned long long red[kScanThreads / 32];
   int64_t base = (int64_t)blockIdx.x * kScanTile;
   unsigned long long s = 0;
@@ -227,6 +233,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load load, int64_t
 
 // Single block: exclusive scan of `nparts` partial sums in place; total at [nparts].
 __global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* partial, int64_t nparts) {
+  pdl_wait();  // launched as a programmatic dependent
   __shared__ unsigned long long sw[33];
   unsigned long long carry = 0;
   for (int64_t base = 0; base < nparts; base += 1024) {
@@ -266,6 +273,7 @@ template <class Load, class Store>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(Load load, int64_t count,
                                                               const unsigned long long* partial,
                                                               Store store) {
+  pdl_wait();  // launched as a programmatic dependent
   __shared__ unsigned long long sw[33];
   __shared__ unsigned long long sv[kScanTile + kScanTile / 16];
   const int64_t tile0 = (int64_t)blockIdx.x * kScanTile;
@@ -303,9 +311,9 @@ static rst_status scan_impl(Load load, Store store, int64_t count, unsigned long
                             cudaStream_t s) {
   int64_t blocks = (count + kScanTile - 1) / kScanTile;
   if (blocks < 1) blocks = 1;
-  RST_LAUNCH(k_scan_reduce, (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp);
-  RST_LAUNCH(k_scan_partials, 1, 1024, 0, s)(tmp, blocks);
-  RST_LAUNCH(k_scan_down, (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp, store);
+  RST_LAUNCH_PDL((k_scan_reduce<Load>), (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp);
+  RST_LAUNCH_PDL(k_scan_partials, 1, 1024, 0, s)(tmp, blocks);
+  RST_LAUNCH_PDL((k_scan_down<Load, Store>), (unsigned)blocks, kScanThreads, 0, s)(load, count, tmp, store);
   RST_CUDA(cudaGetLastError());
   return RST_OK;
 }
@@ -342,6 +350,22 @@ void rst_profile_enable(int on) {
   for (auto& m : rst::g_prof.marks) rst::g_prof.pool.push_back(m.second);
   rst::g_prof.marks.clear();
   rst::g_prof.on = on != 0;
+}
+
+void rst_profile_only(const char* names) {
+  std::lock_guard<std::mutex> g(rst::call_lock());
+  rst::g_prof.only.clear();
+  if (!names) return;
+  std::string cur;
+  for (const char* c = names;; ++c) {
+    if (*c == ',' || *c == '\0') {
+      if (!cur.empty()) rst::g_prof.only.push_back(cur);
+      cur.clear();
+      if (*c == '\0') break;
+    } else {
+      cur.push_back(*c);
+    }
+  }
 }
 
 int rst_profile_read(float* ms_out, const char** names_out, int max_stages) {
