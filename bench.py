@@ -160,6 +160,10 @@ def run_e2e_streamed(rst, g, off, col, par, off_h, col_h, dev, stream, steps, wo
     cols = [torch.empty_like(col) for _ in range(2)]
     pars = [torch.empty_like(par) for _ in range(2)]
     par_h = [torch.empty(g.n, dtype=torch.int32).pin_memory() for _ in range(2)]
+    for b in range(2):  # untimed first copies into the fresh buffers
+        offs[b].copy_(off_h, non_blocking=True)
+        cols[b].copy_(col_h, non_blocking=True)
+        par_h[b].copy_(par, non_blocking=True)
     ev = lambda: torch.cuda.Event()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -434,7 +438,13 @@ def run_ours(args, rank, world, local_rank):
     par_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
     off_d = torch.empty_like(off)
     col_d = torch.empty_like(col)
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 10))
+    for _ in range(max(2, min(args.warmup, 3))):  # untimed: first copies from freshly pinned pages
+        off_d.copy_(off_h, non_blocking=True)
+        col_d.copy_(col_h, non_blocking=True)
+        rst.build(off_d, col_d, g.root, "cc_euler", out=par)
+        par_h.copy_(par, non_blocking=True)
+    torch.cuda.synchronize(dev)
     e2e_ms = []
     for _ in range(e2e_steps):
         flush.fill_(1)
