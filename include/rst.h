@@ -364,7 +364,14 @@ rst_status rst_build_noalloc(const void *csr_offsets, int offsets_bits, const in
  *                             256);
  *     "pr_levels_per_launch"  PR-RST computes this many pointer-jumping
  *                             levels per launch and host check, [1, 3]
- *                             (default 1; each level is recomputed exactly).
+ *                             (default 1; each level is recomputed exactly);
+ *     "giant_share_pct"       CC+Euler: when one round-1 component holds at
+ *                             least this percentage of a fixed sample of the
+ *                             vertices with edges, the contracted edge list is
+ *                             built from the rows of the other vertices only
+ *                             (the giant's rows are not read); [0, 101]
+ *                             (default 75; 0 = always from the largest
+ *                             sampled component, 101 = never).
  *   Out-of-range values and unknown keys return RST_ERR_INVALID_ARG and change
  *   nothing.  Options are process-wide: set them between calls, not during.
  * rst_get_option: reads the current value of any key above into *value (host). */
@@ -403,8 +410,10 @@ long long rst_launch_count(void);
  * ranked (after leaf pruning), and for CC+Euler the hooking rounds finished
  * by one thread block once few components remain (0: none) and the times
  * that block handed back to the grid-wide rounds because the remaining
- * component pairs did not fit.  Returns the number of values written (at
- * most max, at most 10). */
+ * component pairs did not fit, and the number of vertices whose rows built
+ * the contracted edge list when a giant round-1 component was found (-1:
+ * every row was read).  Returns the number of values written (at most max,
+ * at most 10). */
 int rst_last_stats(long long *out, int max);
 void rst_profile_enable(int on);
 /* Record only the stage marks named in `names` (comma-separated, as returned

@@ -57,6 +57,10 @@ struct CcCtl {
   unsigned int tail_overflow;   // the deduplicated pairs did not fit
   int tail_first_back;          // round of the first hand-back (0: none)
   int tail_backs;               // hand-backs
+  // the list build (below): the root vertex of a giant round-1 component
+  // (-1: none) and the number of vertices with edges outside it
+  int giant;
+  unsigned int ng;
 };
 
 // The tail: once at most kTailC components with edges remain, the list
@@ -365,26 +369,102 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
   }
 }
 
+// A giant round-1 component (power-law graphs: a hub's neighbourhood merges
+// in round 1) makes the list build a filter: almost every arc joins two
+// vertices of the giant.  A fixed, evenly spaced sample of kGiantSamples
+// vertices decides: the roots of kGiantCands spread samples are candidates,
+// and the one most samples share is the giant when it holds at least `pct`
+// percent of the samples with edges (pct 0: the most shared one always).
+// The choice changes no result, only which rows the list build reads.
+constexpr int kGiantSamples = 2048;
+constexpr int kGiantCands = 32;
+constexpr int kGiantMinSamples = 64;  // fewer samples with edges: no giant
+__global__ void __launch_bounds__(1024) k_r1_giant(int64_t n, const int32_t* __restrict__ P,
+                                                   const uint32_t* __restrict__ J, int pct, CcCtl* ctl) {
+  pdl_wait();  // launched as a programmatic dependent
+  __shared__ int32_t s_root[kGiantSamples];
+  __shared__ int32_t s_cand[kGiantCands];
+  __shared__ unsigned s_cnt[kGiantCands];
+  __shared__ unsigned s_have;
+  if (threadIdx.x == 0) s_have = 0;
+  if (threadIdx.x < kGiantCands) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < kGiantSamples; i += blockDim.x) {
+    int32_t r = -1;
+    if (n > 0 && pct <= 100) {
+      const int64_t v = ((2 * (int64_t)i + 1) * n) / (2 * kGiantSamples);
+      if (J[v] != kNone) {
+        r = P[v];
+        atomicAdd(&s_have, 1u);
+      }
+    }
+    s_root[i] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x < kGiantCands) s_cand[threadIdx.x] = s_root[threadIdx.x * (kGiantSamples / kGiantCands)];
+  __syncthreads();
+  for (int i = threadIdx.x; i < kGiantSamples; i += blockDim.x) {
+    const int32_t r = s_root[i];
+    if (r < 0) continue;
+    for (int k = 0; k < kGiantCands; ++k)
+      if (s_cand[k] == r) {  // counted under the first candidate slot holding r
+        atomicAdd(&s_cnt[k], 1u);
+        break;
+      }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int k = 1; k < kGiantCands; ++k)
+      if (s_cnt[k] > s_cnt[best]) best = k;
+    const bool giant = s_have >= (unsigned)kGiantMinSamples && s_cand[best] >= 0 &&
+                       100ull * s_cnt[best] >= (unsigned long long)pct * s_have;
+    ctl->giant = giant ? s_cand[best] : -1;
+    ctl->ng = 0;
+  }
+}
+
 // Round-1 labels: the dense id of a root with edges is its rank among those
 // roots (a popcount prefix over their bitmap, so ids follow vertex order), and
 // every non-isolated vertex takes the id of its root.  The root of a round-1
 // component is its minimum vertex (the minimum vertex w hooks to its first
 // neighbour x, whose first neighbour is w), so minv starts as the root id.
+// With a giant component, the vertices with edges outside it are collected
+// into ng (one reservation per warp; ctl->ng counts them, capacity ng_cap).
 __global__ void k_r1_label(int64_t n, const int32_t* __restrict__ P, const uint32_t* __restrict__ J,
                            const uint2* __restrict__ rrank, int32_t* __restrict__ C1,
-                           int32_t* __restrict__ minv, unsigned long long* counters) {
+                           int32_t* __restrict__ minv, unsigned long long* counters, const CcCtl* ctl,
+                           unsigned int* ng_count, int32_t* __restrict__ ng, int64_t ng_cap) {
   pdl_wait();  // launched as a programmatic dependent
   if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_COMPS] = rrank[n / 32 + 1].y;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
+  const int32_t giant = ctl ? ctl->giant : -1;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
     int32_t c = -1;
-    if (J[v] != kNone) {
+    bool out = false;
+    if (v < n && J[v] != kNone) {
       const int32_t r = P[v];
       c = (int32_t)bit_rank2(rrank, (uint64_t)r);
       if (r == (int32_t)v) minv[c] = (int32_t)v;
+      out = giant >= 0 && r != giant;
     }
-    C1[v] = c;
+    if (v < n) C1[v] = c;
+    if (giant >= 0) {
+      const unsigned bal = __ballot_sync(0xffffffffu, out);
+      unsigned at = 0;
+      if (lane == 0 && bal) at = atomicAdd(ng_count, (unsigned)__popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      const unsigned slot = at + __popc(bal & ((1u << lane) - 1u));
+      if (out && (int64_t)slot < ng_cap) ng[slot] = (int32_t)v;
+    }
   }
+}
+
+// The list is built from the giant's complement when there is a giant and
+// its complement fit the buffer.
+__device__ __forceinline__ bool sparse_list(const CcCtl* ctl, int64_t ng_cap) {
+  return ctl->giant >= 0 && (int64_t)ctl->ng <= ng_cap;
 }
 
 // The inter-component edges after round 1: every arc u->v with u < v whose
@@ -404,8 +484,10 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
                                                             unsigned long long* counter, int64_t cap,
                                                             const int32_t* __restrict__ tile_row,
                                                             unsigned long long* __restrict__ best,
+                                                            const CcCtl* ctl, int64_t ng_cap,
                                                             uint32_t* status) {
   pdl_wait();  // launched as a programmatic dependent
+  if (sparse_list(ctl, ng_cap)) return;  // k_build_list_sparse builds the list
   __shared__ __align__(16) int32_t s_row[kArcTile];
   const uint64_t once = l2_evict_first();  // the columns stream past; L2 keeps C1 and the hook slots
   for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
@@ -479,6 +561,108 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
       run += __popc(bal);
     }
     __syncthreads();
+  }
+}
+
+// k_build_list's grid: one tile per block up to this many blocks (the row
+// searches of many resident blocks overlap); larger lists loop over tiles.
+constexpr int64_t kListMaxBlocks = 1 << 16;
+
+// tile_row for k_build_list (as k_arc_tile_rows), skipped when
+// k_build_list_sparse builds the list.
+template <class OffT>
+__global__ void k_list_tile_rows(const OffT* __restrict__ off, int64_t n, int64_t A, int64_t tiles,
+                                 int32_t* __restrict__ tile_row, const CcCtl* ctl, int64_t ng_cap) {
+  pdl_wait();  // launched as a programmatic dependent
+  if (sparse_list(ctl, ng_cap)) return;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t * kArcTile < A ? t * kArcTile : A - 1;
+    tile_row[t] = (int32_t)row_of_arc(off, n, a < 0 ? 0 : a);
+  }
+}
+
+// The same list and first hook when a giant round-1 component g exists, from
+// the rows of the vertices outside it only (the list ng of k_r1_label), one
+// warp per row: an inter-component edge has at least one end outside g.  An
+// edge between two such vertices is taken from its smaller end's row; an
+// edge with one end in g from the outside end's row, its key (the position
+// of the arc min -> max) found by a search of g's end's row when that end is
+// the smaller one.
+template <class OffT>
+__global__ void __launch_bounds__(kBlock) k_build_list_sparse(const OffT* __restrict__ off,
+                                                              const int32_t* __restrict__ col, int64_t n,
+                                                              const int32_t* __restrict__ C1,
+                                                              const int32_t* __restrict__ ng, int64_t ng_cap,
+                                                              const CcCtl* ctl, unsigned long long* counter,
+                                                              int32_t* __restrict__ Ecu, int32_t* __restrict__ Ecv,
+                                                              uint32_t* __restrict__ Ep, int64_t cap,
+                                                              unsigned long long* __restrict__ best,
+                                                              uint32_t* status) {
+  pdl_wait();  // launched as a programmatic dependent
+  if (!sparse_list(ctl, ng_cap)) return;
+  const int64_t count = (int64_t)ctl->ng;
+  const int32_t cg = C1[ctl->giant];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += warps) {
+    const int32_t u = ng[w];
+    const int32_t cu = C1[u];
+    const int64_t lo = (int64_t)off[u], hi = (int64_t)off[u + 1];
+    for (int64_t a0 = lo; a0 < hi; a0 += 32) {
+      const int64_t a = a0 + lane;
+      bool emit = false;
+      int32_t eu = 0, ev = 0;
+      uint32_t p = 0;
+      if (a < hi) {
+        const int32_t v = col[a];
+        if (v < 0 || (int64_t)v >= n) {
+          raise_error(status, DERR_INDEX);
+        } else if (v != u) {
+          const int32_t cv = C1[v];
+          if (cv < 0) {
+            raise_error(status, DERR_INDEX);  // v has no arcs: the CSR is not symmetric
+          } else if (cv != cu) {
+            if (u < v) {
+              emit = true;
+              p = (uint32_t)a;
+              eu = cu;
+              ev = cv;
+            } else if (cv == cg) {  // g's rows are not read: take the edge from this side
+              const int64_t q = row_find(off, col, v, u);
+              if (q < 0) {
+                raise_error(status, DERR_INDEX);
+              } else {
+                emit = true;
+                p = (uint32_t)q;
+                eu = cv;
+                ev = cu;
+              }
+            }
+          }
+        }
+      }
+      if (emit) {  // the first contraction round's hook
+        const unsigned long long key = (unsigned long long)p << 32;
+        atomicMin(&best[eu], key | (uint32_t)ev);
+        atomicMin(&best[ev], key | (uint32_t)eu);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, emit);
+      unsigned long long at = 0;
+      if (lane == 0 && bal) at = atomicAdd(counter, (unsigned long long)__popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (emit) {
+        const unsigned long long slot = at + __popc(bal & lt);
+        if ((int64_t)slot < cap) {
+          Ecu[slot] = eu;
+          Ecv[slot] = ev;
+          Ep[slot] = p;
+        } else {
+          raise_error(status, DERR_CAPACITY);
+        }
+      }
+    }
   }
 }
 
@@ -1474,7 +1658,11 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   prof_mark(s, "k_r1_resolve");
   RST_TRY(scan_popcount_ranked(b.rbits, b.rrank, n / 32 + 1, b.rtmp, s));
   prof_mark(s, "r1_rootscan");
-  RST_LAUNCH_PDL(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rrank, b.C1, b.minvpool, cnt);
+  // the vertices outside a giant round-1 component collect in list buffer 0,
+  // which the rounds first write in round 1
+  RST_LAUNCH_PDL(k_r1_giant, 1, 1024, 0, s)(A > 0 ? n : 0, b.P, b.J, tuning().giant_pct, b.ctl);
+  RST_LAUNCH_PDL(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rrank, b.C1, b.minvpool, cnt, b.ctl,
+                                              &b.ctl->ng, b.Ecu[0], b.ecap);
   prof_mark(s, "k_r1_label");
   CcPtrs p;
   p.col = col;
@@ -1506,11 +1694,15 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
     // one tile per block: the row searches of many resident blocks overlap;
     // entries go to list buffer 1 (round 1 reads it) and are counted in st[1].E
     const int64_t tiles = (A + kArcTile - 1) / kArcTile;
-    const unsigned g = (unsigned)tiles;
-    RST_LAUNCH_PDL((k_arc_tile_rows<OffT>), grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row);
+    const unsigned g = (unsigned)std::min<int64_t>(tiles, kListMaxBlocks);
+    RST_LAUNCH_PDL((k_list_tile_rows<OffT>), grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row,
+                                                                               b.ctl, b.ecap);
     RST_LAUNCH_PDL((k_build_list<OffT>), g, kArcThreads, 0, s)(off, col, n, A, b.C1, b.Ecu[1], b.Ecv[1],
                                                          b.Ep[1], &b.ctl->st[1].E, b.ecap, b.tile_row,
-                                                         b.best[0], status);
+                                                         b.best[0], b.ctl, b.ecap, status);
+    RST_LAUNCH_PDL((k_build_list_sparse<OffT>), grid_for(n, kBlock, 8), kBlock, 0, s)(
+        off, col, n, b.C1, b.Ecu[0], b.ecap, b.ctl, &b.ctl->st[1].E, b.Ecu[1], b.Ecv[1], b.Ep[1], b.ecap,
+        b.best[0], status);
   }
   prof_mark(s, "k_build_list");
   RST_CUDA(cudaGetLastError());
@@ -1601,6 +1793,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   set_stat(STAT_ROUNDS, out->rounds);
   set_stat(STAT_TAIL, tailed ? hctl->tail_rounds : 0);
   set_stat(STAT_TAIL_BACKS, hctl->tail_backs);
+  set_stat(STAT_SPARSE, (hctl->giant >= 0 && (int64_t)hctl->ng <= b.ecap) ? (long long)hctl->ng : -1);
   set_stat(STAT_T, out->T);
   set_stat(STAT_NROOTS, out->nroots);
   return RST_OK;

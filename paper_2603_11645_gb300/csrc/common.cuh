@@ -100,6 +100,7 @@ enum StatSlot : int {
   STAT_LR_N = 6,     // elements list-ranked (tree arcs left after leaf pruning)
   STAT_TAIL = 7,     // CC+Euler: rounds the single-block tail ran (0: it did not finish the rounds)
   STAT_TAIL_BACKS = 8,  // CC+Euler: times the tail's component pairs did not fit
+  STAT_SPARSE = 9,   // CC+Euler: rows the list build read outside a giant round-1 component (-1: all rows)
   STAT_COUNT = 10
 };
 void set_stat(int slot, long long v);
@@ -126,6 +127,8 @@ struct Tuning {
   long long insert_walk_limit = 2048;  // edge insertion: sparse rounds while walks to roots stay this short (0: never)
   int euler_block = 256;  // block size of the tour's grid-stride kernels (run flags, successors, parents): 128/256/512
   int pr_levels = 1;      // PR-RST: pointer-jumping levels computed per launch and host check (1..3)
+  int giant_pct = 75;     // list build from the rows outside a round-1 component holding this
+                          // percentage of the sampled vertices (0: the largest always; 101: never)
 };
 Tuning& tuning();
 

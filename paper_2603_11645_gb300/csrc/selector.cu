@@ -652,6 +652,11 @@ rst_status rst_set_option(const char* key, long long value) {
     t.euler_block = (int)value;
     return RST_OK;
   }
+  if (std::strcmp(key, "giant_share_pct") == 0) {
+    if (value < 0 || value > 101) return RST_ERR_INVALID_ARG;
+    t.giant_pct = (int)value;
+    return RST_OK;
+  }
   if (std::strcmp(key, "insert_walk_limit") == 0) {
     if (value < 0 || value > (1LL << 30)) return RST_ERR_INVALID_ARG;
     t.insert_walk_limit = value;
@@ -677,6 +682,7 @@ rst_status rst_get_option(const char* key, long long* value) {
   else if (std::strcmp(key, "insert_walk_limit") == 0) *value = t.insert_walk_limit;
   else if (std::strcmp(key, "euler_block") == 0) *value = t.euler_block;
   else if (std::strcmp(key, "pr_levels_per_launch") == 0) *value = t.pr_levels;
+  else if (std::strcmp(key, "giant_share_pct") == 0) *value = t.giant_pct;
   else return RST_ERR_INVALID_ARG;
   return RST_OK;
 }
