@@ -372,51 +372,67 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
 // A giant round-1 component (power-law graphs: a hub's neighbourhood merges
 // in round 1) makes the list build a filter: almost every arc joins two
 // vertices of the giant.  A fixed, evenly spaced sample of kGiantSamples
-// vertices decides: the roots of kGiantCands spread samples are candidates,
-// and the one most samples share is the giant when it holds at least `pct`
-// percent of the samples with edges (pct 0: the most shared one always).
-// The choice changes no result, only which rows the list build reads.
+// vertices decides (one block of k_round_init): the roots of kGiantCands
+// spread samples are candidates, and the one most samples share is the giant
+// when it holds at least `pct` percent of the samples with edges (pct 0: the
+// most shared one always).  The choice changes no result, only which rows the
+// list build reads.
 constexpr int kGiantSamples = 2048;
 constexpr int kGiantCands = 32;
 constexpr int kGiantMinSamples = 64;  // fewer samples with edges: no giant
-__global__ void __launch_bounds__(1024) k_r1_giant(int64_t n, const int32_t* __restrict__ P,
-                                                   const uint32_t* __restrict__ J, int pct, CcCtl* ctl) {
-  pdl_wait();  // launched as a programmatic dependent
-  __shared__ int32_t s_root[kGiantSamples];
+// Run by every thread of one kBlock-thread block.
+__device__ __forceinline__ void giant_sample(int64_t n, const int32_t* __restrict__ P,
+                                             const uint32_t* __restrict__ J, int pct, CcCtl* ctl) {
+  constexpr int kPer = kGiantSamples / kBlock;
+  static_assert(kPer * kBlock == kGiantSamples && kGiantSamples % kGiantCands == 0, "sample split");
+  constexpr int kStep = kGiantSamples / kGiantCands;  // candidate c is sample c * kStep
   __shared__ int32_t s_cand[kGiantCands];
   __shared__ unsigned s_cnt[kGiantCands];
   __shared__ unsigned s_have;
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) s_have = 0;
   if (threadIdx.x < kGiantCands) s_cnt[threadIdx.x] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < kGiantSamples; i += blockDim.x) {
-    int32_t r = -1;
-    if (n > 0 && pct <= 100) {
-      const int64_t v = ((2 * (int64_t)i + 1) * n) / (2 * kGiantSamples);
-      if (J[v] != kNone) {
-        r = P[v];
-        atomicAdd(&s_have, 1u);
-      }
-    }
-    s_root[i] = r;
+  // the samples' roots (-1: isolated), all loads issued together
+  int32_t r[kPer];
+  uint32_t jv[kPer];
+  const bool on = n > 0 && pct <= 100;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int i = k * kBlock + threadIdx.x;
+    const int64_t v = ((2 * (int64_t)i + 1) * n) / (2 * kGiantSamples);
+    jv[k] = on ? J[v] : kNone;
+    r[k] = on ? P[v] : -1;
   }
+  unsigned have = 0;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if (jv[k] == kNone) r[k] = -1;
+    have += __popc(__ballot_sync(0xffffffffu, r[k] >= 0));
+    const int i = k * kBlock + threadIdx.x;
+    if (i % kStep == 0) s_cand[i / kStep] = r[k];
+  }
+  if (lane == 0) atomicAdd(&s_have, have);
   __syncthreads();
-  if (threadIdx.x < kGiantCands) s_cand[threadIdx.x] = s_root[threadIdx.x * (kGiantSamples / kGiantCands)];
-  __syncthreads();
-  for (int i = threadIdx.x; i < kGiantSamples; i += blockDim.x) {
-    const int32_t r = s_root[i];
-    if (r < 0) continue;
-    for (int k = 0; k < kGiantCands; ++k)
-      if (s_cand[k] == r) {  // counted under the first candidate slot holding r
-        atomicAdd(&s_cnt[k], 1u);
-        break;
-      }
+  // each sample counts under the first candidate slot holding its root (one
+  // shared atomic per distinct slot and warp)
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    int slot = -1;
+    if (r[k] >= 0)
+      for (int c = 0; c < kGiantCands; ++c)
+        if (s_cand[c] == r[k]) {
+          slot = c;
+          break;
+        }
+    const unsigned peers = __match_any_sync(0xffffffffu, slot);
+    if (slot >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[slot], (unsigned)__popc(peers));
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     int best = 0;
-    for (int k = 1; k < kGiantCands; ++k)
-      if (s_cnt[k] > s_cnt[best]) best = k;
+    for (int c = 1; c < kGiantCands; ++c)
+      if (s_cnt[c] > s_cnt[best]) best = c;
     const bool giant = s_have >= (unsigned)kGiantMinSamples && s_cand[best] >= 0 &&
                        100ull * s_cnt[best] >= (unsigned long long)pct * s_have;
     ctl->giant = giant ? s_cand[best] : -1;
@@ -429,43 +445,25 @@ __global__ void __launch_bounds__(1024) k_r1_giant(int64_t n, const int32_t* __r
 // every non-isolated vertex takes the id of its root.  The root of a round-1
 // component is its minimum vertex (the minimum vertex w hooks to its first
 // neighbour x, whose first neighbour is w), so minv starts as the root id.
-// With a giant component, the vertices with edges outside it are collected
-// into ng (one reservation per warp; ctl->ng counts them, capacity ng_cap).
 __global__ void k_r1_label(int64_t n, const int32_t* __restrict__ P, const uint32_t* __restrict__ J,
                            const uint2* __restrict__ rrank, int32_t* __restrict__ C1,
-                           int32_t* __restrict__ minv, unsigned long long* counters, const CcCtl* ctl,
-                           unsigned int* ng_count, int32_t* __restrict__ ng, int64_t ng_cap) {
+                           int32_t* __restrict__ minv, unsigned long long* counters) {
   pdl_wait();  // launched as a programmatic dependent
   if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_COMPS] = rrank[n / 32 + 1].y;
-  const int32_t giant = ctl ? ctl->giant : -1;
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = base + threadIdx.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
     int32_t c = -1;
-    bool out = false;
-    if (v < n && J[v] != kNone) {
+    if (J[v] != kNone) {
       const int32_t r = P[v];
       c = (int32_t)bit_rank2(rrank, (uint64_t)r);
       if (r == (int32_t)v) minv[c] = (int32_t)v;
-      out = giant >= 0 && r != giant;
     }
-    if (v < n) C1[v] = c;
-    if (giant >= 0) {
-      const unsigned bal = __ballot_sync(0xffffffffu, out);
-      unsigned at = 0;
-      if (lane == 0 && bal) at = atomicAdd(ng_count, (unsigned)__popc(bal));
-      at = __shfl_sync(0xffffffffu, at, 0);
-      const unsigned slot = at + __popc(bal & ((1u << lane) - 1u));
-      if (out && (int64_t)slot < ng_cap) ng[slot] = (int32_t)v;
-    }
+    C1[v] = c;
   }
 }
 
-// The list is built from the giant's complement when there is a giant and
-// its complement fit the buffer.
-__device__ __forceinline__ bool sparse_list(const CcCtl* ctl, int64_t ng_cap) {
-  return ctl->giant >= 0 && (int64_t)ctl->ng <= ng_cap;
-}
+// The list is built from the giant's complement when there is a giant.
+__device__ __forceinline__ bool sparse_list(const CcCtl* ctl) { return ctl->giant >= 0; }
 
 // The inter-component edges after round 1: every arc u->v with u < v whose
 // endpoints lie in different round-1 components, as {C1[u], C1[v], position}.
@@ -484,10 +482,9 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
                                                             unsigned long long* counter, int64_t cap,
                                                             const int32_t* __restrict__ tile_row,
                                                             unsigned long long* __restrict__ best,
-                                                            const CcCtl* ctl, int64_t ng_cap,
-                                                            uint32_t* status) {
+                                                            const CcCtl* ctl, uint32_t* status) {
   pdl_wait();  // launched as a programmatic dependent
-  if (sparse_list(ctl, ng_cap)) return;  // k_build_list_sparse builds the list
+  if (sparse_list(ctl)) return;  // k_build_list_sparse builds the list
   __shared__ __align__(16) int32_t s_row[kArcTile];
   const uint64_t once = l2_evict_first();  // the columns stream past; L2 keeps C1 and the hook slots
   for (int64_t a0 = (int64_t)blockIdx.x * kArcTile; a0 < A; a0 += (int64_t)gridDim.x * kArcTile) {
@@ -572,9 +569,9 @@ constexpr int64_t kListMaxBlocks = 1 << 16;
 // k_build_list_sparse builds the list.
 template <class OffT>
 __global__ void k_list_tile_rows(const OffT* __restrict__ off, int64_t n, int64_t A, int64_t tiles,
-                                 int32_t* __restrict__ tile_row, const CcCtl* ctl, int64_t ng_cap) {
+                                 int32_t* __restrict__ tile_row, const CcCtl* ctl) {
   pdl_wait();  // launched as a programmatic dependent
-  if (sparse_list(ctl, ng_cap)) return;
+  if (sparse_list(ctl)) return;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tiles;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = t * kArcTile < A ? t * kArcTile : A - 1;
@@ -583,87 +580,106 @@ __global__ void k_list_tile_rows(const OffT* __restrict__ off, int64_t n, int64_
 }
 
 // The same list and first hook when a giant round-1 component g exists, from
-// the rows of the vertices outside it only (the list ng of k_r1_label), one
-// warp per row: an inter-component edge has at least one end outside g.  An
-// edge between two such vertices is taken from its smaller end's row; an
-// edge with one end in g from the outside end's row, its key (the position
-// of the arc min -> max) found by a search of g's end's row when that end is
-// the smaller one.
+// the rows of the vertices outside it only: an inter-component edge has at
+// least one end outside g.  Each warp takes 32 consecutive vertices and
+// reads, together, the rows of those with edges outside g (ctl->ng counts
+// them).  An edge between two such vertices is taken from its smaller end's
+// row; an edge with one end in g from the outside end's row, its key (the
+// position of the arc min -> max) found by a search of g's end's row when
+// that end is the smaller one.
 template <class OffT>
-__global__ void __launch_bounds__(kBlock) k_build_list_sparse(const OffT* __restrict__ off,
+__global__ void __launch_bounds__(kBlock, 6) k_build_list_sparse(const OffT* __restrict__ off,
                                                               const int32_t* __restrict__ col, int64_t n,
-                                                              const int32_t* __restrict__ C1,
-                                                              const int32_t* __restrict__ ng, int64_t ng_cap,
-                                                              const CcCtl* ctl, unsigned long long* counter,
+                                                              const int32_t* __restrict__ C1, CcCtl* ctl,
+                                                              unsigned long long* counter,
                                                               int32_t* __restrict__ Ecu, int32_t* __restrict__ Ecv,
                                                               uint32_t* __restrict__ Ep, int64_t cap,
                                                               unsigned long long* __restrict__ best,
                                                               uint32_t* status) {
   pdl_wait();  // launched as a programmatic dependent
-  if (!sparse_list(ctl, ng_cap)) return;
-  const int64_t count = (int64_t)ctl->ng;
+  if (!sparse_list(ctl)) return;
   const int32_t cg = C1[ctl->giant];
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += warps) {
-    const int32_t u = ng[w];
-    const int32_t cu = C1[u];
-    const int64_t lo = (int64_t)off[u], hi = (int64_t)off[u + 1];
-    for (int64_t a0 = lo; a0 < hi; a0 += 32) {
-      const int64_t a = a0 + lane;
-      bool emit = false;
-      int32_t eu = 0, ev = 0;
-      uint32_t p = 0;
-      if (a < hi) {
-        const int32_t v = col[a];
-        if (v < 0 || (int64_t)v >= n) {
-          raise_error(status, DERR_INDEX);
-        } else if (v != u) {
-          const int32_t cv = C1[v];
-          if (cv < 0) {
-            raise_error(status, DERR_INDEX);  // v has no arcs: the CSR is not symmetric
-          } else if (cv != cu) {
-            if (u < v) {
-              emit = true;
-              p = (uint32_t)a;
-              eu = cu;
-              ev = cv;
-            } else if (cv == cg) {  // g's rows are not read: take the edge from this side
-              const int64_t q = row_find(off, col, v, u);
-              if (q < 0) {
-                raise_error(status, DERR_INDEX);
-              } else {
-                emit = true;
-                p = (uint32_t)q;
-                eu = cv;
-                ev = cu;
+  unsigned outside = 0;
+  constexpr int kChunks = 4;  // 32-vertex chunks per warp and step, their labels read together
+  for (int64_t w00 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * kChunks); w00 < n;
+       w00 += warps * (32 * kChunks)) {
+    int32_t cls[kChunks];
+#pragma unroll
+    for (int k = 0; k < kChunks; ++k) {
+      const int64_t v = w00 + 32 * k + lane;
+      cls[k] = v < n ? C1[v] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kChunks; ++k) {
+      const int32_t cl = cls[k];
+      unsigned todo = __ballot_sync(0xffffffffu, cl >= 0 && cl != cg);
+      outside += __popc(todo);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int32_t u = (int32_t)(w00 + 32 * k + src);
+        const int32_t cu = __shfl_sync(0xffffffffu, cl, src);
+        const int64_t lo = (int64_t)off[u], hi = (int64_t)off[u + 1];
+        for (int64_t a0 = lo; a0 < hi; a0 += 32) {
+          const int64_t a = a0 + lane;
+          bool emit = false;
+          int32_t eu = 0, ev = 0;
+          uint32_t p = 0;
+          if (a < hi) {
+            const int32_t x = col[a];
+            if (x < 0 || (int64_t)x >= n) {
+              raise_error(status, DERR_INDEX);
+            } else if (x != u) {
+              const int32_t cx = C1[x];
+              if (cx < 0) {
+                raise_error(status, DERR_INDEX);  // x has no arcs: the CSR is not symmetric
+              } else if (cx != cu) {
+                if (u < x) {
+                  emit = true;
+                  p = (uint32_t)a;
+                  eu = cu;
+                  ev = cx;
+                } else if (cx == cg) {  // g's rows are not read: take the edge from this side
+                  const int64_t q = row_find(off, col, x, u);
+                  if (q < 0) {
+                    raise_error(status, DERR_INDEX);
+                  } else {
+                    emit = true;
+                    p = (uint32_t)q;
+                    eu = cx;
+                    ev = cu;
+                  }
+                }
               }
+            }
+          }
+          if (emit) {  // the first contraction round's hook
+            const unsigned long long key = (unsigned long long)p << 32;
+            atomicMin(&best[eu], key | (uint32_t)ev);
+            atomicMin(&best[ev], key | (uint32_t)eu);
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, emit);
+          unsigned long long at = 0;
+          if (lane == 0 && bal) at = atomicAdd(counter, (unsigned long long)__popc(bal));
+          at = __shfl_sync(0xffffffffu, at, 0);
+          if (emit) {
+            const unsigned long long slot = at + __popc(bal & lt);
+            if ((int64_t)slot < cap) {
+              Ecu[slot] = eu;
+              Ecv[slot] = ev;
+              Ep[slot] = p;
+            } else {
+              raise_error(status, DERR_CAPACITY);
             }
           }
         }
       }
-      if (emit) {  // the first contraction round's hook
-        const unsigned long long key = (unsigned long long)p << 32;
-        atomicMin(&best[eu], key | (uint32_t)ev);
-        atomicMin(&best[ev], key | (uint32_t)eu);
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, emit);
-      unsigned long long at = 0;
-      if (lane == 0 && bal) at = atomicAdd(counter, (unsigned long long)__popc(bal));
-      at = __shfl_sync(0xffffffffu, at, 0);
-      if (emit) {
-        const unsigned long long slot = at + __popc(bal & lt);
-        if ((int64_t)slot < cap) {
-          Ecu[slot] = eu;
-          Ecv[slot] = ev;
-          Ep[slot] = p;
-        } else {
-          raise_error(status, DERR_CAPACITY);
-        }
-      }
     }
   }
+  if (lane == 0 && outside) atomicAdd(&ctl->ng, outside);
 }
 
 // ------------------------------------------------------------------ rounds >= 2
@@ -712,8 +728,11 @@ struct CcPtrs {
   int64_t bcap;  // slots in each best[] buffer
 };
 
-__global__ void k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__ C1) {
+__global__ void __launch_bounds__(kBlock) k_round_init(CcPtrs b, int32_t root, const int32_t* __restrict__ C1,
+                                                       int64_t n, const int32_t* __restrict__ P,
+                                                       const uint32_t* __restrict__ J, int giant_pct) {
   pdl_wait();  // launched as a programmatic dependent
+  if (blockIdx.x == 0) giant_sample(n, P, J, giant_pct, b.ctl);
   const unsigned long long C = b.counters[CNT_COMPS];
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < (int64_t)C;
        c += (int64_t)gridDim.x * blockDim.x)
@@ -1499,19 +1518,28 @@ static void launch_round_body(const CcPtrs& p, const OffT* off, cudaGraphConditi
                               int use_handle, int allow_tail, cudaStream_t s) {
   const int g = device_info().sms * tuning().round_bps;
   const int gh = device_info().sms * std::min(tuning().round_bps, kHookBlocksPerSm);
+  // stage marks only where the rounds are stepped from the host (a mark is an
+  // event, which a graph body captured here must not hold)
   RST_LAUNCH(k_round_hook, gh, kBlock, 0, s)(p);
+  if (!use_handle) prof_mark(s, "rd_hook");
   const int gr = device_info().sms * std::min(tuning().round_bps, kResolveBlocksPerSm);
   RST_LAUNCH(k_round_resolve<OffT>, gr, kBlock, 0, s)(p, off);
+  if (!use_handle) prof_mark(s, "rd_resolve");
   RST_LAUNCH(k_round_settle, g, kBlock, 0, s)(p);
+  if (!use_handle) prof_mark(s, "rd_settle");
   RST_LAUNCH(k_round_map, g, kBlock, 0, s)(p, h, use_handle, allow_tail);
+  if (!use_handle) prof_mark(s, "rd_map");
 }
 
 template <class OffT>
 static void launch_tail(const CcPtrs& p, const OffT* off, cudaGraphConditionalHandle h2, int use_handle,
                         cudaStream_t s) {
   RST_LAUNCH(k_tail_dedup, device_info().sms * 8, kBlock, 0, s)(p);
+  if (!use_handle) prof_mark(s, "tail_dedup");
   RST_LAUNCH(k_tail, 1, kTailThreads, kTailSmem, s)(p, h2, use_handle);
+  if (!use_handle) prof_mark(s, "tail_rounds");
   RST_LAUNCH(k_tail_records<OffT>, device_info().sms * 4, kBlock, 0, s)(p, off);
+  if (!use_handle) prof_mark(s, "tail_records");
 }
 
 // A while node whose body is one contraction round (captured from the
@@ -1658,11 +1686,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   prof_mark(s, "k_r1_resolve");
   RST_TRY(scan_popcount_ranked(b.rbits, b.rrank, n / 32 + 1, b.rtmp, s));
   prof_mark(s, "r1_rootscan");
-  // the vertices outside a giant round-1 component collect in list buffer 0,
-  // which the rounds first write in round 1
-  RST_LAUNCH_PDL(k_r1_giant, 1, 1024, 0, s)(A > 0 ? n : 0, b.P, b.J, tuning().giant_pct, b.ctl);
-  RST_LAUNCH_PDL(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rrank, b.C1, b.minvpool, cnt, b.ctl,
-                                              &b.ctl->ng, b.Ecu[0], b.ecap);
+  RST_LAUNCH_PDL(k_r1_label, gN, kBlock, 0, s)(n, b.P, b.J, b.rrank, b.C1, b.minvpool, cnt);
   prof_mark(s, "k_r1_label");
   CcPtrs p;
   p.col = col;
@@ -1688,7 +1712,8 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   p.tp = b.tp;
   p.ecap = b.ecap;
   p.bcap = b.bcap;
-  RST_LAUNCH_PDL(k_round_init, grid_for(n / 2 + 1), kBlock, 0, s)(p, root, b.C1);
+  RST_LAUNCH_PDL(k_round_init, grid_for(n / 2 + 1), kBlock, 0, s)(p, root, b.C1, A > 0 ? n : 0, b.P, b.J,
+                                                                  tuning().giant_pct);
   prof_mark(s, "k_round_init");
   if (A > 0) {
     // one tile per block: the row searches of many resident blocks overlap;
@@ -1696,13 +1721,12 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
     const int64_t tiles = (A + kArcTile - 1) / kArcTile;
     const unsigned g = (unsigned)std::min<int64_t>(tiles, kListMaxBlocks);
     RST_LAUNCH_PDL((k_list_tile_rows<OffT>), grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row,
-                                                                               b.ctl, b.ecap);
+                                                                               b.ctl);
     RST_LAUNCH_PDL((k_build_list<OffT>), g, kArcThreads, 0, s)(off, col, n, A, b.C1, b.Ecu[1], b.Ecv[1],
                                                          b.Ep[1], &b.ctl->st[1].E, b.ecap, b.tile_row,
-                                                         b.best[0], b.ctl, b.ecap, status);
-    RST_LAUNCH_PDL((k_build_list_sparse<OffT>), grid_for(n, kBlock, 8), kBlock, 0, s)(
-        off, col, n, b.C1, b.Ecu[0], b.ecap, b.ctl, &b.ctl->st[1].E, b.Ecu[1], b.Ecv[1], b.Ep[1], b.ecap,
-        b.best[0], status);
+                                                         b.best[0], b.ctl, status);
+    RST_LAUNCH_PDL((k_build_list_sparse<OffT>), grid_for(n, kBlock, 6), kBlock, 0, s)(
+        off, col, n, b.C1, b.ctl, &b.ctl->st[1].E, b.Ecu[1], b.Ecv[1], b.Ep[1], b.ecap, b.best[0], status);
   }
   prof_mark(s, "k_build_list");
   RST_CUDA(cudaGetLastError());
@@ -1793,7 +1817,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   set_stat(STAT_ROUNDS, out->rounds);
   set_stat(STAT_TAIL, tailed ? hctl->tail_rounds : 0);
   set_stat(STAT_TAIL_BACKS, hctl->tail_backs);
-  set_stat(STAT_SPARSE, (hctl->giant >= 0 && (int64_t)hctl->ng <= b.ecap) ? (long long)hctl->ng : -1);
+  set_stat(STAT_SPARSE, hctl->giant >= 0 ? (long long)hctl->ng : -1);
   set_stat(STAT_T, out->T);
   set_stat(STAT_NROOTS, out->nroots);
   return RST_OK;
