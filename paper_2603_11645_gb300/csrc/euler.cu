@@ -240,8 +240,7 @@ __global__ void __launch_bounds__(kBlock, kEuBlocksPerSm) k_prune_leaves(int64_t
       if (la[j]) parent[a] = b;
       atomicAnd(&bits[r[j].x >> 5], ~(1u << (r[j].x & 31)));
       atomicAnd(&bits[r[j].y >> 5], ~(1u << (r[j].y & 31)));
-      r[j].x = kNone;
-      pairs[t] = r[j];
+      pairs[t].x = kNone;  // the record's first word marks it done
     }
   }
 }
