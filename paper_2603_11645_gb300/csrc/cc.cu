@@ -603,36 +603,24 @@ __global__ void __launch_bounds__(kBlock, 6) k_build_list_sparse(const OffT* __r
   const unsigned lt = (1u << lane) - 1u;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned outside = 0;
-  // each step a warp reads the labels of 256 consecutive vertices, two
-  // 16-byte loads per lane (C1 is 256-byte aligned), both in flight together
-  constexpr int kVec = 2;
-  constexpr int kStepV = 32 * 4 * kVec;
-  for (int64_t w00 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kStepV; w00 < n;
-       w00 += warps * kStepV) {
-    int32_t cls[kVec][4];
+  constexpr int kChunks = 4;  // 32-vertex chunks per warp and step, their labels read together
+  for (int64_t w00 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * kChunks); w00 < n;
+       w00 += warps * (32 * kChunks)) {
+    int32_t cls[kChunks];
 #pragma unroll
-    for (int k = 0; k < kVec; ++k) {
-      const int64_t v0 = w00 + 128 * k + 4 * lane;
-      if (v0 + 3 < n) {
-        const int4 t = __ldg(reinterpret_cast<const int4*>(C1 + v0));
-        cls[k][0] = t.x;
-        cls[k][1] = t.y;
-        cls[k][2] = t.z;
-        cls[k][3] = t.w;
-      } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) cls[k][i] = v0 + i < n ? C1[v0 + i] : -1;
-      }
+    for (int k = 0; k < kChunks; ++k) {
+      const int64_t v = w00 + 32 * k + lane;
+      cls[k] = v < n ? C1[v] : -1;
     }
 #pragma unroll
-    for (int k = 0; k < kVec * 4; ++k) {
-      const int32_t cl = cls[k >> 2][k & 3];
+    for (int k = 0; k < kChunks; ++k) {
+      const int32_t cl = cls[k];
       unsigned todo = __ballot_sync(0xffffffffu, cl >= 0 && cl != cg);
       outside += __popc(todo);
       while (todo) {
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
-        const int32_t u = (int32_t)(w00 + 128 * (k >> 2) + 4 * src + (k & 3));
+        const int32_t u = (int32_t)(w00 + 32 * k + src);
         const int32_t cu = __shfl_sync(0xffffffffu, cl, src);
         const int64_t lo = (int64_t)off[u], hi = (int64_t)off[u + 1];
         for (int64_t a0 = lo; a0 < hi; a0 += 32) {
