@@ -214,27 +214,31 @@ __global__ void k_r1_choose(const OffT* __restrict__ off, const int32_t* __restr
 // the tree edge and shortcut u to its root (in place; any value a concurrent
 // reader sees is an ancestor, and a 2-cycle is a mutual pair whose smaller id
 // is the root).
-constexpr int kR1Per = 2;  // vertices per thread and step in round-1 resolve
-constexpr int kR1BlocksPerSm = 5;
-template <class OffT>
-__global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const OffT* __restrict__ off, const int32_t* __restrict__ col,
+// Vertices per thread and step, and the blocks per SM their registers allow:
+// two on meshes; three where rows are long (the twin searches of power-law
+// graphs gain from the third chain in flight, meshes lose a little).
+constexpr int kR1Per = 2, kR1BlocksPerSm = 5;
+constexpr int kR1PerLong = 3, kR1BlocksPerSmLong = 4;
+constexpr int64_t kR1LongRowDegree = 8;  // arcs per vertex above which rows count as long
+template <class OffT, int kPer, int kBps>
+__global__ void __launch_bounds__(kBlock, kBps) k_r1_resolve(const OffT* __restrict__ off, const int32_t* __restrict__ col,
                              int64_t n, int32_t* P, const uint32_t* __restrict__ J,
                              const RowRec* __restrict__ rows, uint4* __restrict__ pairs,
                              uint32_t* __restrict__ bits, uint32_t* __restrict__ rbits,
                              unsigned long long* counters, uint32_t* status) {
   pdl_wait();  // launched as a programmatic dependent
   const uint64_t once = l2_evict_first();  // J and the records stream; L2 keeps P and the row records
-  const int64_t tile = (int64_t)blockDim.x * kR1Per;
+  const int64_t tile = (int64_t)blockDim.x * kPer;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
     // Every load of a step is issued for both vertices before either is used:
     // own pointers, then the chosen neighbours' records, then the chases in
     // lockstep.  Positions fit 32 bits (fewer than 2^32 arcs).
-    int32_t v0[kR1Per], y[kR1Per];
+    int32_t v0[kPer], y[kPer];
     uint32_t act = 0;
 #pragma unroll
-    for (int j = 0; j < kR1Per; ++j) {
+    for (int j = 0; j < kPer; ++j) {
       const int64_t u = base + (int64_t)j * blockDim.x + threadIdx.x;
       v0[j] = u < n ? P[u] : (int32_t)u;  // only this thread writes P[u]
       if (u < n && v0[j] != (int32_t)u) act |= 1u << j;
@@ -242,15 +246,15 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
     // v0's first choice y0 (its first non-self entry) and u's position q in
     // v0's row: from v0's record when it holds the whole row, else from P and
     // a binary search of the row
-    uint32_t q[kR1Per];
+    uint32_t q[kPer];
     uint32_t haveq = 0;
     if (rows) {
-      RowRec R[kR1Per];
+      RowRec R[kPer];
 #pragma unroll
-      for (int j = 0; j < kR1Per; ++j)
+      for (int j = 0; j < kPer; ++j)
         if ((act >> j) & 1u) R[j] = rows[v0[j]];
 #pragma unroll
-      for (int j = 0; j < kR1Per; ++j) {
+      for (int j = 0; j < kPer; ++j) {
         y[j] = -1;
         q[j] = kNone;
         if (!((act >> j) & 1u)) continue;
@@ -264,20 +268,20 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
         if (R[j].deg <= (uint32_t)kRecCols) haveq |= 1u << j;
       }
 #pragma unroll
-      for (int j = 0; j < kR1Per; ++j)  // long row of self-loops, or a bad id
+      for (int j = 0; j < kPer; ++j)  // long row of self-loops, or a bad id
         if (((act >> j) & 1u) && (y[j] < 0 || (int64_t)y[j] >= n)) y[j] = P[v0[j]];
     } else {
 #pragma unroll
-      for (int j = 0; j < kR1Per; ++j) {
+      for (int j = 0; j < kPer; ++j) {
         y[j] = -1;
         q[j] = kNone;
         if ((act >> j) & 1u) y[j] = P[v0[j]];
       }
     }
     uint32_t emit = 0, chase = 0;
-    int32_t x[kR1Per], root[kR1Per];
+    int32_t x[kPer], root[kPer];
 #pragma unroll
-    for (int j = 0; j < kR1Per; ++j) {
+    for (int j = 0; j < kPer; ++j) {
       x[j] = 0;
       root[j] = -1;
       if (!((act >> j) & 1u)) continue;
@@ -313,9 +317,9 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
       }
     }
     for (int64_t it = 0; chase && it <= n; ++it) {
-      int32_t z[kR1Per];
+      int32_t z[kPer];
 #pragma unroll
-      for (int j = 0; j < kR1Per; ++j) {
+      for (int j = 0; j < kPer; ++j) {
         z[j] = 0;
         if ((chase >> j) & 1u) {
           if (y[j] == x[j]) {
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
         }
       }
 #pragma unroll
-      for (int j = 0; j < kR1Per; ++j) {
+      for (int j = 0; j < kPer; ++j) {
         if (!((chase >> j) & 1u)) continue;
         if (z[j] == x[j]) {
           root[j] = x[j] < y[j] ? x[j] : y[j];
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
       }
     }
 #pragma unroll
-    for (int j = 0; j < kR1Per; ++j) {
+    for (int j = 0; j < kPer; ++j) {
       if (!((act >> j) & 1u)) continue;
       const int64_t u = base + (int64_t)j * blockDim.x + threadIdx.x;
       if (root[j] < 0) {
@@ -351,11 +355,11 @@ __global__ void __launch_bounds__(kBlock, kR1BlocksPerSm) k_r1_resolve(const Off
     }
     unsigned wtot = 0;
 #pragma unroll
-    for (int j = 0; j < kR1Per; ++j) wtot += __popc(__ballot_sync(0xffffffffu, (emit >> j) & 1u));
+    for (int j = 0; j < kPer; ++j) wtot += __popc(__ballot_sync(0xffffffffu, (emit >> j) & 1u));
     const unsigned long long mine = block_reserve<kBlock>(&counters[CNT_PAIRS], lane == 0 ? wtot : 0u);
     unsigned long long run = __shfl_sync(0xffffffffu, mine, 0);
 #pragma unroll
-    for (int j = 0; j < kR1Per; ++j) {
+    for (int j = 0; j < kPer; ++j) {
       const unsigned bal = __ballot_sync(0xffffffffu, (emit >> j) & 1u);
       if ((emit >> j) & 1u) {
         const int64_t u = base + (int64_t)j * blockDim.x + threadIdx.x;
@@ -563,7 +567,10 @@ __global__ void __launch_bounds__(kArcThreads, 6) k_build_list(const OffT* __res
 
 // k_build_list's grid: one tile per block up to this many blocks (the row
 // searches of many resident blocks overlap); larger lists loop over tiles.
+// Graphs with long rows take a smaller grid: there a giant round-1 component
+// usually makes the kernel exit at once, and every launched block costs.
 constexpr int64_t kListMaxBlocks = 1 << 16;
+constexpr int64_t kListMaxBlocksLong = 1 << 12;
 
 // tile_row for k_build_list (as k_arc_tile_rows), skipped when
 // k_build_list_sparse builds the list.
@@ -1681,8 +1688,13 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
   prof_mark(s, "cc_setup");
   RST_LAUNCH_PDL((k_r1_choose<OffT>), gN, kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, pre_rs, status);
   prof_mark(s, "k_r1_choose");
-  RST_LAUNCH_PDL((k_r1_resolve<OffT>), grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
-      off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, b.rbits, cnt, status);
+  if (A > kR1LongRowDegree * n)
+    RST_LAUNCH_PDL((k_r1_resolve<OffT, kR1PerLong, kR1BlocksPerSmLong>),
+                   grid_for((n + kR1PerLong - 1) / kR1PerLong, kBlock, kR1BlocksPerSmLong), kBlock, 0, s)(
+        off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, b.rbits, cnt, status);
+  else
+    RST_LAUNCH_PDL((k_r1_resolve<OffT, kR1Per, kR1BlocksPerSm>), grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm),
+                   kBlock, 0, s)(off, col, n, b.P, b.J, b.rec, b.pairs, b.bits, b.rbits, cnt, status);
   prof_mark(s, "k_r1_resolve");
   RST_TRY(scan_popcount_ranked(b.rbits, b.rrank, n / 32 + 1, b.rtmp, s));
   prof_mark(s, "r1_rootscan");
@@ -1719,7 +1731,7 @@ rst_status cc_run(Arena& ar, const OffT* off, const int32_t* col, int64_t n, int
     // one tile per block: the row searches of many resident blocks overlap;
     // entries go to list buffer 1 (round 1 reads it) and are counted in st[1].E
     const int64_t tiles = (A + kArcTile - 1) / kArcTile;
-    const unsigned g = (unsigned)std::min<int64_t>(tiles, kListMaxBlocks);
+    const unsigned g = (unsigned)std::min<int64_t>(tiles, A > kR1LongRowDegree * n ? kListMaxBlocksLong : kListMaxBlocks);
     RST_LAUNCH_PDL((k_list_tile_rows<OffT>), grid_for(tiles + 1), kBlock, 0, s)(off, n, A, tiles, b.tile_row,
                                                                                b.ctl);
     RST_LAUNCH_PDL((k_build_list<OffT>), g, kArcThreads, 0, s)(off, col, n, A, b.C1, b.Ecu[1], b.Ecv[1],
@@ -1832,7 +1844,7 @@ rst_status round1_forest(const OffT* off, const int32_t* col, int64_t n, int32_t
   uint32_t* status = state().status;
   const int gN = grid_for(n);
   RST_LAUNCH(k_r1_choose<OffT>, gN, kBlock, 0, s)(off, col, n, P, J, nullptr, nullptr, status);
-  RST_LAUNCH(k_r1_resolve<OffT>, grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
+  RST_LAUNCH((k_r1_resolve<OffT, kR1Per, kR1BlocksPerSm>), grid_for((n + kR1Per - 1) / kR1Per, kBlock, kR1BlocksPerSm), kBlock, 0, s)(
       off, col, n, P, J, nullptr, pairs, bits, nullptr, counters, status);
   RST_CUDA(cudaGetLastError());
   return RST_OK;
