@@ -37,12 +37,18 @@ def test_option_defaults_roundtrip_and_rejects(rst_lib):
                      ("bfs_device_blocks_per_sm", 9), ("bfs_persistent_blocks_per_sm", 0),
                      ("euler_block", 64), ("euler_block", 384), ("insert_walk_limit", -1),
                      ("pr_levels_per_launch", 0), ("pr_levels_per_launch", 4),
+                     ("giant_share_pct", -1), ("giant_share_pct", 102),
                      ("no_such_knob", 1)]:
         with pytest.raises(rst.RstError):
             rst.set_option(key, bad)
     assert rst.get_option("lr_spacing") == 128  # a rejected value changes nothing
     rst.set_option("round_blocks_per_sm", 3)
     assert rst.get_option("round_blocks_per_sm") == 3
+    # the giant-component list build's share: default 75, 0 and 101 accepted
+    assert rst.get_option("giant_share_pct") == 75
+    for v in (0, 101, 75):
+        rst.set_option("giant_share_pct", v)
+        assert rst.get_option("giant_share_pct") == v
 
 
 def test_bucket_lookup():

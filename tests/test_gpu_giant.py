@@ -152,12 +152,3 @@ def test_default_share_picks_the_path():
             assert 0 <= sparse < g.n // 4, g.name
         else:
             assert sparse == -1, g.name
-
-
-def test_share_option_range():
-    import paper_2603_11645_gb300 as rst
-    with pytest.raises(Exception):
-        rst.set_option("giant_share_pct", 102)
-    with pytest.raises(Exception):
-        rst.set_option("giant_share_pct", -1)
-    assert rst.get_option("giant_share_pct") == 75
